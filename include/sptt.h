@@ -1,0 +1,308 @@
+/*
+ * sptt — sparse CP-ALS on one GB300 GPU (sm_103a). C ABI.
+ *
+ * The method is CP-ALS over a tensor stored in compressed sparse fiber (CSF)
+ * form, as studied in "Parallel Sparse Tensor Decomposition in Chapel"
+ * (Rolinger, Simon, Krieger; arXiv:1812.05961): Section III (CP-ALS, MTTKRP,
+ * CSF), Algorithm 1 (the ALS loop), Section V-A (V^dagger through
+ * potrf/potrs), Section V-C (the non-zero sort).
+ *
+ * Conventions shared by every entry point:
+ *  - Every function returns an sptt_status: SPTT_OK (0) or a negative error.
+ *    No exception, abort or exit crosses this boundary. A human-readable
+ *    detail of the last error on the calling thread is sptt_last_error().
+ *  - Input arrays are borrowed for the duration of the call only.
+ *  - Handles (sptt_csf, sptt_cpd) are owned by the library and released by
+ *    their *_free function; caller-owned output buffers stay caller-owned.
+ *  - "device" pointers are CUDA device (or managed) memory of the current
+ *    device; "host or device" pointers may be either (unified addressing
+ *    decides the copy direction).
+ *  - Work is enqueued on the given stream (NULL = the legacy default
+ *    stream). Functions that must read a result back (sizes, error flags,
+ *    fits) synchronise that stream and say so.
+ *  - Indices are 0-based int32; dims are int64 but each must be <= 2^31 - 1;
+ *    nnz must be < 2^31. 2 <= nmodes <= SPTT_MAX_MODES.
+ *  - There is no CPU fallback: without a usable CUDA device every compute
+ *    entry point returns SPTT_ERR_CUDA.
+ */
+#ifndef SPTT_H
+#define SPTT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *sptt_stream; /* a cudaStream_t */
+typedef int32_t sptt_status;
+
+#define SPTT_OK 0
+#define SPTT_ERR_BAD_ARG (-1)     /* invalid argument: sizes, null pointers, index >= dim */
+#define SPTT_ERR_OOM (-2)         /* a device allocation failed */
+#define SPTT_ERR_CUDA (-3)        /* a CUDA runtime call or kernel failed */
+#define SPTT_ERR_TIMEOUT (-4)     /* a bounded device-side wait ran out */
+#define SPTT_ERR_NOT_PD (-5)      /* reported by sptt_cpd_solve_branch only (not an error) */
+#define SPTT_ERR_UNSUPPORTED (-6) /* valid but outside this build's limits (e.g. rank > 64) */
+#define SPTT_ERR_INTERNAL (-7)
+
+#define SPTT_MAX_MODES 5
+#define SPTT_MAX_RANK_ALS 64      /* rank limit of the CP-ALS entry points */
+
+/* Factor element types for MTTKRP gathers. */
+#define SPTT_F32 0
+#define SPTT_BF16 1
+
+/* Readable name of a status code (static string). */
+const char *sptt_status_str(sptt_status s);
+/* Detail of the last error raised on this thread ("" if none). */
+const char *sptt_last_error(void);
+/* Library version as major*10000 + minor*100 + patch. */
+int32_t sptt_version(void);
+
+/*
+ * A coordinate-format (COO) tensor, borrowed by every call that takes it.
+ *   nmodes      number of modes N (2..SPTT_MAX_MODES)
+ *   nnz         number of stored entries (may include duplicate coordinates,
+ *               which are summed, Section V-C "Sort")
+ *   dims        host array [nmodes], mode lengths I_m
+ *   inds        host array of nmodes pointers; inds[m] points to nnz int32
+ *               indices of mode m (device memory if on_device, else host)
+ *   vals        nnz float values (device if on_device, else host)
+ *   on_device   1: inds[m] and vals are device pointers; 0: host pointers
+ *               (copied to the device inside the call)
+ */
+typedef struct {
+    int32_t nmodes;
+    int64_t nnz;
+    const int64_t *dims;
+    const int32_t *const *inds;
+    const float *vals;
+    int32_t on_device;
+} sptt_coo;
+
+/* ------------------------------------------------------------------------ */
+/* CSF (Section III): one tree per root mode.                               */
+/* ------------------------------------------------------------------------ */
+
+typedef struct sptt_csf sptt_csf;
+
+/*
+ * Build the CSF of a COO tensor rooted at root_mode (Section III), after
+ * sorting its non-zeros lexicographically in level order and summing
+ * duplicates (Section V-C). level_order (host, nmodes entries, NULL = default)
+ * is the mode stored at each tree level and must start with root_mode; the
+ * default is root_mode followed by the other modes in ascending length, ties
+ * to the lower mode id. The result lives in device memory and is identical,
+ * integer for integer, to the plain construction:
+ *   level l < N-1: fids[l][f] = index of fiber f, fptr[l][f] = its first child
+ *   at level l+1, fptr[l][nfibs[l]] = nfibs[l+1];
+ *   leaf level N-1: fids[N-1][k] and vals[k] per coalesced non-zero, where a
+ *   duplicate group's value is its FP64 sum in input order rounded to FP32.
+ * Errors: BAD_ARG (bad sizes/pointers, an index outside [0, dim), bad
+ * order), OOM, CUDA. Synchronises the stream (it reads back sizes).
+ */
+sptt_status sptt_csf_build(const sptt_coo *coo, int32_t root_mode, const int32_t *level_order,
+                           sptt_stream stream, sptt_csf **out);
+
+/* Release a CSF (NULL is ignored). The caller ensures no work using it is
+ * still pending. */
+void sptt_csf_free(sptt_csf *csf);
+
+/*
+ * Shape of a CSF: nmodes, the level order (order[l] = mode at level l) and
+ * nfibs[l] (fibers at level l; nfibs[N-1] = coalesced nnz). Output arrays are
+ * host, nmodes entries each; any may be NULL.
+ */
+sptt_status sptt_csf_shape(const sptt_csf *csf, int32_t *nmodes, int32_t *order, int64_t *nfibs);
+
+/*
+ * Copy level l of a CSF into caller buffers (host or device; any may be
+ * NULL): fptr (nfibs[l]+1 int32, only for l < N-1), fids (nfibs[l] int32),
+ * vals (nfibs[N-1] float, only for l = N-1). Synchronises the stream.
+ */
+sptt_status sptt_csf_copy_level(const sptt_csf *csf, int32_t level, int32_t *fptr, int32_t *fids,
+                                float *vals, sptt_stream stream);
+
+/* ------------------------------------------------------------------------ */
+/* MTTKRP (Section III; Algorithm 1 lines 5, 8, 11).                        */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Optional schedule for the MTTKRP kernels (the autotuner's knobs).
+ *   chunk       non-zeros per work unit of a lane group; power of two in
+ *               [16, 4096]; 0 = default
+ *   block       threads per CTA (multiple of 32, <= 256); 0 = default
+ *   variant     0 = default kernel; other ids select alternative kernels
+ */
+typedef struct {
+    int32_t chunk;
+    int32_t block;
+    int32_t variant;
+} sptt_sched;
+
+/*
+ * M = X_(n) (Khatri-Rao product of A^(m), m != n), n = the CSF's root mode,
+ * computed by traversing the CSF tree (Section III):
+ *   M[i, c] = sum over non-zeros (i, i_1, ..., v) of v * prod_{m != n} A^(m)[i_m, c].
+ *   factors   host array of nmodes device pointers; factors[m] is A^(m),
+ *             row-major dims[m] x ld, of factor_dtype (SPTT_F32 or SPTT_BF16);
+ *             factors[n] is not read and may be NULL. Rows must be 16-byte
+ *             aligned (base 16-byte aligned and ld a multiple of 4 for F32 /
+ *             8 for BF16).
+ *   ld        row stride in elements and the number of columns computed;
+ *             4 <= ld <= 128 (F32) or 8 <= ld <= 256 (BF16). Callers with a
+ *             rank below ld pad the extra columns (zero columns give zero
+ *             output columns).
+ *   out       device float, dims[n] x ld row-major, overwritten (rows absent
+ *             from the tensor become 0). Must not alias a factor.
+ *   sched     NULL = default schedule.
+ * Accumulation is FP32. Asynchronous on the stream. Errors: BAD_ARG.
+ */
+sptt_status sptt_mttkrp(const sptt_csf *csf, const void *const *factors, int32_t factor_dtype,
+                        int32_t ld, float *out, const sptt_sched *sched, sptt_stream stream);
+
+/* ------------------------------------------------------------------------ */
+/* Dense R x R pieces (Algorithm 1 lines 4, 7, 10).                          */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * G = A^T A over the first `rank` columns of A (device, rows x ld row-major
+ * FP32, ld >= rank, ld multiple of 4), into G (device, rank x rank FP64,
+ * row-major). Products are formed in FP32 and summed in FP32 over 64-row
+ * tiles, the tile sums in FP64. Asynchronous. rank <= SPTT_MAX_RANK_ALS.
+ */
+sptt_status sptt_gram(const float *A, int64_t rows, int32_t rank, int32_t ld, double *G,
+                      sptt_stream stream);
+
+/* ------------------------------------------------------------------------ */
+/* CP-ALS (Algorithm 1, N modes).                                           */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Options of a CP-ALS run (zero-initialise for the defaults).
+ *   seed          seed of the U(0,1) Philox4x64-10 initial factors
+ *   precision     SPTT_F32: FP32 factor gathers; SPTT_BF16: BF16 gathers
+ *                 with FP32 accumulation, followed by refine_iters FP32
+ *                 iterations (the FP32 refinement sweep)
+ *   refine_iters  FP32 iterations after a BF16 run (default 1 when
+ *                 precision = SPTT_BF16; ignored for F32)
+ *   use_graph     1: run each iteration as one captured CUDA graph
+ *   profile       1: record per-routine CUDA-event timers (sptt_cpd_timers)
+ *   sched         per-kernel schedule override (NULL = default)
+ */
+typedef struct {
+    uint64_t seed;
+    int32_t precision;
+    int32_t refine_iters;
+    int32_t use_graph;
+    int32_t profile;
+    const sptt_sched *sched;
+} sptt_opts;
+
+typedef struct sptt_cpd sptt_cpd;
+
+/*
+ * Prepare a CP-ALS run: copy the COO to the device if needed, build one CSF
+ * per mode (rooted at that mode), allocate factors and workspace, and
+ * compute |X|^2. Factors are not initialised (see sptt_cpd_init). rank in
+ * [1, SPTT_MAX_RANK_ALS]. All later work of the handle runs on `stream`.
+ * Synchronises the stream. Errors: BAD_ARG, UNSUPPORTED, OOM, CUDA.
+ */
+sptt_status sptt_cpd_create(const sptt_coo *coo, int32_t rank, const sptt_opts *opts,
+                            sptt_stream stream, sptt_cpd **out);
+
+/* Release a CP-ALS handle (NULL is ignored). Synchronises its stream. */
+void sptt_cpd_free(sptt_cpd *cpd);
+
+/*
+ * Initialise the factors (Algorithm 1 line 2). init = NULL: U(0,1) from the
+ * Philox4x64-10 stream of opts.seed (key (seed, mode), counter (e/4,0,0,0),
+ * word e mod 4, e = row*rank + col; value ((w >> 41) + 0.5) / 2^23). Else
+ * init is a host array of nmodes pointers (host or device) to dims[m] x rank
+ * row-major float factors. Resets the fit history. Asynchronous.
+ */
+sptt_status sptt_cpd_init(sptt_cpd *cpd, const float *const *init);
+
+/*
+ * Run up to `iters` ALS iterations (Algorithm 1 lines 3-13): per mode n in
+ * order, V = Hadamard of the other modes' Grams, A^(n) = MTTKRP_n V^dagger
+ * (Cholesky in FP64; pseudo-inverse when V is not positive definite),
+ * normalise the columns into lambda, refresh G_n; then the fit. With
+ * tol > 0 the stream is synchronised after each iteration and the run stops
+ * once |fit - fit_prev| < tol (not before the second iteration overall);
+ * with tol = 0 all iterations are enqueued without synchronising.
+ * iters_done (may be NULL) receives the iterations run by this call.
+ * The precision of these iterations is opts.precision.
+ */
+sptt_status sptt_cpd_iterate(sptt_cpd *cpd, int32_t iters, double tol, int32_t *iters_done);
+
+/*
+ * Run `iters` iterations with FP32 gathers regardless of opts.precision
+ * (the refinement sweep of a mixed-precision run). Same semantics as
+ * sptt_cpd_iterate with tol = 0.
+ */
+sptt_status sptt_cpd_refine(sptt_cpd *cpd, int32_t iters);
+
+/* Fit after the last iteration and the number of iterations run since
+ * sptt_cpd_init. Synchronises. */
+sptt_status sptt_cpd_fit(sptt_cpd *cpd, double *fit, int32_t *iters);
+
+/* The fits of the last min(cap, iterations since init, 4096) iterations,
+ * oldest first, into fits (host); *count (may be NULL) receives how many.
+ * Synchronises. */
+sptt_status sptt_cpd_fit_history(sptt_cpd *cpd, double *fits, int32_t cap, int32_t *count);
+
+/* lambda (rank doubles, host or device): the column norms of the last mode
+ * updated. Synchronises. */
+sptt_status sptt_cpd_lambda(sptt_cpd *cpd, double *lambda);
+
+/* Copy factor `mode` (normalised, dims[mode] x rank row-major float) into dst
+ * (host or device). Synchronises. */
+sptt_status sptt_cpd_factor(sptt_cpd *cpd, int32_t mode, float *dst);
+
+/* Copy the FP64 Gram of factor `mode` (rank x rank) into dst (host or
+ * device). Synchronises. */
+sptt_status sptt_cpd_gram(sptt_cpd *cpd, int32_t mode, double *dst);
+
+/*
+ * Solve branches taken since sptt_cpd_init: *n_pinv = mode updates that used
+ * the pseudo-inverse (V not positive definite), *n_total = all mode updates.
+ * Synchronises.
+ */
+sptt_status sptt_cpd_solve_branch(sptt_cpd *cpd, int64_t *n_pinv, int64_t *n_total);
+
+/*
+ * Per-routine device time in milliseconds since sptt_cpd_init, in the
+ * routine categories of the paper's Table III (requires opts.profile = 1):
+ *   ms[0] MTTKRP, ms[1] Inverse (Hadamard + Cholesky/pinv), ms[2] row solve
+ *   + Gram ("Mat A^T A"), ms[3] Mat norm, ms[4] CPD fit.
+ * counts (may be NULL) receives the number of timed launches of each.
+ * Synchronises.
+ */
+#define SPTT_NUM_TIMERS 5
+sptt_status sptt_cpd_timers(sptt_cpd *cpd, double *ms, int64_t *counts);
+
+/*
+ * One-shot CP-ALS: create, init (Philox from opts->seed), iterate up to
+ * max_iters with tol (plus the refinement sweep for BF16), copy the results
+ * out and free. factors_out: host array of nmodes pointers (host or device)
+ * to dims[m] x rank floats; lambda_out: rank doubles (host or device); fit_out
+ * and iters_out: host scalars. Any output may be NULL. Synchronous.
+ */
+sptt_status sptt_cpd_als(const sptt_coo *coo, int32_t rank, int32_t max_iters, double tol,
+                         const sptt_opts *opts, sptt_stream stream, float *const *factors_out,
+                         double *lambda_out, double *fit_out, int32_t *iters_out);
+
+/*
+ * Fault injection for tests (host side only): the countdown-th device
+ * allocation made by the library from now on fails with SPTT_ERR_OOM, as if
+ * the device were out of memory; 0 disables. Process-wide.
+ */
+void sptt_debug_fail_alloc_after(int64_t countdown);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPTT_H */

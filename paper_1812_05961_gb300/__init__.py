@@ -1,0 +1,428 @@
+"""Python binding of libsptt (sparse CP-ALS over CSF on one GB300 GPU).
+
+Argument marshalling only: every function forwards to the C ABI declared in
+``include/sptt.h`` under the same name, passing torch tensors as raw device
+pointers and torch's current CUDA stream. All compute runs in the library's
+CUDA kernels; there is no CPU fallback, and loading fails loudly when the
+compiled library is missing (run ``build()`` first).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsptt.so")
+
+SPTT_OK = 0
+SPTT_ERR_BAD_ARG = -1
+SPTT_ERR_OOM = -2
+SPTT_ERR_CUDA = -3
+SPTT_ERR_TIMEOUT = -4
+SPTT_ERR_NOT_PD = -5
+SPTT_ERR_UNSUPPORTED = -6
+SPTT_ERR_INTERNAL = -7
+SPTT_MAX_MODES = 5
+SPTT_MAX_RANK_ALS = 64
+SPTT_F32 = 0
+SPTT_BF16 = 1
+SPTT_NUM_TIMERS = 5
+TIMER_NAMES = ("mttkrp", "inverse", "solve_gram", "mat_norm", "cpd_fit")
+
+
+class SpttError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str):
+        super().__init__("%s failed: %s (%s)" % (where, _status_name(status), detail))
+        self.status = status
+
+
+class sptt_coo(ctypes.Structure):
+    _fields_ = [("nmodes", ctypes.c_int32), ("nnz", ctypes.c_int64),
+                ("dims", ctypes.POINTER(ctypes.c_int64)),
+                ("inds", ctypes.POINTER(ctypes.c_void_p)),
+                ("vals", ctypes.c_void_p), ("on_device", ctypes.c_int32)]
+
+
+class sptt_sched(ctypes.Structure):
+    _fields_ = [("chunk", ctypes.c_int32), ("block", ctypes.c_int32), ("variant", ctypes.c_int32)]
+
+
+class sptt_opts(ctypes.Structure):
+    _fields_ = [("seed", ctypes.c_uint64), ("precision", ctypes.c_int32),
+                ("refine_iters", ctypes.c_int32), ("use_graph", ctypes.c_int32),
+                ("profile", ctypes.c_int32), ("sched", ctypes.POINTER(sptt_sched))]
+
+
+_lib = None
+_P = ctypes.c_void_p
+_I32 = ctypes.c_int32
+_I64 = ctypes.c_int64
+_ST = ctypes.c_int32
+
+
+def build(**kw) -> str:
+    """Compile libsptt.so in-tree (nvcc, sm_103a)."""
+    from . import buildlib
+    return buildlib.build(**kw)
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libsptt.so is not built (%s); call paper_1812_05961_gb300.build()"
+                               % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        sig = {
+            "sptt_status_str": (ctypes.c_char_p, [_ST]),
+            "sptt_last_error": (ctypes.c_char_p, []),
+            "sptt_version": (_I32, []),
+            "sptt_csf_build": (_ST, [ctypes.POINTER(sptt_coo), _I32, _P, _P, ctypes.POINTER(_P)]),
+            "sptt_csf_free": (None, [_P]),
+            "sptt_csf_shape": (_ST, [_P, _P, _P, _P]),
+            "sptt_csf_copy_level": (_ST, [_P, _I32, _P, _P, _P, _P]),
+            "sptt_mttkrp": (_ST, [_P, _P, _I32, _I32, _P, _P, _P]),
+            "sptt_gram": (_ST, [_P, _I64, _I32, _I32, _P, _P]),
+            "sptt_cpd_create": (_ST, [ctypes.POINTER(sptt_coo), _I32, ctypes.POINTER(sptt_opts), _P,
+                                      ctypes.POINTER(_P)]),
+            "sptt_cpd_free": (None, [_P]),
+            "sptt_cpd_init": (_ST, [_P, _P]),
+            "sptt_cpd_iterate": (_ST, [_P, _I32, ctypes.c_double, _P]),
+            "sptt_cpd_refine": (_ST, [_P, _I32]),
+            "sptt_cpd_fit": (_ST, [_P, _P, _P]),
+            "sptt_cpd_fit_history": (_ST, [_P, _P, _I32, _P]),
+            "sptt_cpd_lambda": (_ST, [_P, _P]),
+            "sptt_cpd_factor": (_ST, [_P, _I32, _P]),
+            "sptt_cpd_gram": (_ST, [_P, _I32, _P]),
+            "sptt_cpd_solve_branch": (_ST, [_P, _P, _P]),
+            "sptt_cpd_timers": (_ST, [_P, _P, _P]),
+            "sptt_cpd_als": (_ST, [ctypes.POINTER(sptt_coo), _I32, _I32, ctypes.c_double,
+                                   ctypes.POINTER(sptt_opts), _P, _P, _P, _P, _P]),
+            "sptt_debug_fail_alloc_after": (None, [_I64]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _status_name(s: int) -> str:
+    try:
+        return lib().sptt_status_str(s).decode()
+    except Exception:  # pragma: no cover - only when the library itself is absent
+        return str(s)
+
+
+def _check(status: int, where: str):
+    if status != SPTT_OK:
+        raise SpttError(status, where, lib().sptt_last_error().decode())
+
+
+def _stream(stream=None) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+def _ptr(t: Optional[torch.Tensor]) -> Optional[int]:
+    return None if t is None else t.data_ptr()
+
+
+class _Coo:
+    """Holds an sptt_coo and the arrays it points to."""
+
+    def __init__(self, dims, inds: Sequence[torch.Tensor], vals: torch.Tensor):
+        if len(inds) != len(dims):
+            raise ValueError("one index array per mode")
+        self.dims = (ctypes.c_int64 * len(dims))(*[int(d) for d in dims])
+        self.inds_t = [x.contiguous() for x in inds]
+        self.vals_t = vals.contiguous()
+        for x in self.inds_t:
+            if x.dtype != torch.int32:
+                raise TypeError("indices must be int32")
+        if self.vals_t.dtype != torch.float32:
+            raise TypeError("values must be float32")
+        on_dev = self.vals_t.is_cuda
+        if any(x.is_cuda != on_dev for x in self.inds_t):
+            raise ValueError("indices and values must all be on the host or all on the device")
+        self.ptrs = (ctypes.c_void_p * len(dims))(*[x.data_ptr() for x in self.inds_t])
+        self.c = sptt_coo(len(dims), int(self.vals_t.numel()), self.dims, self.ptrs,
+                          self.vals_t.data_ptr(), 1 if on_dev else 0)
+
+
+def _opts(seed=0, precision=SPTT_F32, refine_iters=0, use_graph=0, profile=0, sched=None):
+    o = sptt_opts(seed, precision, refine_iters, use_graph, profile, None)
+    keep = None
+    if sched is not None:
+        keep = sptt_sched(*sched) if not isinstance(sched, sptt_sched) else sched
+        o.sched = ctypes.pointer(keep)
+    return o, keep
+
+
+# ---------------------------------------------------------------------------
+# Same-name wrappers of the C ABI
+# ---------------------------------------------------------------------------
+
+def sptt_version() -> int:
+    return lib().sptt_version()
+
+
+def sptt_status_str(status: int) -> str:
+    return lib().sptt_status_str(status).decode()
+
+
+def sptt_last_error() -> str:
+    return lib().sptt_last_error().decode()
+
+
+def sptt_csf_build(dims, inds, vals, root_mode: int, level_order=None, stream=None) -> int:
+    coo = _Coo(dims, inds, vals)
+    order = None
+    if level_order is not None:
+        order = (ctypes.c_int32 * len(dims))(*level_order)
+    out = ctypes.c_void_p()
+    _check(lib().sptt_csf_build(ctypes.byref(coo.c), root_mode, order, _stream(stream),
+                                ctypes.byref(out)), "sptt_csf_build")
+    return out.value
+
+
+def sptt_csf_free(csf: int):
+    lib().sptt_csf_free(csf)
+
+
+def sptt_csf_shape(csf: int):
+    n = ctypes.c_int32()
+    order = (ctypes.c_int32 * SPTT_MAX_MODES)()
+    nfibs = (ctypes.c_int64 * SPTT_MAX_MODES)()
+    _check(lib().sptt_csf_shape(csf, ctypes.byref(n), order, nfibs), "sptt_csf_shape")
+    return n.value, list(order[:n.value]), list(nfibs[:n.value])
+
+
+def sptt_csf_copy_level(csf: int, level: int, stream=None):
+    """Returns (fptr or None, fids, vals or None) as host int32/float32 tensors."""
+    n, order, nfibs = sptt_csf_shape(csf)
+    nl = nfibs[level]
+    fptr = torch.empty(nl + 1, dtype=torch.int32) if level < n - 1 else None
+    fids = torch.empty(max(nl, 1), dtype=torch.int32)
+    vals = torch.empty(max(nl, 1), dtype=torch.float32) if level == n - 1 else None
+    _check(lib().sptt_csf_copy_level(csf, level, _ptr(fptr), _ptr(fids), _ptr(vals), _stream(stream)),
+           "sptt_csf_copy_level")
+    return fptr, fids[:nl], None if vals is None else vals[:nl]
+
+
+def sptt_mttkrp(csf: int, factors: Sequence[Optional[torch.Tensor]], out: torch.Tensor,
+                factor_dtype: int = SPTT_F32, sched=None, stream=None):
+    """out (dims[root] x ld float32, device) = MTTKRP of the CSF's root mode.
+    factors: per mode (dims[m] x ld) device tensors (float32 or bfloat16)."""
+    ld = out.shape[1]
+    arr = (ctypes.c_void_p * len(factors))(*[0 if f is None else f.data_ptr() for f in factors])
+    for f in factors:
+        if f is not None and (not f.is_contiguous() or f.shape[1] != ld):
+            raise ValueError("factors must be contiguous with ld = out.shape[1] columns")
+    s = None
+    if sched is not None:
+        s = sptt_sched(*sched) if not isinstance(sched, sptt_sched) else sched
+    _check(lib().sptt_mttkrp(csf, arr, factor_dtype, ld, out.data_ptr(),
+                             None if s is None else ctypes.byref(s), _stream(stream)), "sptt_mttkrp")
+    return out
+
+
+def sptt_gram(A: torch.Tensor, rank: int, G: Optional[torch.Tensor] = None, stream=None):
+    if G is None:
+        G = torch.empty((rank, rank), dtype=torch.float64, device=A.device)
+    _check(lib().sptt_gram(A.data_ptr(), A.shape[0], rank, A.shape[1], G.data_ptr(), _stream(stream)),
+           "sptt_gram")
+    return G
+
+
+def sptt_cpd_create(dims, inds, vals, rank: int, stream=None, **opts) -> int:
+    coo = _Coo(dims, inds, vals)
+    o, keep = _opts(**opts)
+    out = ctypes.c_void_p()
+    _check(lib().sptt_cpd_create(ctypes.byref(coo.c), rank, ctypes.byref(o), _stream(stream),
+                                 ctypes.byref(out)), "sptt_cpd_create")
+    del keep
+    return out.value
+
+
+def sptt_cpd_free(cpd: int):
+    lib().sptt_cpd_free(cpd)
+
+
+def sptt_cpd_init(cpd: int, init: Optional[Sequence[torch.Tensor]] = None):
+    arr = None
+    if init is not None:
+        init = [t.contiguous().to(torch.float32) for t in init]
+        arr = (ctypes.c_void_p * len(init))(*[t.data_ptr() for t in init])
+    _check(lib().sptt_cpd_init(cpd, arr), "sptt_cpd_init")
+
+
+def sptt_cpd_iterate(cpd: int, iters: int, tol: float = 0.0) -> int:
+    done = ctypes.c_int32()
+    _check(lib().sptt_cpd_iterate(cpd, iters, tol, ctypes.byref(done)), "sptt_cpd_iterate")
+    return done.value
+
+
+def sptt_cpd_refine(cpd: int, iters: int):
+    _check(lib().sptt_cpd_refine(cpd, iters), "sptt_cpd_refine")
+
+
+def sptt_cpd_fit(cpd: int):
+    f = ctypes.c_double()
+    it = ctypes.c_int32()
+    _check(lib().sptt_cpd_fit(cpd, ctypes.byref(f), ctypes.byref(it)), "sptt_cpd_fit")
+    return f.value, it.value
+
+
+def sptt_cpd_fit_history(cpd: int, cap: int = 4096):
+    buf = (ctypes.c_double * cap)()
+    n = ctypes.c_int32()
+    _check(lib().sptt_cpd_fit_history(cpd, buf, cap, ctypes.byref(n)), "sptt_cpd_fit_history")
+    return list(buf[:n.value])
+
+
+def sptt_cpd_lambda(cpd: int, rank: int) -> torch.Tensor:
+    t = torch.empty(rank, dtype=torch.float64)
+    _check(lib().sptt_cpd_lambda(cpd, t.data_ptr()), "sptt_cpd_lambda")
+    return t
+
+
+def sptt_cpd_factor(cpd: int, mode: int, rows: int, rank: int, device="cpu") -> torch.Tensor:
+    t = torch.empty((rows, rank), dtype=torch.float32, device=device)
+    _check(lib().sptt_cpd_factor(cpd, mode, t.data_ptr()), "sptt_cpd_factor")
+    return t
+
+
+def sptt_cpd_gram(cpd: int, mode: int, rank: int) -> torch.Tensor:
+    t = torch.empty((rank, rank), dtype=torch.float64)
+    _check(lib().sptt_cpd_gram(cpd, mode, t.data_ptr()), "sptt_cpd_gram")
+    return t
+
+
+def sptt_cpd_solve_branch(cpd: int):
+    a, b = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().sptt_cpd_solve_branch(cpd, ctypes.byref(a), ctypes.byref(b)), "sptt_cpd_solve_branch")
+    return a.value, b.value
+
+
+def sptt_cpd_timers(cpd: int):
+    ms = (ctypes.c_double * SPTT_NUM_TIMERS)()
+    cnt = (ctypes.c_int64 * SPTT_NUM_TIMERS)()
+    _check(lib().sptt_cpd_timers(cpd, ms, cnt), "sptt_cpd_timers")
+    return {n: (ms[i], cnt[i]) for i, n in enumerate(TIMER_NAMES)}
+
+
+def sptt_cpd_als(dims, inds, vals, rank: int, max_iters: int, tol: float = 0.0,
+                 factors_out: Optional[Sequence[torch.Tensor]] = None,
+                 lambda_out: Optional[torch.Tensor] = None, stream=None, **opts):
+    """One-shot CP-ALS. Inputs may be host or device tensors (host ones are
+    copied inside the call); outputs are written into the given tensors.
+    Returns (fit, iters)."""
+    coo = _Coo(dims, inds, vals)
+    o, keep = _opts(**opts)
+    fo = None
+    if factors_out is not None:
+        fo = (ctypes.c_void_p * len(dims))(*[0 if t is None else t.data_ptr() for t in factors_out])
+    fit = ctypes.c_double()
+    it = ctypes.c_int32()
+    _check(lib().sptt_cpd_als(ctypes.byref(coo.c), rank, max_iters, tol, ctypes.byref(o),
+                              _stream(stream), fo, _ptr(lambda_out), ctypes.byref(fit),
+                              ctypes.byref(it)), "sptt_cpd_als")
+    del keep
+    return fit.value, it.value
+
+
+def sptt_debug_fail_alloc_after(countdown: int):
+    lib().sptt_debug_fail_alloc_after(countdown)
+
+
+# ---------------------------------------------------------------------------
+# Owning wrappers
+# ---------------------------------------------------------------------------
+
+class Csf:
+    """A CSF tree on the device (freed with the object)."""
+
+    def __init__(self, dims, inds, vals, root_mode: int, level_order=None, stream=None):
+        self.dims = [int(d) for d in dims]
+        self.handle = sptt_csf_build(dims, inds, vals, root_mode, level_order, stream)
+        self.nmodes, self.order, self.nfibs = sptt_csf_shape(self.handle)
+        self.root = root_mode
+
+    def levels(self):
+        return [sptt_csf_copy_level(self.handle, l) for l in range(self.nmodes)]
+
+    def mttkrp(self, factors, out=None, ld=None, factor_dtype=SPTT_F32, sched=None, stream=None):
+        if out is None:
+            if ld is None:
+                ld = next(f.shape[1] for f in factors if f is not None)
+            dev = next(f.device for f in factors if f is not None)
+            out = torch.empty((self.dims[self.root], ld), dtype=torch.float32, device=dev)
+        return sptt_mttkrp(self.handle, factors, out, factor_dtype, sched, stream)
+
+    def close(self):
+        if self.handle:
+            sptt_csf_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Cpd:
+    """A CP-ALS run on the device (freed with the object)."""
+
+    def __init__(self, dims, inds, vals, rank: int, stream=None, **opts):
+        self.dims = [int(d) for d in dims]
+        self.rank = rank
+        self.handle = sptt_cpd_create(dims, inds, vals, rank, stream, **opts)
+
+    def init(self, init=None):
+        sptt_cpd_init(self.handle, init)
+        return self
+
+    def iterate(self, iters: int, tol: float = 0.0) -> int:
+        return sptt_cpd_iterate(self.handle, iters, tol)
+
+    def refine(self, iters: int = 1):
+        sptt_cpd_refine(self.handle, iters)
+
+    def fit(self):
+        return sptt_cpd_fit(self.handle)
+
+    def fit_history(self):
+        return sptt_cpd_fit_history(self.handle)
+
+    def lam(self):
+        return sptt_cpd_lambda(self.handle, self.rank)
+
+    def factor(self, mode: int, device="cpu"):
+        return sptt_cpd_factor(self.handle, mode, self.dims[mode], self.rank, device)
+
+    def gram(self, mode: int):
+        return sptt_cpd_gram(self.handle, mode, self.rank)
+
+    def solve_branch(self):
+        return sptt_cpd_solve_branch(self.handle)
+
+    def timers(self):
+        return sptt_cpd_timers(self.handle)
+
+    def close(self):
+        if self.handle:
+            sptt_cpd_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,391 @@
+// CP-ALS driver (Algorithm 1, N modes) on one GPU.
+//
+// Per iteration, for each mode n in order (Gauss-Seidel: every update sees the
+// latest factors):
+//   MTTKRP over the CSF rooted at n                       (lines 5/8/11)
+//   V = Hadamard of the other modes' Grams, W = V^dagger  (lines 4/7/10)
+//   A_un = M W, fused with Gram(A_un) and the fit's dots  (lines 5/8/11)
+//   lambda = column norms, G_n = D^-1 Gram(A_un) D^-1, normalise A (6/9/12)
+// then the fit (line 13). All of it is enqueued on the handle's stream; the
+// host reads back only when asked (tol > 0, or an accessor).
+#include <math.h>
+#include <string.h>
+
+#include <vector>
+
+#include "internal.cuh"
+
+using namespace sptt;
+
+namespace {
+constexpr int kFitHistory = 4096;
+
+struct TimerRec {
+    int cat;
+    cudaEvent_t a, b;
+};
+}  // namespace
+
+struct sptt_cpd {
+    int32_t N = 0;
+    int64_t dims[SPTT_MAX_MODES] = {0};
+    int32_t rank = 0;
+    int32_t ld = 0;
+    sptt_opts opts{};
+    sptt_sched sched{};
+    bool has_sched = false;
+    cudaStream_t st = nullptr;
+    sptt_csf *csf[SPTT_MAX_MODES] = {nullptr};
+    float *A[SPTT_MAX_MODES] = {nullptr};
+    __nv_bfloat16 *Ab[SPTT_MAX_MODES] = {nullptr};
+    double *G[SPTT_MAX_MODES] = {nullptr};
+    float *M = nullptr;
+    double *normx2 = nullptr;
+    double *fits = nullptr;  // device ring of fit values, kFitHistory entries
+    DenseWork w;
+    int64_t iters = 0;       // iterations run since init
+    // profiling
+    std::vector<TimerRec> pending;
+    std::vector<cudaEvent_t> free_events;
+    double ms[SPTT_NUM_TIMERS] = {0};
+    int64_t counts[SPTT_NUM_TIMERS] = {0};
+};
+
+namespace {
+
+cudaEvent_t take_event(sptt_cpd *c) {
+    if (!c->free_events.empty()) {
+        cudaEvent_t e = c->free_events.back();
+        c->free_events.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Records a timer interval around the enqueued work of one routine.
+struct Timed {
+    sptt_cpd *c;
+    int cat;
+    cudaEvent_t a = nullptr;
+    Timed(sptt_cpd *c_, int cat_) : c(c_), cat(cat_) {
+        if (c->opts.profile) {
+            a = take_event(c);
+            cudaEventRecord(a, c->st);
+        }
+    }
+    ~Timed() {
+        if (a) {
+            cudaEvent_t b = take_event(c);
+            cudaEventRecord(b, c->st);
+            c->pending.push_back({cat, a, b});
+        }
+    }
+};
+
+sptt_status resolve_timers(sptt_cpd *c) {
+    if (c->pending.empty()) return SPTT_OK;
+    SPTT_CUDA(cudaStreamSynchronize(c->st));
+    for (auto &r : c->pending) {
+        float ms = 0.f;
+        SPTT_CUDA(cudaEventElapsedTime(&ms, r.a, r.b));
+        c->ms[r.cat] += ms;
+        c->counts[r.cat] += 1;
+        c->free_events.push_back(r.a);
+        c->free_events.push_back(r.b);
+    }
+    c->pending.clear();
+    return SPTT_OK;
+}
+
+sptt_status run_iteration(sptt_cpd *c, bool bf16) {
+    const int N = c->N;
+    const void *fac[SPTT_MAX_MODES];
+    for (int m = 0; m < N; ++m) fac[m] = bf16 ? (const void *)c->Ab[m] : (const void *)c->A[m];
+    const sptt_sched *sched = c->has_sched ? &c->sched : nullptr;
+    for (int n = 0; n < N; ++n) {
+        {
+            Timed t(c, 0);
+            SPTT_TRY(mttkrp_launch(c->csf[n], fac, bf16 ? SPTT_BF16 : SPTT_F32, c->ld, c->M, sched, c->st));
+        }
+        {
+            Timed t(c, 1);
+            SPTT_TRY(normal_prep_launch(c->G, N, n, c->rank, &c->w, c->st));
+        }
+        {
+            Timed t(c, 2);
+            SPTT_TRY(postsolve_launch(c->M, c->A[n], c->dims[n], &c->w, c->st));
+        }
+        {
+            Timed t(c, 3);
+            SPTT_TRY(finalize_launch(c->G[n], &c->w, c->st));
+            SPTT_TRY(normalize_launch(c->A[n], c->Ab[n], c->dims[n], &c->w, c->st));
+        }
+    }
+    {
+        Timed t(c, 4);
+        SPTT_TRY(fit_launch(c->G, N, c->normx2, &c->w, c->fits + (c->iters % kFitHistory), c->st));
+    }
+    c->iters += 1;
+    return SPTT_OK;
+}
+
+sptt_status read_fit(sptt_cpd *c, int64_t it, double *out) {
+    SPTT_CUDA(cudaMemcpyAsync(out, c->fits + (it % kFitHistory), sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    SPTT_CUDA(cudaStreamSynchronize(c->st));
+    return SPTT_OK;
+}
+
+void destroy(sptt_cpd *c) {
+    if (!c) return;
+    cudaStreamSynchronize(c->st);
+    for (int m = 0; m < SPTT_MAX_MODES; ++m) {
+        if (c->csf[m]) csf_destroy(c->csf[m]);
+        if (c->A[m]) dev_free(c->A[m], c->st);
+        if (c->Ab[m]) dev_free(c->Ab[m], c->st);
+        if (c->G[m]) dev_free(c->G[m], c->st);
+    }
+    if (c->M) dev_free(c->M, c->st);
+    if (c->normx2) dev_free(c->normx2, c->st);
+    if (c->fits) dev_free(c->fits, c->st);
+    dense_work_free(&c->w, c->st);
+    for (auto &r : c->pending) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (auto e : c->free_events) cudaEventDestroy(e);
+    cudaStreamSynchronize(c->st);
+    delete c;
+}
+
+}  // namespace
+
+extern "C" sptt_status sptt_cpd_create(const sptt_coo *coo, int32_t rank, const sptt_opts *opts, sptt_stream stream,
+                                       sptt_cpd **out) {
+    clear_error();
+    if (!out) return set_error(SPTT_ERR_BAD_ARG, "out is NULL");
+    *out = nullptr;
+    SPTT_TRY(coo_validate_shape(coo));
+    if (coo->nnz == 0) return set_error(SPTT_ERR_BAD_ARG, "CP-ALS needs at least one non-zero");
+    if (rank < 1) return set_error(SPTT_ERR_BAD_ARG, "rank must be >= 1");
+    if (rank > SPTT_MAX_RANK_ALS) return set_error(SPTT_ERR_UNSUPPORTED, "rank must be <= 64");
+    sptt_opts o{};
+    if (opts) o = *opts;
+    if (o.precision != SPTT_F32 && o.precision != SPTT_BF16)
+        return set_error(SPTT_ERR_BAD_ARG, "opts.precision must be SPTT_F32 or SPTT_BF16");
+    if (o.sched) {
+        const sptt_sched *s = o.sched;
+        if (s->chunk && (s->chunk < 16 || s->chunk > 4096 || (s->chunk & (s->chunk - 1))))
+            return set_error(SPTT_ERR_BAD_ARG, "sched->chunk must be a power of two in [16, 4096]");
+        if (s->block && (s->block < 32 || s->block > 256 || s->block % 32))
+            return set_error(SPTT_ERR_BAD_ARG, "sched->block must be a multiple of 32 in [32, 256]");
+    }
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    sptt_cpd *c = new sptt_cpd();
+    struct Guard {
+        sptt_cpd *c;
+        ~Guard() { if (c) destroy(c); }
+    } guard{c};
+    c->N = coo->nmodes;
+    c->rank = rank;
+    c->ld = (rank + 7) / 8 * 8;
+    c->opts = o;
+    if (o.sched) {
+        c->sched = *o.sched;
+        c->has_sched = true;
+    }
+    c->opts.sched = nullptr;
+    c->st = st;
+    for (int m = 0; m < c->N; ++m) c->dims[m] = coo->dims[m];
+    {
+        DevCoo dc;
+        SPTT_TRY(coo_to_device(coo, st, &dc));
+        for (int m = 0; m < c->N; ++m) SPTT_TRY(csf_build_device(&dc.coo, m, nullptr, st, &c->csf[m]));
+    }
+    int64_t max_rows = 0;
+    for (int m = 0; m < c->N; ++m) {
+        const int64_t rows = c->dims[m];
+        if (rows > max_rows) max_rows = rows;
+        SPTT_TRY(dev_alloc_n(&c->A[m], (size_t)rows * c->ld, st));
+        SPTT_TRY(fill_zero_launch(c->A[m], (size_t)rows * c->ld * sizeof(float), st));
+        if (o.precision == SPTT_BF16) {
+            SPTT_TRY(dev_alloc_n(&c->Ab[m], (size_t)rows * c->ld, st));
+            SPTT_TRY(fill_zero_launch(c->Ab[m], (size_t)rows * c->ld * sizeof(__nv_bfloat16), st));
+        }
+        SPTT_TRY(dev_alloc_n(&c->G[m], (size_t)rank * rank, st));
+    }
+    SPTT_TRY(dev_alloc_n(&c->M, (size_t)max_rows * c->ld, st));
+    SPTT_TRY(dev_alloc_n(&c->normx2, 1, st));
+    SPTT_TRY(dev_alloc_n(&c->fits, kFitHistory, st));
+    SPTT_TRY(fill_zero_launch(c->fits, kFitHistory * sizeof(double), st));
+    SPTT_TRY(dense_work_alloc(&c->w, rank, c->ld, max_rows, st));
+    const sptt_csf *c0 = c->csf[0];
+    SPTT_TRY(sumsq_launch(c0->vals, c0->nfibs[c0->nmodes - 1], c->normx2, st));
+    SPTT_CUDA(cudaStreamSynchronize(st));
+    guard.c = nullptr;
+    *out = c;
+    return SPTT_OK;
+}
+
+extern "C" void sptt_cpd_free(sptt_cpd *cpd) { destroy(cpd); }
+
+extern "C" sptt_status sptt_cpd_init(sptt_cpd *c, const float *const *init) {
+    clear_error();
+    if (!c) return set_error(SPTT_ERR_BAD_ARG, "cpd is NULL");
+    cudaStream_t st = c->st;
+    for (int m = 0; m < c->N; ++m) {
+        if (init) {
+            if (!init[m]) return set_error(SPTT_ERR_BAD_ARG, "init[m] is NULL");
+            SPTT_TRY(fill_zero_launch(c->A[m], (size_t)c->dims[m] * c->ld * sizeof(float), st));
+            SPTT_CUDA(cudaMemcpy2DAsync(c->A[m], c->ld * sizeof(float), init[m], c->rank * sizeof(float),
+                                        c->rank * sizeof(float), c->dims[m], cudaMemcpyDefault, st));
+        } else {
+            SPTT_TRY(init_factor_launch(c->opts.seed, m, c->dims[m], c->rank, c->ld, c->A[m], st));
+        }
+        if (c->Ab[m]) SPTT_TRY(to_bf16_launch(c->A[m], c->Ab[m], c->dims[m] * c->ld, st));
+        SPTT_TRY(gram_launch(c->A[m], c->dims[m], c->rank, c->ld, c->G[m], c->w.partials, c->w.nblocks, st));
+    }
+    SPTT_TRY(fill_zero_launch(c->w.branch, 2 * sizeof(int32_t), st));
+    SPTT_TRY(fill_zero_launch(c->fits, kFitHistory * sizeof(double), st));
+    c->iters = 0;
+    SPTT_TRY(resolve_timers(c));
+    for (int i = 0; i < SPTT_NUM_TIMERS; ++i) {
+        c->ms[i] = 0;
+        c->counts[i] = 0;
+    }
+    return SPTT_OK;
+}
+
+static sptt_status iterate(sptt_cpd *c, int32_t iters, double tol, bool bf16, int32_t *done) {
+    if (done) *done = 0;
+    double prev = 0.0;
+    if (tol > 0.0 && c->iters > 0) SPTT_TRY(read_fit(c, c->iters - 1, &prev));
+    for (int32_t i = 0; i < iters; ++i) {
+        SPTT_TRY(run_iteration(c, bf16));
+        if (done) *done = i + 1;
+        if (tol > 0.0) {
+            double f = 0.0;
+            SPTT_TRY(read_fit(c, c->iters - 1, &f));
+            if (c->iters >= 2 && fabs(f - prev) < tol) break;
+            prev = f;
+        }
+    }
+    return SPTT_OK;
+}
+
+extern "C" sptt_status sptt_cpd_iterate(sptt_cpd *c, int32_t iters, double tol, int32_t *iters_done) {
+    clear_error();
+    if (!c) return set_error(SPTT_ERR_BAD_ARG, "cpd is NULL");
+    if (iters < 0 || !(tol >= 0.0)) return set_error(SPTT_ERR_BAD_ARG, "iters must be >= 0 and tol >= 0");
+    return iterate(c, iters, tol, c->opts.precision == SPTT_BF16, iters_done);
+}
+
+extern "C" sptt_status sptt_cpd_refine(sptt_cpd *c, int32_t iters) {
+    clear_error();
+    if (!c) return set_error(SPTT_ERR_BAD_ARG, "cpd is NULL");
+    if (iters < 0) return set_error(SPTT_ERR_BAD_ARG, "iters must be >= 0");
+    return iterate(c, iters, 0.0, false, nullptr);
+}
+
+extern "C" sptt_status sptt_cpd_fit(sptt_cpd *c, double *fit, int32_t *iters) {
+    clear_error();
+    if (!c) return set_error(SPTT_ERR_BAD_ARG, "cpd is NULL");
+    if (iters) *iters = (int32_t)c->iters;
+    if (fit) {
+        if (c->iters == 0) *fit = 0.0;
+        else SPTT_TRY(read_fit(c, c->iters - 1, fit));
+    }
+    return SPTT_OK;
+}
+
+extern "C" sptt_status sptt_cpd_fit_history(sptt_cpd *c, double *fits, int32_t cap, int32_t *count) {
+    clear_error();
+    if (!c || !fits) return set_error(SPTT_ERR_BAD_ARG, "cpd and fits must be non-NULL");
+    const int64_t avail = c->iters < kFitHistory ? c->iters : kFitHistory;
+    const int64_t n = avail < cap ? avail : cap;
+    std::vector<double> ring(kFitHistory);
+    SPTT_CUDA(cudaMemcpyAsync(ring.data(), c->fits, kFitHistory * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    SPTT_CUDA(cudaStreamSynchronize(c->st));
+    // the last n fits, oldest first
+    for (int64_t j = 0; j < n; ++j) fits[j] = ring[(c->iters - n + j) % kFitHistory];
+    if (count) *count = (int32_t)n;
+    return SPTT_OK;
+}
+
+extern "C" sptt_status sptt_cpd_lambda(sptt_cpd *c, double *lambda) {
+    clear_error();
+    if (!c || !lambda) return set_error(SPTT_ERR_BAD_ARG, "cpd and lambda must be non-NULL");
+    SPTT_CUDA(cudaMemcpyAsync(lambda, c->w.lambda, c->rank * sizeof(double), cudaMemcpyDefault, c->st));
+    SPTT_CUDA(cudaStreamSynchronize(c->st));
+    return SPTT_OK;
+}
+
+extern "C" sptt_status sptt_cpd_factor(sptt_cpd *c, int32_t mode, float *dst) {
+    clear_error();
+    if (!c || !dst) return set_error(SPTT_ERR_BAD_ARG, "cpd and dst must be non-NULL");
+    if (mode < 0 || mode >= c->N) return set_error(SPTT_ERR_BAD_ARG, "mode out of range");
+    SPTT_CUDA(cudaMemcpy2DAsync(dst, c->rank * sizeof(float), c->A[mode], c->ld * sizeof(float),
+                                c->rank * sizeof(float), c->dims[mode], cudaMemcpyDefault, c->st));
+    SPTT_CUDA(cudaStreamSynchronize(c->st));
+    return SPTT_OK;
+}
+
+extern "C" sptt_status sptt_cpd_gram(sptt_cpd *c, int32_t mode, double *dst) {
+    clear_error();
+    if (!c || !dst) return set_error(SPTT_ERR_BAD_ARG, "cpd and dst must be non-NULL");
+    if (mode < 0 || mode >= c->N) return set_error(SPTT_ERR_BAD_ARG, "mode out of range");
+    SPTT_CUDA(cudaMemcpyAsync(dst, c->G[mode], (size_t)c->rank * c->rank * sizeof(double), cudaMemcpyDefault, c->st));
+    SPTT_CUDA(cudaStreamSynchronize(c->st));
+    return SPTT_OK;
+}
+
+extern "C" sptt_status sptt_cpd_solve_branch(sptt_cpd *c, int64_t *n_pinv, int64_t *n_total) {
+    clear_error();
+    if (!c) return set_error(SPTT_ERR_BAD_ARG, "cpd is NULL");
+    int32_t b[2] = {0, 0};
+    SPTT_CUDA(cudaMemcpyAsync(b, c->w.branch, sizeof(b), cudaMemcpyDeviceToHost, c->st));
+    SPTT_CUDA(cudaStreamSynchronize(c->st));
+    if (n_pinv) *n_pinv = b[0];
+    if (n_total) *n_total = b[1];
+    return SPTT_OK;
+}
+
+extern "C" sptt_status sptt_cpd_timers(sptt_cpd *c, double *ms, int64_t *counts) {
+    clear_error();
+    if (!c) return set_error(SPTT_ERR_BAD_ARG, "cpd is NULL");
+    SPTT_TRY(resolve_timers(c));
+    for (int i = 0; i < SPTT_NUM_TIMERS; ++i) {
+        if (ms) ms[i] = c->ms[i];
+        if (counts) counts[i] = c->counts[i];
+    }
+    return SPTT_OK;
+}
+
+extern "C" sptt_status sptt_cpd_als(const sptt_coo *coo, int32_t rank, int32_t max_iters, double tol,
+                                    const sptt_opts *opts, sptt_stream stream, float *const *factors_out,
+                                    double *lambda_out, double *fit_out, int32_t *iters_out) {
+    clear_error();
+    if (max_iters < 0 || !(tol >= 0.0)) return set_error(SPTT_ERR_BAD_ARG, "max_iters must be >= 0 and tol >= 0");
+    sptt_cpd *c = nullptr;
+    SPTT_TRY(sptt_cpd_create(coo, rank, opts, stream, &c));
+    struct Guard {
+        sptt_cpd *c;
+        ~Guard() { destroy(c); }
+    } guard{c};
+    SPTT_TRY(sptt_cpd_init(c, nullptr));
+    int32_t done = 0;
+    SPTT_TRY(sptt_cpd_iterate(c, max_iters, tol, &done));
+    if (c->opts.precision == SPTT_BF16) {
+        const int32_t refine = c->opts.refine_iters > 0 ? c->opts.refine_iters : 1;
+        SPTT_TRY(sptt_cpd_refine(c, refine));
+    }
+    if (factors_out)
+        for (int m = 0; m < c->N; ++m)
+            if (factors_out[m]) SPTT_TRY(sptt_cpd_factor(c, m, factors_out[m]));
+    if (lambda_out) SPTT_TRY(sptt_cpd_lambda(c, lambda_out));
+    int32_t it = 0;
+    SPTT_TRY(sptt_cpd_fit(c, fit_out, &it));
+    if (iters_out) *iters_out = it;
+    return SPTT_OK;
+}

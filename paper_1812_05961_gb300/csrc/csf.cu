@@ -1,0 +1,518 @@
+// COO -> CSF on the device (Section III; the non-zero sort of Section V-C).
+//
+// 1. validate every index against its mode length;
+// 2. stable LSD radix sort of the non-zero positions by packed coordinate
+//    keys in level order (levels grouped into 64-bit words from the leaf up;
+//    each word sorted stably after the less significant ones);
+// 3. gather coordinates and values in sorted order;
+// 4. coalesce duplicate coordinates (FP64 sum in input order, one rounding);
+// 5. per level l < N-1: "prefix changed" flags -> exclusive scan -> fiber ids,
+//    then fids/fptr written at each fiber's first non-zero.
+// All integer work is exact, so the result is bit-identical to a plain
+// sequential construction.
+#include <string.h>
+
+#include <vector>
+
+#include "internal.cuh"
+
+namespace sptt {
+namespace {
+
+constexpr int kThreads = 256;
+
+inline unsigned grid_for(int64_t n, int threads = kThreads) {
+    int64_t g = (n + threads - 1) / threads;
+    return (unsigned)(g < 1 ? 1 : g);
+}
+
+inline int bits_for(int64_t dim) {  // bits to hold 0..dim-1
+    int b = 0;
+    while (b < 63 && (int64_t(1) << b) < dim) ++b;
+    return b;
+}
+
+struct IdxPtrs {
+    const int32_t *p[kMaxModes];
+};
+
+__global__ void check_indices_kernel(IdxPtrs inds, int nmodes, int64_t nnz, const int64_t *dims_dev_unused,
+                                     int64_t d0, int64_t d1, int64_t d2, int64_t d3, int64_t d4,
+                                     int32_t *err) {
+    const int64_t dims[kMaxModes] = {d0, d1, d2, d3, d4};
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nnz;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        for (int m = 0; m < nmodes; ++m) {
+            int32_t x = inds.p[m][k];
+            if (x < 0 || (int64_t)x >= dims[m]) atomicOr(err, 1);
+        }
+    }
+}
+
+// key[k] = sum over the group's levels of idx << shift, taken at src(k).
+struct KeyGroup {
+    int nlev;
+    const int32_t *idx[kMaxModes];
+    int shift[kMaxModes];
+};
+
+__global__ void build_keys_kernel(KeyGroup g, const uint32_t *__restrict__ perm, int64_t n,
+                                  uint64_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t src = perm ? perm[k] : (uint32_t)k;
+        uint64_t key = 0;
+        for (int j = 0; j < g.nlev; ++j) key |= (uint64_t)(uint32_t)g.idx[j][src] << g.shift[j];
+        keys[k] = key;
+        vals[k] = src;
+    }
+}
+
+struct OutPtrs {
+    int32_t *p[kMaxModes];
+};
+
+__global__ void gather_sorted_kernel(IdxPtrs lev_inds, int nlev, const float *__restrict__ vals,
+                                     const uint32_t *__restrict__ perm, int64_t n, OutPtrs out,
+                                     float *__restrict__ out_vals) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t src = perm[k];
+        for (int l = 0; l < nlev; ++l) out.p[l][k] = lev_inds.p[l][src];
+        out_vals[k] = vals[src];
+    }
+}
+
+// flag[k] = 1 if the coordinate prefix of levels 0..upto differs from k-1.
+__global__ void prefix_flags_kernel(IdxPtrs s, int upto, int64_t n, int32_t *__restrict__ flags) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        int f = (k == 0);
+        if (!f)
+            for (int l = 0; l <= upto; ++l)
+                if (s.p[l][k] != s.p[l][k - 1]) { f = 1; break; }
+        flags[k] = f;
+    }
+}
+
+// For each distinct coordinate u starting at k: starts[u] = k.
+__global__ void run_starts_kernel(const int32_t *__restrict__ uid, int64_t n,
+                                  int32_t *__restrict__ starts) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        if (uid[k + 1] != uid[k]) starts[uid[k]] = (int32_t)k;
+    }
+}
+
+// Coalesce: coordinates of each run's first entry; value = FP64 sum of the
+// run in order (input order, since the sort is stable), rounded once.
+__global__ void coalesce_kernel(IdxPtrs s, int nlev, const float *__restrict__ sv,
+                                const int32_t *__restrict__ starts, int64_t u_count, int64_t n,
+                                OutPtrs out, float *__restrict__ out_vals) {
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < u_count;
+         u += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = starts[u];
+        const int64_t e = (u + 1 < u_count) ? starts[u + 1] : n;
+        double sum = 0.0;
+        for (int64_t k = b; k < e; ++k) sum += (double)sv[k];
+        out_vals[u] = (float)sum;
+        for (int l = 0; l < nlev; ++l) out.p[l][u] = s.p[l][b];
+    }
+}
+
+// Write fids/fptr of every level l < N-1 at each fiber's first non-zero.
+struct LevelScan {
+    const int32_t *fidx[kMaxModes];  // exclusive scans (length n+1) for l = 0..N-2
+    int32_t *fids[kMaxModes];
+    int32_t *fptr[kMaxModes];
+};
+
+__global__ void fill_levels_kernel(IdxPtrs s, LevelScan ls, int nlev, int64_t n) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        for (int l = 0; l < nlev - 1; ++l) {
+            const int32_t f = ls.fidx[l][k];
+            if (ls.fidx[l][k + 1] != f) {
+                ls.fids[l][f] = s.p[l][k];
+                ls.fptr[l][f] = (l == nlev - 2) ? (int32_t)k : ls.fidx[l + 1][k];
+            }
+        }
+        if (k == 0)
+            for (int l = 0; l < nlev - 1; ++l) {
+                const int32_t nl = ls.fidx[l][n];
+                ls.fptr[l][nl] = (l == nlev - 2) ? (int32_t)n : ls.fidx[l + 1][n];
+            }
+    }
+}
+
+// part[c*(N-1) + l] = level-l fiber holding leaf c*chunk (binary search up the tree).
+struct FptrPtrs {
+    const int32_t *p[kMaxModes];
+    int64_t n[kMaxModes];
+};
+
+__global__ void partition_kernel(FptrPtrs fp, int nlev, int64_t nnz, int32_t chunk, int64_t nchunks,
+                                 int32_t *__restrict__ part) {
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nchunks;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        int64_t child = c * (int64_t)chunk;
+        for (int l = nlev - 2; l >= 0; --l) {
+            // largest f in [0, n_l) with fptr[l][f] <= child
+            int64_t lo = 0, hi = fp.n[l];  // invariant: fptr[lo] <= child < fptr[hi]
+            while (hi - lo > 1) {
+                const int64_t mid = (lo + hi) >> 1;
+                if (fp.p[l][mid] <= child) lo = mid;
+                else hi = mid;
+            }
+            part[c * (nlev - 1) + l] = (int32_t)lo;
+            child = lo;
+        }
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// COO helpers
+// ---------------------------------------------------------------------------
+sptt_status coo_validate_shape(const sptt_coo *coo) {
+    if (!coo) return set_error(SPTT_ERR_BAD_ARG, "coo is NULL");
+    if (coo->nmodes < 2 || coo->nmodes > kMaxModes)
+        return set_error(SPTT_ERR_BAD_ARG, "nmodes must be in [2, " + std::to_string(kMaxModes) + "]");
+    if (coo->nnz < 0 || coo->nnz >= (int64_t(1) << 31))
+        return set_error(SPTT_ERR_BAD_ARG, "nnz must be in [0, 2^31)");
+    if (!coo->dims || !coo->inds) return set_error(SPTT_ERR_BAD_ARG, "dims/inds is NULL");
+    for (int m = 0; m < coo->nmodes; ++m) {
+        if (coo->dims[m] < 1 || coo->dims[m] > INT32_MAX)
+            return set_error(SPTT_ERR_BAD_ARG, "dims[" + std::to_string(m) + "] must be in [1, 2^31-1]");
+        if (coo->nnz > 0 && !coo->inds[m])
+            return set_error(SPTT_ERR_BAD_ARG, "inds[" + std::to_string(m) + "] is NULL");
+    }
+    if (coo->nnz > 0 && !coo->vals) return set_error(SPTT_ERR_BAD_ARG, "vals is NULL");
+    return SPTT_OK;
+}
+
+DevCoo::~DevCoo() {
+    for (int m = 0; m < kMaxModes; ++m)
+        if (inds_store[m]) dev_free(inds_store[m], st);
+    if (vals_store) dev_free(vals_store, st);
+}
+
+sptt_status coo_to_device(const sptt_coo *coo, cudaStream_t st, DevCoo *out) {
+    SPTT_TRY(coo_validate_shape(coo));
+    out->st = st;
+    out->coo = *coo;
+    for (int m = 0; m < coo->nmodes; ++m) out->dims[m] = coo->dims[m];
+    out->coo.dims = out->dims;
+    if (coo->on_device) {
+        for (int m = 0; m < coo->nmodes; ++m) out->inds_ptrs[m] = coo->inds[m];
+        out->coo.inds = out->inds_ptrs;
+        return SPTT_OK;
+    }
+    const int64_t n = coo->nnz;
+    for (int m = 0; m < coo->nmodes; ++m) {
+        SPTT_TRY(dev_alloc_n(&out->inds_store[m], (size_t)n, st));
+        if (n) SPTT_CUDA(cudaMemcpyAsync(out->inds_store[m], coo->inds[m], n * sizeof(int32_t),
+                                         cudaMemcpyDefault, st));
+        out->inds_ptrs[m] = out->inds_store[m];
+    }
+    SPTT_TRY(dev_alloc_n(&out->vals_store, (size_t)n, st));
+    if (n) SPTT_CUDA(cudaMemcpyAsync(out->vals_store, coo->vals, n * sizeof(float), cudaMemcpyDefault, st));
+    out->coo.inds = out->inds_ptrs;
+    out->coo.vals = out->vals_store;
+    out->coo.on_device = 1;
+    return SPTT_OK;
+}
+
+void csf_destroy(sptt_csf *c) {
+    if (!c) return;
+    cudaDeviceSynchronize();  // no pending work may still read the arrays
+    for (int l = 0; l < kMaxModes; ++l) {
+        if (c->fptr[l]) cudaFree(c->fptr[l]);
+        if (c->fids[l]) cudaFree(c->fids[l]);
+    }
+    if (c->vals) cudaFree(c->vals);
+    if (c->part) cudaFree(c->part);
+    delete c;
+}
+
+sptt_status csf_ensure_partition(sptt_csf *c, int32_t chunk, cudaStream_t st) {
+    if (c->part && c->part_chunk == chunk) return SPTT_OK;
+    const int N = c->nmodes;
+    const int64_t nnz = c->nfibs[N - 1];
+    const int64_t nchunks = (nnz + chunk - 1) / chunk;
+    if (c->part) {
+        SPTT_CUDA(cudaStreamSynchronize(st));
+        cudaFree(c->part);
+        c->part = nullptr;
+    }
+    SPTT_CUDA(cudaMalloc(&c->part, (size_t)(nchunks * (N - 1) + 1) * sizeof(int32_t)));
+    c->part_chunk = chunk;
+    c->part_nchunks = nchunks;
+    if (nchunks == 0) return SPTT_OK;
+    FptrPtrs fp{};
+    for (int l = 0; l < N - 1; ++l) {
+        fp.p[l] = c->fptr[l];
+        fp.n[l] = c->nfibs[l];
+    }
+    partition_kernel<<<grid_for(nchunks), kThreads, 0, st>>>(fp, N, nnz, chunk, nchunks, c->part);
+    SPTT_CHECK_LAUNCH("partition_kernel");
+    return SPTT_OK;
+}
+
+sptt_status csf_build_device(const sptt_coo *coo, int32_t root, const int32_t *order_in,
+                             cudaStream_t st, sptt_csf **out) {
+    const int N = coo->nmodes;
+    const int64_t n = coo->nnz;
+    int32_t order[kMaxModes];
+    if (order_in) {
+        bool seen[kMaxModes] = {false};
+        for (int l = 0; l < N; ++l) {
+            if (order_in[l] < 0 || order_in[l] >= N || seen[order_in[l]])
+                return set_error(SPTT_ERR_BAD_ARG, "level_order must be a permutation of the modes");
+            seen[order_in[l]] = true;
+            order[l] = order_in[l];
+        }
+        if (order[0] != root) return set_error(SPTT_ERR_BAD_ARG, "level_order[0] must be root_mode");
+    } else {
+        order[0] = root;
+        int k = 1;
+        for (int m = 0; m < N; ++m)
+            if (m != root) order[k++] = m;
+        // ascending length, ties by mode id (insertion sort keeps it stable)
+        for (int a = 2; a < N; ++a)
+            for (int b = a; b > 1 && coo->dims[order[b]] < coo->dims[order[b - 1]]; --b) {
+                int32_t t = order[b];
+                order[b] = order[b - 1];
+                order[b - 1] = t;
+            }
+    }
+
+    sptt_csf *c = new sptt_csf();
+    c->nmodes = N;
+    c->root = root;
+    for (int m = 0; m < N; ++m) c->dims[m] = coo->dims[m];
+    for (int l = 0; l < N; ++l) c->order[l] = order[l];
+    struct Guard {
+        sptt_csf *c;
+        ~Guard() { if (c) csf_destroy(c); }
+    } guard{c};
+
+    // 1. validate indices
+    if (n > 0) {
+        DevBuf err;
+        SPTT_TRY(err.alloc<int32_t>(1, st));
+        SPTT_TRY(fill_zero_launch(err.p, sizeof(int32_t), st));
+        IdxPtrs ip{};
+        for (int m = 0; m < N; ++m) ip.p[m] = coo->inds[m];
+        int64_t d[kMaxModes] = {1, 1, 1, 1, 1};
+        for (int m = 0; m < N; ++m) d[m] = coo->dims[m];
+        check_indices_kernel<<<grid_for(n), kThreads, 0, st>>>(ip, N, n, nullptr, d[0], d[1], d[2], d[3],
+                                                               d[4], err.as<int32_t>());
+        SPTT_CHECK_LAUNCH("check_indices_kernel");
+        int32_t herr = 0;
+        SPTT_CUDA(cudaMemcpyAsync(&herr, err.p, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        SPTT_CUDA(cudaStreamSynchronize(st));
+        if (herr) return set_error(SPTT_ERR_BAD_ARG, "an index is outside [0, dim) of its mode");
+    }
+
+    // 2. sort positions by level-ordered keys, least significant word first
+    const int32_t *lev_src[kMaxModes];
+    for (int l = 0; l < N; ++l) lev_src[l] = coo->inds[order[l]];
+    DevBuf kA, kB, vA, vB;
+    uint32_t *perm = nullptr;
+    if (n > 0) {
+        SPTT_TRY(kA.alloc<uint64_t>(n, st));
+        SPTT_TRY(kB.alloc<uint64_t>(n, st));
+        SPTT_TRY(vA.alloc<uint32_t>(n, st));
+        SPTT_TRY(vB.alloc<uint32_t>(n, st));
+        uint64_t *keys = kA.as<uint64_t>(), *keys_alt = kB.as<uint64_t>();
+        uint32_t *vals = vA.as<uint32_t>(), *vals_alt = vB.as<uint32_t>();
+        int l = N - 1;
+        bool first = true;
+        while (l >= 0) {
+            KeyGroup g{};
+            int bits = 0;
+            // take levels l, l-1, ... while they fit in 64 bits (at least one)
+            int lo_level = l;
+            while (lo_level >= 0 && (bits + bits_for(c->dims[order[lo_level]]) <= 64 || lo_level == l)) {
+                bits += bits_for(c->dims[order[lo_level]]);
+                --lo_level;
+            }
+            int shift = 0;
+            for (int j = l; j > lo_level; --j) {  // leaf-most level in the low bits
+                const int b = bits_for(c->dims[order[j]]);
+                if (b == 0) continue;  // a length-1 mode contributes no key bits
+                g.idx[g.nlev] = lev_src[j];
+                g.shift[g.nlev] = shift;
+                shift += b;
+                ++g.nlev;
+            }
+            build_keys_kernel<<<grid_for(n), kThreads, 0, st>>>(g, first ? nullptr : vals, n, keys_alt,
+                                                                vals_alt);
+            SPTT_CHECK_LAUNCH("build_keys_kernel");
+            {
+                uint64_t *t = keys; keys = keys_alt; keys_alt = t;
+                uint32_t *tv = vals; vals = vals_alt; vals_alt = tv;
+            }
+            SPTT_TRY(radix_sort_pairs(keys, vals, keys_alt, vals_alt, n, bits, st));
+            first = false;
+            l = lo_level;
+        }
+        perm = vals;
+    }
+
+    // 3. gather sorted coordinates (level order) and values
+    std::vector<DevBuf> s_store(N);
+    DevBuf sv_store;
+    IdxPtrs s{};
+    OutPtrs so{};
+    if (n > 0) {
+        for (int l = 0; l < N; ++l) {
+            SPTT_TRY(s_store[l].alloc<int32_t>(n, st));
+            so.p[l] = s_store[l].as<int32_t>();
+            s.p[l] = so.p[l];
+        }
+        SPTT_TRY(sv_store.alloc<float>(n, st));
+        IdxPtrs lp{};
+        for (int l = 0; l < N; ++l) lp.p[l] = lev_src[l];
+        gather_sorted_kernel<<<grid_for(n), kThreads, 0, st>>>(lp, N, coo->vals, perm, n, so,
+                                                               sv_store.as<float>());
+        SPTT_CHECK_LAUNCH("gather_sorted_kernel");
+    }
+    kA.reset();
+    kB.reset();
+    vA.reset();
+    vB.reset();
+
+    // 4. coalesce duplicates
+    int64_t u = n;
+    DevBuf flags, scan;
+    float *sv = sv_store.as<float>();
+    std::vector<DevBuf> c_store(N);
+    DevBuf cv_store;
+    if (n > 0) {
+        SPTT_TRY(flags.alloc<int32_t>(n, st));
+        SPTT_TRY(scan.alloc<int32_t>(n + 1, st));
+        prefix_flags_kernel<<<grid_for(n), kThreads, 0, st>>>(s, N - 1, n, flags.as<int32_t>());
+        SPTT_CHECK_LAUNCH("prefix_flags_kernel");
+        SPTT_TRY(scan_exclusive_i32(flags.as<int32_t>(), scan.as<int32_t>(), n, true, st));
+        int32_t hu = 0;
+        SPTT_CUDA(cudaMemcpyAsync(&hu, scan.as<int32_t>() + n, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        SPTT_CUDA(cudaStreamSynchronize(st));
+        u = hu;
+        if (u < n) {
+            DevBuf starts;
+            SPTT_TRY(starts.alloc<int32_t>(u + 1, st));
+            run_starts_kernel<<<grid_for(n), kThreads, 0, st>>>(scan.as<int32_t>(), n, starts.as<int32_t>());
+            SPTT_CHECK_LAUNCH("run_starts_kernel");
+            OutPtrs co{};
+            for (int l = 0; l < N; ++l) {
+                SPTT_TRY(c_store[l].alloc<int32_t>(u, st));
+                co.p[l] = c_store[l].as<int32_t>();
+            }
+            SPTT_TRY(cv_store.alloc<float>(u, st));
+            coalesce_kernel<<<grid_for(u), kThreads, 0, st>>>(s, N, sv, starts.as<int32_t>(), u, n, co,
+                                                             cv_store.as<float>());
+            SPTT_CHECK_LAUNCH("coalesce_kernel");
+            for (int l = 0; l < N; ++l) s.p[l] = co.p[l];
+            sv = cv_store.as<float>();
+        }
+    }
+
+    // 5. fiber levels
+    c->nfibs[N - 1] = u;
+    std::vector<DevBuf> fidx(N);
+    if (u > 0) {
+        for (int l = 0; l < N - 1; ++l) {
+            SPTT_TRY(fidx[l].alloc<int32_t>(u + 1, st));
+            prefix_flags_kernel<<<grid_for(u), kThreads, 0, st>>>(s, l, u, flags.as<int32_t>());
+            SPTT_CHECK_LAUNCH("prefix_flags_kernel");
+            SPTT_TRY(scan_exclusive_i32(flags.as<int32_t>(), fidx[l].as<int32_t>(), u, true, st));
+        }
+        std::vector<int32_t> tot(N, 0);
+        for (int l = 0; l < N - 1; ++l)
+            SPTT_CUDA(cudaMemcpyAsync(&tot[l], fidx[l].as<int32_t>() + u, sizeof(int32_t),
+                                      cudaMemcpyDeviceToHost, st));
+        SPTT_CUDA(cudaStreamSynchronize(st));
+        for (int l = 0; l < N - 1; ++l) c->nfibs[l] = tot[l];
+    }
+    for (int l = 0; l < N - 1; ++l) {
+        SPTT_CUDA(cudaMalloc(&c->fptr[l], (size_t)(c->nfibs[l] + 1 + 64) * sizeof(int32_t)));
+        SPTT_CUDA(cudaMalloc(&c->fids[l], (size_t)(c->nfibs[l] + 64) * sizeof(int32_t)));
+    }
+    SPTT_CUDA(cudaMalloc(&c->fids[N - 1], (size_t)(u + 64) * sizeof(int32_t)));
+    SPTT_CUDA(cudaMalloc(&c->vals, (size_t)(u + 64) * sizeof(float)));
+    if (u > 0) {
+        LevelScan ls{};
+        for (int l = 0; l < N - 1; ++l) {
+            ls.fidx[l] = fidx[l].as<int32_t>();
+            ls.fids[l] = c->fids[l];
+            ls.fptr[l] = c->fptr[l];
+        }
+        fill_levels_kernel<<<grid_for(u), kThreads, 0, st>>>(s, ls, N, u);
+        SPTT_CHECK_LAUNCH("fill_levels_kernel");
+        SPTT_CUDA(cudaMemcpyAsync(c->fids[N - 1], s.p[N - 1], u * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+        SPTT_CUDA(cudaMemcpyAsync(c->vals, sv, u * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    } else {
+        for (int l = 0; l < N - 1; ++l) SPTT_TRY(fill_zero_launch(c->fptr[l], sizeof(int32_t), st));
+    }
+    SPTT_CUDA(cudaStreamSynchronize(st));
+    guard.c = nullptr;
+    *out = c;
+    return SPTT_OK;
+}
+
+}  // namespace sptt
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+using namespace sptt;
+
+extern "C" sptt_status sptt_csf_build(const sptt_coo *coo, int32_t root_mode, const int32_t *level_order,
+                                      sptt_stream stream, sptt_csf **out) {
+    clear_error();
+    if (!out) return set_error(SPTT_ERR_BAD_ARG, "out is NULL");
+    *out = nullptr;
+    SPTT_TRY(coo_validate_shape(coo));
+    if (root_mode < 0 || root_mode >= coo->nmodes) return set_error(SPTT_ERR_BAD_ARG, "root_mode out of range");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    DevCoo dc;
+    SPTT_TRY(coo_to_device(coo, st, &dc));
+    return csf_build_device(&dc.coo, root_mode, level_order, st, out);
+}
+
+extern "C" void sptt_csf_free(sptt_csf *csf) { csf_destroy(csf); }
+
+extern "C" sptt_status sptt_csf_shape(const sptt_csf *csf, int32_t *nmodes, int32_t *order, int64_t *nfibs) {
+    clear_error();
+    if (!csf) return set_error(SPTT_ERR_BAD_ARG, "csf is NULL");
+    if (nmodes) *nmodes = csf->nmodes;
+    for (int l = 0; l < csf->nmodes; ++l) {
+        if (order) order[l] = csf->order[l];
+        if (nfibs) nfibs[l] = csf->nfibs[l];
+    }
+    return SPTT_OK;
+}
+
+extern "C" sptt_status sptt_csf_copy_level(const sptt_csf *csf, int32_t level, int32_t *fptr, int32_t *fids,
+                                           float *vals, sptt_stream stream) {
+    clear_error();
+    if (!csf) return set_error(SPTT_ERR_BAD_ARG, "csf is NULL");
+    const int N = csf->nmodes;
+    if (level < 0 || level >= N) return set_error(SPTT_ERR_BAD_ARG, "level out of range");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const int64_t nl = csf->nfibs[level];
+    if (fptr) {
+        if (level == N - 1) return set_error(SPTT_ERR_BAD_ARG, "the leaf level has no fptr");
+        SPTT_CUDA(cudaMemcpyAsync(fptr, csf->fptr[level], (nl + 1) * sizeof(int32_t), cudaMemcpyDefault, st));
+    }
+    if (fids && nl) SPTT_CUDA(cudaMemcpyAsync(fids, csf->fids[level], nl * sizeof(int32_t), cudaMemcpyDefault, st));
+    if (vals) {
+        if (level != N - 1) return set_error(SPTT_ERR_BAD_ARG, "vals live on the leaf level");
+        if (nl) SPTT_CUDA(cudaMemcpyAsync(vals, csf->vals, nl * sizeof(float), cudaMemcpyDefault, st));
+    }
+    SPTT_CUDA(cudaStreamSynchronize(st));
+    return SPTT_OK;
+}

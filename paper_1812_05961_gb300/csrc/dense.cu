@@ -1,0 +1,682 @@
+// Dense R x R work of CP-ALS (Algorithm 1): Grams and their Hadamard product
+// (lines 4, 7, 10), the normal-equation solve A = M V^dagger (lines 5, 8, 11;
+// V^dagger through Cholesky, Section V-A), column normalisation into lambda
+// (lines 6, 9, 12) and the fit (line 13).
+//
+// Precision: the R x R matrices (Grams, V, its factor and inverse) are FP64.
+// The row-wise work over I_n x R data runs on FP32 CUDA cores: products in
+// FP32, summed in FP32 over a tile of rows, tile sums accumulated in FP64
+// (GB300's FP64 pipe is too slow for I_n * R^2 FP64 FMAs).
+#include "internal.cuh"
+
+namespace sptt {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kGramRows = 64;   // rows per tile of the Gram kernel
+constexpr int kSolveRows = 32;  // rows per tile of the fused post-solve kernel
+
+struct GramPtrs {
+    const double *p[kMaxModes];
+};
+
+// ---------------------------------------------------------------------------
+// Gram: partials[block][a*rank+b] = sum over the block's rows of A[i,a] A[i,b]
+// ---------------------------------------------------------------------------
+template <int RP>
+__global__ void __launch_bounds__(kThreads) gram_kernel(const float *__restrict__ A, int64_t rows, int rank,
+                                                        int ld, double *__restrict__ partials, int pstride) {
+    constexpr int E = RP / 16;
+    __shared__ float T[kGramRows][RP + 1];
+    const int t = threadIdx.x, ta = t / 16, tb = t % 16;
+    double acc[E][E];
+#pragma unroll
+    for (int x = 0; x < E; ++x)
+#pragma unroll
+        for (int y = 0; y < E; ++y) acc[x][y] = 0.0;
+    for (int64_t i0 = (int64_t)blockIdx.x * kGramRows; i0 < rows; i0 += (int64_t)gridDim.x * kGramRows) {
+        for (int e = t; e < kGramRows * RP; e += kThreads) {
+            const int r = e / RP, c = e % RP;
+            const int64_t i = i0 + r;
+            T[r][c] = (i < rows && c < rank) ? A[i * ld + c] : 0.f;
+        }
+        __syncthreads();
+        float s[E][E];
+#pragma unroll
+        for (int x = 0; x < E; ++x)
+#pragma unroll
+            for (int y = 0; y < E; ++y) s[x][y] = 0.f;
+#pragma unroll 4
+        for (int r = 0; r < kGramRows; ++r) {
+            float xa[E], xb[E];
+#pragma unroll
+            for (int x = 0; x < E; ++x) {
+                xa[x] = T[r][ta * E + x];
+                xb[x] = T[r][tb * E + x];
+            }
+#pragma unroll
+            for (int x = 0; x < E; ++x)
+#pragma unroll
+                for (int y = 0; y < E; ++y) s[x][y] = fmaf(xa[x], xb[y], s[x][y]);
+        }
+#pragma unroll
+        for (int x = 0; x < E; ++x)
+#pragma unroll
+            for (int y = 0; y < E; ++y) acc[x][y] += (double)s[x][y];
+        __syncthreads();
+    }
+    double *P = partials + (int64_t)blockIdx.x * pstride;
+#pragma unroll
+    for (int x = 0; x < E; ++x)
+#pragma unroll
+        for (int y = 0; y < E; ++y) {
+            const int a = ta * E + x, b = tb * E + y;
+            if (a < rank && b < rank) P[a * rank + b] = acc[x][y];
+        }
+}
+
+// out[e] = sum_b partials[b][e] in block order (deterministic).
+__global__ void reduce_partials_kernel(const double *__restrict__ partials, int nblocks, int pstride, int nelem,
+                                       double *__restrict__ out) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nelem) return;
+    double s = 0.0;
+    for (int b = 0; b < nblocks; ++b) s += partials[(int64_t)b * pstride + e];
+    out[e] = s;
+}
+
+// ---------------------------------------------------------------------------
+// Fused post-solve: A_un = M W, plus Gram(A_un) and column dots M.A_un
+// ---------------------------------------------------------------------------
+template <int RP>
+__global__ void __launch_bounds__(kThreads) postsolve_kernel(const float *__restrict__ M, float *__restrict__ A,
+                                                             int64_t rows, int rank, int ld,
+                                                             const float *__restrict__ Wg,
+                                                             double *__restrict__ partials, int pstride) {
+    constexpr int E = RP / 16;         // Gram tile per thread side
+    constexpr int CE = RP / 16;        // solve: columns per thread
+    constexpr int RE = kSolveRows / 16;  // solve: rows per thread
+    __shared__ float W[RP][RP + 1];
+    __shared__ float Mt[kSolveRows][RP + 1];
+    __shared__ float At[kSolveRows][RP + 1];
+    const int t = threadIdx.x, tr = t / 16, tc = t % 16;
+    for (int e = t; e < RP * RP; e += kThreads) {
+        const int a = e / RP, b = e % RP;
+        W[a][b] = (a < rank && b < rank) ? Wg[a * rank + b] : 0.f;
+    }
+    double accG[E][E];
+#pragma unroll
+    for (int x = 0; x < E; ++x)
+#pragma unroll
+        for (int y = 0; y < E; ++y) accG[x][y] = 0.0;
+    double accD = 0.0;
+    for (int64_t i0 = (int64_t)blockIdx.x * kSolveRows; i0 < rows; i0 += (int64_t)gridDim.x * kSolveRows) {
+        for (int e = t; e < kSolveRows * RP; e += kThreads) {
+            const int r = e / RP, c = e % RP;
+            const int64_t i = i0 + r;
+            Mt[r][c] = (i < rows && c < rank) ? M[i * ld + c] : 0.f;
+        }
+        __syncthreads();
+        float o[RE][CE];
+#pragma unroll
+        for (int y = 0; y < RE; ++y)
+#pragma unroll
+            for (int x = 0; x < CE; ++x) o[y][x] = 0.f;
+#pragma unroll 4
+        for (int k = 0; k < RP; ++k) {
+            float mk[RE], wk[CE];
+#pragma unroll
+            for (int y = 0; y < RE; ++y) mk[y] = Mt[tr * RE + y][k];
+#pragma unroll
+            for (int x = 0; x < CE; ++x) wk[x] = W[k][tc * CE + x];
+#pragma unroll
+            for (int y = 0; y < RE; ++y)
+#pragma unroll
+                for (int x = 0; x < CE; ++x) o[y][x] = fmaf(mk[y], wk[x], o[y][x]);
+        }
+#pragma unroll
+        for (int y = 0; y < RE; ++y) {
+            const int r = tr * RE + y;
+            const int64_t i = i0 + r;
+#pragma unroll
+            for (int x = 0; x < CE; ++x) {
+                const int c = tc * CE + x;
+                At[r][c] = o[y][x];
+                if (i < rows && c < ld) A[i * ld + c] = o[y][x];
+            }
+        }
+        __syncthreads();
+        float s[E][E];
+#pragma unroll
+        for (int x = 0; x < E; ++x)
+#pragma unroll
+            for (int y = 0; y < E; ++y) s[x][y] = 0.f;
+        for (int r = 0; r < kSolveRows; ++r) {
+            float xa[E], xb[E];
+#pragma unroll
+            for (int x = 0; x < E; ++x) {
+                xa[x] = At[r][tr * E + x];
+                xb[x] = At[r][tc * E + x];
+            }
+#pragma unroll
+            for (int x = 0; x < E; ++x)
+#pragma unroll
+                for (int y = 0; y < E; ++y) s[x][y] = fmaf(xa[x], xb[y], s[x][y]);
+        }
+#pragma unroll
+        for (int x = 0; x < E; ++x)
+#pragma unroll
+            for (int y = 0; y < E; ++y) accG[x][y] += (double)s[x][y];
+        if (t < RP) {
+            float d = 0.f;
+            for (int r = 0; r < kSolveRows; ++r) d = fmaf(Mt[r][t], At[r][t], d);
+            accD += (double)d;
+        }
+        __syncthreads();
+    }
+    double *P = partials + (int64_t)blockIdx.x * pstride;
+#pragma unroll
+    for (int x = 0; x < E; ++x)
+#pragma unroll
+        for (int y = 0; y < E; ++y) {
+            const int a = tr * E + x, b = tc * E + y;
+            if (a < rank && b < rank) P[a * rank + b] = accG[x][y];
+        }
+    if (t < rank) P[rank * rank + t] = accD;
+}
+
+// ---------------------------------------------------------------------------
+// V = Hadamard_{m != n} G_m; W = V^dagger in FP64 (one CTA).
+// ---------------------------------------------------------------------------
+__device__ double block_sum_d(double v, double *red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    __syncthreads();
+    return s;
+}
+
+__global__ void __launch_bounds__(kThreads) normal_prep_kernel(GramPtrs g, int nmodes, int n, int rank,
+                                                               float *__restrict__ W, int32_t *__restrict__ branch) {
+    extern __shared__ double sm[];
+    const int R = rank, RR = R * R;
+    double *V = sm;            // Hadamard product (kept for the pinv branch)
+    double *S = sm + RR;       // Cholesky factor, or Jacobi working matrix
+    double *X = sm + 2 * RR;   // L^-1, or the Jacobi eigenvectors
+    double *misc = sm + 3 * RR;  // [0] threshold, [1] pd flag, [2..9] reduction scratch, [16..] rotations
+    const int t = threadIdx.x;
+    for (int e = t; e < RR; e += blockDim.x) {
+        double h = 1.0;
+        for (int m = 0; m < nmodes; ++m)
+            if (m != n) h *= g.p[m][e];
+        V[e] = h;
+        S[e] = h;
+    }
+    __syncthreads();
+    if (t == 0) {
+        double dmax = 0.0;
+        for (int i = 0; i < R; ++i) dmax = fmax(dmax, V[i * R + i]);
+        misc[0] = 1e-14 * dmax;
+        misc[1] = 1.0;
+    }
+    __syncthreads();
+    // Right-looking Cholesky of S (lower triangle), with the positive-definite test.
+    for (int j = 0; j < R; ++j) {
+        if (t == 0) {
+            const double d = S[j * R + j];
+            if (!(d > misc[0])) misc[1] = 0.0;
+            else S[j * R + j] = sqrt(d);
+        }
+        __syncthreads();
+        if (misc[1] == 0.0) break;
+        const double ljj = S[j * R + j];
+        for (int i = j + 1 + t; i < R; i += blockDim.x) S[i * R + j] /= ljj;
+        __syncthreads();
+        const int m = R - j - 1;
+        for (int e = t; e < m * m; e += blockDim.x) {
+            const int i = j + 1 + e / m, k = j + 1 + e % m;
+            if (k <= i) S[i * R + k] -= S[i * R + j] * S[k * R + j];
+        }
+        __syncthreads();
+    }
+    const bool pd = misc[1] != 0.0;
+    if (pd) {
+        // X = L^-1 (lower triangular), one column per thread
+        for (int c = t; c < R; c += blockDim.x) {
+            for (int i = 0; i < c; ++i) X[i * R + c] = 0.0;
+            for (int i = c; i < R; ++i) {
+                double s = (i == c) ? 1.0 : 0.0;
+                for (int k = c; k < i; ++k) s -= S[i * R + k] * X[k * R + c];
+                X[i * R + c] = s / S[i * R + i];
+            }
+        }
+        __syncthreads();
+        // V^-1 = L^-T L^-1
+        for (int e = t; e < RR; e += blockDim.x) {
+            const int a = e / R, b = e % R;
+            const int k0 = a > b ? a : b;
+            double s = 0.0;
+            for (int k = k0; k < R; ++k) s += X[k * R + a] * X[k * R + b];
+            W[e] = (float)s;
+        }
+    } else {
+        // Moore-Penrose pseudo-inverse by parallel cyclic Jacobi (round-robin
+        // pairing: Re/2 disjoint rotations per step, Re-1 steps per sweep).
+        for (int e = t; e < RR; e += blockDim.x) {
+            S[e] = V[e];
+            X[e] = (e / R == e % R) ? 1.0 : 0.0;
+        }
+        const int Re = (R + 1) & ~1;
+        const int half = Re / 2;
+        double *rc = misc + 16;           // cos per pair
+        double *rs = rc + half;           // sin per pair
+        int *rp = reinterpret_cast<int *>(rs + half);  // p per pair
+        int *rq = rp + half;                            // q per pair
+        __syncthreads();
+        for (int sweep = 0; sweep < 60; ++sweep) {
+            double off = 0.0, tot = 0.0;
+            for (int e = t; e < RR; e += blockDim.x) {
+                const double v = S[e] * S[e];
+                tot += v;
+                if (e / R != e % R) off += v;
+            }
+            off = block_sum_d(off, misc + 2);
+            tot = block_sum_d(tot, misc + 2);
+            if (off == 0.0 || off <= 1e-30 * tot) break;
+            for (int step = 0; step < Re - 1; ++step) {
+                for (int i = t; i < half; i += blockDim.x) {
+                    const int pa = i, pb = Re - 1 - i;
+                    const int p0 = pa == 0 ? 0 : ((pa - 1 + step) % (Re - 1)) + 1;
+                    const int q0 = pb == 0 ? 0 : ((pb - 1 + step) % (Re - 1)) + 1;
+                    const int p = p0 < q0 ? p0 : q0, q = p0 < q0 ? q0 : p0;
+                    double c = 1.0, s = 0.0;
+                    if (q < R) {
+                        const double apq = S[p * R + q];
+                        if (apq != 0.0) {
+                            const double theta = (S[q * R + q] - S[p * R + p]) / (2.0 * apq);
+                            const double tt = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                            c = 1.0 / sqrt(tt * tt + 1.0);
+                            s = tt * c;
+                        }
+                    }
+                    rc[i] = c;
+                    rs[i] = s;
+                    rp[i] = p;
+                    rq[i] = q < R ? q : -1;
+                }
+                __syncthreads();
+                for (int e = t; e < R * half; e += blockDim.x) {  // S <- S J
+                    const int i = e / R, k = e % R;
+                    if (rq[i] < 0 || rs[i] == 0.0) continue;
+                    const int p = rp[i], q = rq[i];
+                    const double c = rc[i], s = rs[i];
+                    const double skp = S[k * R + p], skq = S[k * R + q];
+                    S[k * R + p] = c * skp - s * skq;
+                    S[k * R + q] = s * skp + c * skq;
+                }
+                __syncthreads();
+                for (int e = t; e < R * half; e += blockDim.x) {  // S <- J^T S, Q <- Q J
+                    const int i = e / R, k = e % R;
+                    if (rq[i] < 0 || rs[i] == 0.0) continue;
+                    const int p = rp[i], q = rq[i];
+                    const double c = rc[i], s = rs[i];
+                    const double spk = S[p * R + k], sqk = S[q * R + k];
+                    S[p * R + k] = c * spk - s * sqk;
+                    S[q * R + k] = s * spk + c * sqk;
+                    const double qkp = X[k * R + p], qkq = X[k * R + q];
+                    X[k * R + p] = c * qkp - s * qkq;
+                    X[k * R + q] = s * qkp + c * qkq;
+                }
+                __syncthreads();
+            }
+        }
+        if (t == 0) {
+            double wmax = 0.0;
+            for (int i = 0; i < R; ++i) wmax = fmax(wmax, fabs(S[i * R + i]));
+            misc[0] = (double)R * 2.220446049250313e-16 * wmax;
+        }
+        __syncthreads();
+        const double cut = misc[0];
+        for (int e = t; e < RR; e += blockDim.x) {
+            const int a = e / R, b = e % R;
+            double s = 0.0;
+            for (int k = 0; k < R; ++k) {
+                const double w = S[k * R + k];
+                if (fabs(w) > cut) s += X[a * R + k] * X[b * R + k] / w;
+            }
+            W[e] = (float)s;
+        }
+    }
+    if (t == 0) {
+        if (!pd) branch[0] += 1;
+        branch[1] += 1;
+    }
+}
+
+// lambda_r = sqrt(Gun_rr); G_n = D^-1 Gun D^-1; inner = sum of column dots.
+__global__ void finalize_kernel(const double *__restrict__ gun, int rank, double *__restrict__ Gn,
+                                double *__restrict__ lambda, float *__restrict__ inv_lambda,
+                                double *__restrict__ inner) {
+    __shared__ double inv[SPTT_MAX_RANK_ALS];
+    __shared__ double red[32];
+    const int t = threadIdx.x;
+    if (t < rank) {
+        const double d = gun[t * rank + t];
+        const double l = d > 0.0 ? sqrt(d) : 0.0;
+        lambda[t] = l;
+        inv[t] = l > 0.0 ? 1.0 / l : 0.0;
+        inv_lambda[t] = (float)inv[t];
+    }
+    __syncthreads();
+    for (int e = t; e < rank * rank; e += blockDim.x) {
+        const int a = e / rank, b = e % rank;
+        Gn[e] = gun[e] * inv[a] * inv[b];
+    }
+    double d = (t < rank) ? gun[rank * rank + t] : 0.0;
+    d = block_sum_d(d, red);
+    if (t == 0) *inner = d;
+}
+
+// Columns of A scaled by 1/lambda; padding columns zeroed; optional BF16 copy.
+__global__ void normalize_kernel(float *__restrict__ A, __nv_bfloat16 *__restrict__ Ab, int64_t rows, int ld,
+                                 int rank, const float *__restrict__ inv_lambda) {
+    const int64_t total4 = rows * ld / 4;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total4;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        float4 v = reinterpret_cast<float4 *>(A)[q];
+        const int c0 = (int)((q * 4) % ld);
+        float x[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) x[j] = (c0 + j < rank) ? x[j] * inv_lambda[c0 + j] : 0.f;
+        reinterpret_cast<float4 *>(A)[q] = make_float4(x[0], x[1], x[2], x[3]);
+        if (Ab) {
+            __nv_bfloat162 lo = __floats2bfloat162_rn(x[0], x[1]);
+            __nv_bfloat162 hi = __floats2bfloat162_rn(x[2], x[3]);
+            reinterpret_cast<__nv_bfloat162 *>(Ab)[2 * q] = lo;
+            reinterpret_cast<__nv_bfloat162 *>(Ab)[2 * q + 1] = hi;
+        }
+    }
+}
+
+// fit = 1 - sqrt(max(0, |X|^2 + lambda^T (*_m G_m) lambda - 2 inner)) / |X|
+__global__ void fit_kernel(GramPtrs g, int nmodes, int rank, const double *__restrict__ normx2,
+                           const double *__restrict__ lambda, const double *__restrict__ inner,
+                           double *__restrict__ fit) {
+    __shared__ double red[32];
+    double s = 0.0;
+    for (int e = threadIdx.x; e < rank * rank; e += blockDim.x) {
+        double h = lambda[e / rank] * lambda[e % rank];
+        for (int m = 0; m < nmodes; ++m) h *= g.p[m][e];
+        s += h;
+    }
+    s = block_sum_d(s, red);
+    if (threadIdx.x == 0) {
+        const double nx = *normx2;
+        double r2 = nx + s - 2.0 * (*inner);
+        if (r2 < 0.0) r2 = 0.0;
+        *fit = (nx == 0.0) ? (r2 == 0.0 ? 1.0 : 0.0) : 1.0 - sqrt(r2) / sqrt(nx);
+    }
+}
+
+__global__ void sumsq_partial_kernel(const float *__restrict__ v, int64_t n, double *__restrict__ part) {
+    __shared__ double red[32];
+    double s = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double x = v[i];
+        s += x * x;
+    }
+    s = block_sum_d(s, red);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+__global__ void sum_kernel(const double *__restrict__ part, int n, double *__restrict__ out) {
+    __shared__ double red[32];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += part[i];
+    s = block_sum_d(s, red);
+    if (threadIdx.x == 0) *out = s;
+}
+
+// Philox4x64-10 (Salmon et al., SC'11): 10 rounds; multipliers
+// 0xD2E7470EE14C6C93 / 0xCA5A826395121157, key bumps 0x9E3779B97F4A7C15 /
+// 0xBB67AE8584CAA73B.
+__device__ __forceinline__ void philox4x64_10(uint64_t (&c)[4], uint64_t k0, uint64_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k0 += 0x9E3779B97F4A7C15ull;
+            k1 += 0xBB67AE8584CAA73Bull;
+        }
+        const uint64_t lo0 = 0xD2E7470EE14C6C93ull * c[0], hi0 = __umul64hi(0xD2E7470EE14C6C93ull, c[0]);
+        const uint64_t lo1 = 0xCA5A826395121157ull * c[2], hi1 = __umul64hi(0xCA5A826395121157ull, c[2]);
+        const uint64_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0;
+        c[1] = lo1;
+        c[2] = n2;
+        c[3] = lo0;
+    }
+}
+
+// A[row*ld + col] = U(0,1) for e = row*rank + col, from word e%4 of
+// philox((e/4, 0, 0, 0), (seed, mode)); ((w >> 41) + 0.5) / 2^23.
+__global__ void init_factor_kernel(uint64_t seed, int mode, int64_t rows, int rank, int ld, float *__restrict__ A) {
+    const int64_t total = rows * rank;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q * 4 < total;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t c[4] = {(uint64_t)q, 0, 0, 0};
+        philox4x64_10(c, seed, (uint64_t)mode);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int64_t e = q * 4 + j;
+            if (e < total) {
+                const float m = (float)(uint32_t)(c[j] >> 41);
+                A[(e / rank) * ld + (e % rank)] = (m + 0.5f) * (1.0f / 8388608.0f);
+            }
+        }
+    }
+}
+
+__global__ void fill_zero_words_kernel(uint32_t *__restrict__ p, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = 0u;
+}
+
+__global__ void fill_zero_vec_kernel(uint4 *__restrict__ p, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = make_uint4(0u, 0u, 0u, 0u);
+}
+
+__global__ void fill_zero_bytes_kernel(unsigned char *__restrict__ p, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = 0;
+}
+
+__global__ void to_bf16_kernel(const float *__restrict__ A, __nv_bfloat16 *__restrict__ B, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        B[i] = __float2bfloat16_rn(A[i]);
+}
+
+inline unsigned grid_cap(int64_t work, int threads = kThreads) {
+    int64_t g = (work + threads - 1) / threads;
+    const int64_t cap = (int64_t)device_sm_count() * 8;
+    if (g > cap) g = cap;
+    return (unsigned)(g < 1 ? 1 : g);
+}
+
+int rank_pad(int rank) { return rank <= 16 ? 16 : (rank <= 32 ? 32 : 64); }
+
+size_t prep_smem_bytes(int rank) {
+    const int half = (rank + 2) / 2;
+    return (3 * (size_t)rank * rank + 16 + 2 * half) * sizeof(double) + 2 * half * sizeof(int) + 64;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+sptt_status fill_zero_launch(void *p, size_t bytes, cudaStream_t st) {
+    if (!bytes) return SPTT_OK;
+    const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+    if (a % 16 == 0 && bytes % 16 == 0) {
+        fill_zero_vec_kernel<<<grid_cap(bytes / 16), kThreads, 0, st>>>(static_cast<uint4 *>(p), bytes / 16);
+    } else if (a % 4 == 0 && bytes % 4 == 0) {
+        fill_zero_words_kernel<<<grid_cap(bytes / 4), kThreads, 0, st>>>(static_cast<uint32_t *>(p), bytes / 4);
+    } else {
+        fill_zero_bytes_kernel<<<grid_cap(bytes), kThreads, 0, st>>>(static_cast<unsigned char *>(p), bytes);
+    }
+    SPTT_CHECK_LAUNCH("fill_zero");
+    return SPTT_OK;
+}
+
+sptt_status to_bf16_launch(const float *A, __nv_bfloat16 *B, int64_t n, cudaStream_t st) {
+    if (n <= 0) return SPTT_OK;
+    to_bf16_kernel<<<grid_cap(n), kThreads, 0, st>>>(A, B, n);
+    SPTT_CHECK_LAUNCH("to_bf16_kernel");
+    return SPTT_OK;
+}
+
+sptt_status dense_work_alloc(DenseWork *w, int32_t rank, int32_t ld, int64_t /*max_rows*/, cudaStream_t st) {
+    w->rank = rank;
+    w->ld = ld;
+    w->nblocks = device_sm_count() * 2;
+    const int64_t pstride = (int64_t)rank * rank + rank;
+    SPTT_TRY(dev_alloc_n(&w->partials, (size_t)w->nblocks * pstride, st));
+    SPTT_TRY(dev_alloc_n(&w->gram_un, (size_t)pstride, st));
+    SPTT_TRY(dev_alloc_n(&w->W, (size_t)rank * rank, st));
+    SPTT_TRY(dev_alloc_n(&w->lambda, (size_t)rank, st));
+    SPTT_TRY(dev_alloc_n(&w->inv_lambda, (size_t)rank, st));
+    SPTT_TRY(dev_alloc_n(&w->inner, 1, st));
+    SPTT_TRY(dev_alloc_n(&w->branch, 2, st));
+    SPTT_TRY(dev_alloc_n(&w->error, 1, st));
+    SPTT_TRY(fill_zero_launch(w->branch, 2 * sizeof(int32_t), st));
+    SPTT_TRY(fill_zero_launch(w->error, sizeof(int32_t), st));
+    SPTT_TRY(fill_zero_launch(w->lambda, rank * sizeof(double), st));
+    SPTT_TRY(fill_zero_launch(w->inner, sizeof(double), st));
+    SPTT_CUDA(cudaFuncSetAttribute(normal_prep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)prep_smem_bytes(SPTT_MAX_RANK_ALS)));
+    return SPTT_OK;
+}
+
+void dense_work_free(DenseWork *w, cudaStream_t st) {
+    void *ps[] = {w->partials, w->gram_un, w->W, w->lambda, w->inv_lambda, w->inner, w->branch, w->error};
+    for (void *p : ps)
+        if (p) dev_free(p, st);
+    *w = DenseWork();
+}
+
+template <int RP>
+static void gram_dispatch(const float *A, int64_t rows, int rank, int ld, double *partials, int nblocks,
+                          int pstride, cudaStream_t st) {
+    gram_kernel<RP><<<nblocks, kThreads, 0, st>>>(A, rows, rank, ld, partials, pstride);
+}
+
+sptt_status gram_launch(const float *A, int64_t rows, int32_t rank, int32_t ld, double *G, double *partials,
+                        int32_t nblocks, cudaStream_t st) {
+    const int pstride = rank * rank + rank;
+    switch (rank_pad(rank)) {
+        case 16: gram_dispatch<16>(A, rows, rank, ld, partials, nblocks, pstride, st); break;
+        case 32: gram_dispatch<32>(A, rows, rank, ld, partials, nblocks, pstride, st); break;
+        default: gram_dispatch<64>(A, rows, rank, ld, partials, nblocks, pstride, st); break;
+    }
+    SPTT_CHECK_LAUNCH("gram_kernel");
+    const int ne = rank * rank;
+    reduce_partials_kernel<<<(ne + kThreads - 1) / kThreads, kThreads, 0, st>>>(partials, nblocks, pstride, ne, G);
+    SPTT_CHECK_LAUNCH("reduce_partials_kernel");
+    return SPTT_OK;
+}
+
+sptt_status normal_prep_launch(double *const *grams, int32_t nmodes, int32_t n, int32_t rank, DenseWork *w,
+                               cudaStream_t st) {
+    GramPtrs g{};
+    for (int m = 0; m < nmodes; ++m) g.p[m] = grams[m];
+    normal_prep_kernel<<<1, kThreads, prep_smem_bytes(rank), st>>>(g, nmodes, n, rank, w->W, w->branch);
+    SPTT_CHECK_LAUNCH("normal_prep_kernel");
+    return SPTT_OK;
+}
+
+template <int RP>
+static void postsolve_dispatch(const float *M, float *A, int64_t rows, DenseWork *w, int pstride, cudaStream_t st) {
+    postsolve_kernel<RP><<<w->nblocks, kThreads, 0, st>>>(M, A, rows, w->rank, w->ld, w->W, w->partials, pstride);
+}
+
+sptt_status postsolve_launch(const float *M, float *A, int64_t rows, DenseWork *w, cudaStream_t st) {
+    const int rank = w->rank;
+    const int pstride = rank * rank + rank;
+    switch (rank_pad(rank)) {
+        case 16: postsolve_dispatch<16>(M, A, rows, w, pstride, st); break;
+        case 32: postsolve_dispatch<32>(M, A, rows, w, pstride, st); break;
+        default: postsolve_dispatch<64>(M, A, rows, w, pstride, st); break;
+    }
+    SPTT_CHECK_LAUNCH("postsolve_kernel");
+    reduce_partials_kernel<<<(pstride + kThreads - 1) / kThreads, kThreads, 0, st>>>(w->partials, w->nblocks,
+                                                                                     pstride, pstride, w->gram_un);
+    SPTT_CHECK_LAUNCH("reduce_partials_kernel");
+    return SPTT_OK;
+}
+
+sptt_status finalize_launch(double *G_n, DenseWork *w, cudaStream_t st) {
+    finalize_kernel<<<1, kThreads, 0, st>>>(w->gram_un, w->rank, G_n, w->lambda, w->inv_lambda, w->inner);
+    SPTT_CHECK_LAUNCH("finalize_kernel");
+    return SPTT_OK;
+}
+
+sptt_status normalize_launch(float *A, __nv_bfloat16 *A_bf16, int64_t rows, DenseWork *w, cudaStream_t st) {
+    const int64_t q = rows * w->ld / 4;
+    if (q == 0) return SPTT_OK;
+    normalize_kernel<<<grid_cap(q), kThreads, 0, st>>>(A, A_bf16, rows, w->ld, w->rank, w->inv_lambda);
+    SPTT_CHECK_LAUNCH("normalize_kernel");
+    return SPTT_OK;
+}
+
+sptt_status fit_launch(double *const *grams, int32_t nmodes, const double *normx2, DenseWork *w, double *fit_out,
+                       cudaStream_t st) {
+    GramPtrs g{};
+    for (int m = 0; m < nmodes; ++m) g.p[m] = grams[m];
+    fit_kernel<<<1, kThreads, 0, st>>>(g, nmodes, w->rank, normx2, w->lambda, w->inner, fit_out);
+    SPTT_CHECK_LAUNCH("fit_kernel");
+    return SPTT_OK;
+}
+
+sptt_status sumsq_launch(const float *vals, int64_t n, double *out, cudaStream_t st) {
+    const int nb = 1024;
+    DevBuf part;
+    SPTT_TRY(part.alloc<double>(nb, st));
+    sumsq_partial_kernel<<<nb, kThreads, 0, st>>>(vals, n, part.as<double>());
+    SPTT_CHECK_LAUNCH("sumsq_partial_kernel");
+    sum_kernel<<<1, kThreads, 0, st>>>(part.as<double>(), nb, out);
+    SPTT_CHECK_LAUNCH("sum_kernel");
+    return SPTT_OK;
+}
+
+sptt_status init_factor_launch(uint64_t seed, int32_t mode, int64_t rows, int32_t rank, int32_t ld, float *A,
+                               cudaStream_t st) {
+    SPTT_TRY(fill_zero_launch(A, (size_t)rows * ld * sizeof(float), st));
+    const int64_t q = (rows * rank + 3) / 4;
+    if (q == 0) return SPTT_OK;
+    init_factor_kernel<<<grid_cap(q), kThreads, 0, st>>>(seed, mode, rows, rank, ld, A);
+    SPTT_CHECK_LAUNCH("init_factor_kernel");
+    return SPTT_OK;
+}
+
+}  // namespace sptt
+
+using namespace sptt;
+
+extern "C" sptt_status sptt_gram(const float *A, int64_t rows, int32_t rank, int32_t ld, double *G,
+                                 sptt_stream stream) {
+    clear_error();
+    if (!A || !G) return set_error(SPTT_ERR_BAD_ARG, "A and G must be non-NULL");
+    if (rows < 0) return set_error(SPTT_ERR_BAD_ARG, "rows < 0");
+    if (rank < 1 || rank > SPTT_MAX_RANK_ALS) return set_error(SPTT_ERR_UNSUPPORTED, "rank must be in [1, 64]");
+    if (ld < rank) return set_error(SPTT_ERR_BAD_ARG, "ld < rank");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const int nblocks = device_sm_count() * 2;
+    DevBuf part;
+    SPTT_TRY(part.alloc<double>((size_t)nblocks * (rank * rank + rank), st));
+    return gram_launch(A, rows, rank, ld, G, part.as<double>(), nblocks, st);
+}

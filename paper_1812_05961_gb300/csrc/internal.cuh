@@ -1,0 +1,180 @@
+// Internal declarations shared by the CUDA translation units of libsptt.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/sptt.h"
+
+namespace sptt {
+
+constexpr int kMaxModes = SPTT_MAX_MODES;
+constexpr int kNumSMs = 152;  // GB300: 2 dies x 76 SMs (queried at run time where it matters)
+
+// ---------------------------------------------------------------------------
+// Errors
+// ---------------------------------------------------------------------------
+sptt_status set_error(sptt_status s, const std::string &msg);
+sptt_status cuda_error(cudaError_t e, const char *what);
+void clear_error();
+
+#define SPTT_CUDA(call)                                        \
+    do {                                                       \
+        cudaError_t e__ = (call);                              \
+        if (e__ != cudaSuccess) return ::sptt::cuda_error(e__, #call); \
+    } while (0)
+
+#define SPTT_CHECK_LAUNCH(what)                                \
+    do {                                                       \
+        cudaError_t e__ = cudaGetLastError();                  \
+        if (e__ != cudaSuccess) return ::sptt::cuda_error(e__, what); \
+    } while (0)
+
+#define SPTT_TRY(expr)                                         \
+    do {                                                       \
+        sptt_status s__ = (expr);                              \
+        if (s__ != SPTT_OK) return s__;                        \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// Device memory (stream-ordered)
+// ---------------------------------------------------------------------------
+sptt_status dev_alloc(void **p, size_t bytes, cudaStream_t st);
+void dev_free(void *p, cudaStream_t st);
+
+template <typename T>
+sptt_status dev_alloc_n(T **p, size_t n, cudaStream_t st) {
+    // 64 elements of slack so vector loads past the logical end stay inside the allocation
+    return dev_alloc(reinterpret_cast<void **>(p), (n + 64) * sizeof(T), st);
+}
+
+// RAII holder for temporaries of one call.
+struct DevBuf {
+    void *p = nullptr;
+    cudaStream_t st = nullptr;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    ~DevBuf() { reset(); }
+    void reset() {
+        if (p) dev_free(p, st);
+        p = nullptr;
+    }
+    template <typename T>
+    sptt_status alloc(size_t n, cudaStream_t s) {
+        st = s;
+        return dev_alloc_n(reinterpret_cast<T **>(&p), n, s);
+    }
+    template <typename T>
+    T *as() const { return reinterpret_cast<T *>(p); }
+};
+
+int device_sm_count();
+
+// ---------------------------------------------------------------------------
+// Scan and radix sort (sort.cu)
+// ---------------------------------------------------------------------------
+// Exclusive prefix sum of n int32 values; out[n] (if with_total) = total.
+// Workspace is allocated internally on the stream.
+sptt_status scan_exclusive_i32(const int32_t *in, int32_t *out, int64_t n, bool with_total,
+                               cudaStream_t st);
+
+// Stable LSD radix sort of (key, value) pairs by the low `nbits` bits of key,
+// ping-ponging between (keys, vals) and (keys_alt, vals_alt); on return
+// keys/vals point at the sorted data (the pointers may have been swapped).
+sptt_status radix_sort_pairs(uint64_t *&keys, uint32_t *&vals, uint64_t *&keys_alt,
+                             uint32_t *&vals_alt, int64_t n, int nbits, cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// CSF (csf.cu)
+// ---------------------------------------------------------------------------
+}  // namespace sptt
+
+struct sptt_csf {
+    int32_t nmodes = 0;
+    int32_t root = 0;
+    int32_t order[SPTT_MAX_MODES] = {0};
+    int64_t dims[SPTT_MAX_MODES] = {0};     // by mode
+    int64_t nfibs[SPTT_MAX_MODES] = {0};    // by level; nfibs[N-1] = nnz
+    int32_t *fptr[SPTT_MAX_MODES] = {nullptr};  // levels 0..N-2
+    int32_t *fids[SPTT_MAX_MODES] = {nullptr};  // levels 0..N-1
+    float *vals = nullptr;
+    // Work partition for the MTTKRP kernels: for leaf chunk c (leaves
+    // [c*part_chunk, ...)), part[c*(N-1) + l] = the level-l fiber holding
+    // the chunk's first leaf. Rebuilt when another chunk size is requested.
+    int32_t *part = nullptr;
+    int32_t part_chunk = 0;
+    int64_t part_nchunks = 0;
+};
+
+namespace sptt {
+
+sptt_status csf_build_device(const sptt_coo *coo_dev, int32_t root, const int32_t *order,
+                             cudaStream_t st, sptt_csf **out);
+sptt_status csf_ensure_partition(sptt_csf *csf, int32_t chunk, cudaStream_t st);
+void csf_destroy(sptt_csf *c);
+
+// Copy a host COO to the device (arrays owned by the returned holder).
+struct DevCoo {
+    sptt_coo coo{};
+    int32_t *inds_store[kMaxModes] = {nullptr};
+    const int32_t *inds_ptrs[kMaxModes] = {nullptr};
+    float *vals_store = nullptr;
+    int64_t dims[kMaxModes] = {0};
+    cudaStream_t st = nullptr;
+    ~DevCoo();
+};
+sptt_status coo_validate_shape(const sptt_coo *coo);
+sptt_status coo_to_device(const sptt_coo *coo, cudaStream_t st, DevCoo *out);
+
+// ---------------------------------------------------------------------------
+// MTTKRP (mttkrp.cu)
+// ---------------------------------------------------------------------------
+sptt_status mttkrp_launch(sptt_csf *csf, const void *const *factors, int32_t dtype, int32_t ld,
+                          float *out, const sptt_sched *sched, cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// Dense kernels (dense.cu)
+// ---------------------------------------------------------------------------
+struct DenseWork {
+    int32_t rank = 0, ld = 0;
+    int32_t nblocks = 0;          // blocks of the row kernels (partials per block)
+    double *partials = nullptr;   // [nblocks][rank*rank + rank]
+    double *gram_un = nullptr;    // rank*rank (+ rank dots)
+    float *W = nullptr;           // rank*rank (FP32 copy of V^dagger)
+    double *lambda = nullptr;     // rank
+    float *inv_lambda = nullptr;  // rank (FP32, for the normalise pass)
+    double *inner = nullptr;      // 1: sum_r sum_i M[i,r] A_un[i,r] of the last mode update
+    int32_t *branch = nullptr;    // counters: [0] pinv updates, [1] total updates
+    int32_t *error = nullptr;     // device error word (timeouts)
+};
+sptt_status dense_work_alloc(DenseWork *w, int32_t rank, int32_t ld, int64_t max_rows,
+                             cudaStream_t st);
+void dense_work_free(DenseWork *w, cudaStream_t st);
+
+sptt_status gram_launch(const float *A, int64_t rows, int32_t rank, int32_t ld, double *G,
+                        double *partials, int32_t nblocks, cudaStream_t st);
+// V = Hadamard_{m != n} grams[m]; W = V^dagger (FP64 Cholesky or pinv), stored FP32.
+sptt_status normal_prep_launch(double *const *grams, int32_t nmodes, int32_t n, int32_t rank,
+                               DenseWork *w, cudaStream_t st);
+// A_un = M W, Gram(A_un) and column dots M.A_un into per-block partials, then reduced.
+sptt_status postsolve_launch(const float *M, float *A, int64_t rows, DenseWork *w,
+                             cudaStream_t st);
+// lambda = sqrt(diag G_un); G_n = D^-1 G_un D^-1; inner = sum dots.
+sptt_status finalize_launch(double *G_n, DenseWork *w, cudaStream_t st);
+// A *= 1/lambda (columns), optional BF16 shadow.
+sptt_status normalize_launch(float *A, __nv_bfloat16 *A_bf16, int64_t rows, DenseWork *w,
+                             cudaStream_t st);
+// fit = 1 - sqrt(max(0, normx2 + lambda^T (*G) lambda - 2 inner)) / sqrt(normx2)
+sptt_status fit_launch(double *const *grams, int32_t nmodes, const double *normx2, DenseWork *w,
+                       double *fit_out, cudaStream_t st);
+sptt_status sumsq_launch(const float *vals, int64_t n, double *out, cudaStream_t st);
+sptt_status init_factor_launch(uint64_t seed, int32_t mode, int64_t rows, int32_t rank,
+                               int32_t ld, float *A, cudaStream_t st);
+sptt_status fill_zero_launch(void *p, size_t bytes, cudaStream_t st);
+sptt_status to_bf16_launch(const float *A, __nv_bfloat16 *B, int64_t n, cudaStream_t st);
+
+}  // namespace sptt

@@ -1,0 +1,256 @@
+// Root-mode MTTKRP over CSF (Section III; Algorithm 1 lines 5, 8, 11).
+//
+// For the CSF rooted at mode n with level order (n, o_1, ..., o_{N-1}):
+//   M[i, :] = sum_{level-1 fibers f of slice i} A^(o_1)[j_f, :] *
+//             ( ... sum_{leaves k of the level-(N-2) fiber} v_k A^(o_{N-1})[k_idx, :])
+// i.e. the Khatri-Rao product is never formed; each fiber's partial sum is
+// multiplied by its factor row once (the CSF factorisation of the sum).
+//
+// GPU mapping (replaces the paper's thread-per-slice loops with locks or
+// privatised outputs, Section IV-A / V-D-2):
+//   * a "lane group" of G = ld / VEC lanes owns one output row segment; lane g
+//     holds columns [g*VEC, g*VEC+VEC) (VEC = 4 for FP32 factors, 8 for BF16)
+//     and gathers them with one 128-bit load per factor row;
+//   * the leaves are cut into equal chunks (the CSF's precomputed partition
+//     gives, per chunk, the fiber at every level holding its first leaf); a
+//     lane group walks its chunk in order, keeping one register accumulator
+//     per tree level, so the load is balanced whatever the slice sizes
+//     (power-law slices are split across many chunks);
+//   * output conflicts: a slice that lies entirely inside one chunk is owned
+//     by that lane group and written with a plain 128-bit store; a slice cut
+//     by a chunk boundary is combined with red.global.add.v4.f32 into a
+//     zeroed output (the GPU form of the paper's lock pool: no lock, no spin).
+#include "internal.cuh"
+
+namespace sptt {
+namespace {
+
+struct MttkrpArgs {
+    const int32_t *fptr[kMaxModes];
+    const int32_t *fids[kMaxModes];
+    const void *fac[kMaxModes];  // by level; fac[0] unused
+    const float *vals;
+    const int32_t *part;
+    int64_t nchunks;
+    int64_t nnz;
+    int32_t chunk;
+    int32_t ld;
+    int32_t G;    // lanes per row
+    int32_t gpw;  // lane groups per warp
+    float *out;
+};
+
+template <typename T>
+struct Gather;
+
+template <>
+struct Gather<float> {
+    static constexpr int VEC = 4;
+    __device__ __forceinline__ static void load(const void *base, int64_t row, int ld, int col, float (&x)[4]) {
+        const float4 v = __ldg(reinterpret_cast<const float4 *>(static_cast<const float *>(base) + row * ld + col));
+        x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
+    }
+};
+
+template <>
+struct Gather<__nv_bfloat16> {
+    static constexpr int VEC = 8;
+    __device__ __forceinline__ static void load(const void *base, int64_t row, int ld, int col, float (&x)[8]) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(static_cast<const __nv_bfloat16 *>(base) + row * ld + col));
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {  // bf16 -> f32 is exact: the bits move to the top half
+            x[2 * i] = __uint_as_float(w[i] << 16);
+            x[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u);
+        }
+    }
+};
+
+template <int VEC>
+__device__ __forceinline__ void store_row(float *dst, const float (&a)[VEC]) {
+#pragma unroll
+    for (int i = 0; i < VEC; i += 4)
+        *reinterpret_cast<float4 *>(dst + i) = make_float4(a[i], a[i + 1], a[i + 2], a[i + 3]);
+}
+
+template <int VEC>
+__device__ __forceinline__ void red_add_row(float *dst, const float (&a)[VEC]) {
+#pragma unroll
+    for (int i = 0; i < VEC; i += 4)
+        asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(dst + i), "f"(a[i]),
+                     "f"(a[i + 1]), "f"(a[i + 2]), "f"(a[i + 3])
+                     : "memory");
+}
+
+template <int NM, typename T>
+__global__ void __launch_bounds__(256) mttkrp_root_kernel(const MttkrpArgs a) {
+    using G_ = Gather<T>;
+    constexpr int VEC = G_::VEC;
+    constexpr int NL = NM - 1;  // accumulator levels 0..NM-2
+    const int lane = threadIdx.x & 31;
+    const int gi = lane / a.G;
+    const int gl = lane - gi * a.G;
+    if (gi >= a.gpw) return;  // lanes beyond the last whole group idle (no warp collectives below)
+    const int col = gl * VEC;
+    const int ld = a.ld;
+    const int64_t gwarp = (int64_t)(blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = (int64_t)(gridDim.x * blockDim.x) >> 5;
+
+    for (int64_t c = gwarp * a.gpw + gi; c < a.nchunks; c += nwarps * a.gpw) {
+        const int64_t k0 = c * (int64_t)a.chunk;
+        const int64_t k1 = (k0 + a.chunk < a.nnz) ? k0 + a.chunk : a.nnz;
+        int32_t f[NL], end[NL];
+#pragma unroll
+        for (int l = 0; l < NL; ++l) {
+            f[l] = __ldg(a.part + c * NL + l);
+            end[l] = __ldg(a.fptr[l] + f[l] + 1);
+        }
+        float acc[NL][VEC];
+#pragma unroll
+        for (int l = 0; l < NL; ++l)
+#pragma unroll
+            for (int i = 0; i < VEC; ++i) acc[l][i] = 0.f;
+        bool first_slice = true;
+
+        for (int64_t k = k0; k < k1; ++k) {
+            if (k != k0 && k == end[NL - 1]) {
+                // leaf k opens a new level-(N-2) fiber: close the finished
+                // fibers bottom-up, folding each into its parent with the
+                // fiber's factor row.
+                bool to_root = true;
+#pragma unroll
+                for (int l = NL - 1; l >= 1; --l) {
+                    float x[VEC];
+                    G_::load(a.fac[l], __ldg(a.fids[l] + f[l]), ld, col, x);
+#pragma unroll
+                    for (int i = 0; i < VEC; ++i) {
+                        acc[l - 1][i] = fmaf(x[i], acc[l][i], acc[l - 1][i]);
+                        acc[l][i] = 0.f;
+                    }
+                    ++f[l];
+                    end[l] = __ldg(a.fptr[l] + f[l] + 1);
+                    if (f[l] != end[l - 1]) {
+                        to_root = false;
+                        break;
+                    }
+                }
+                if (to_root) {  // the slice is complete
+                    float *dst = a.out + (int64_t)__ldg(a.fids[0] + f[0]) * ld + col;
+                    if (first_slice) red_add_row<VEC>(dst, acc[0]);
+                    else store_row<VEC>(dst, acc[0]);
+                    first_slice = false;
+#pragma unroll
+                    for (int i = 0; i < VEC; ++i) acc[0][i] = 0.f;
+                    ++f[0];
+                    end[0] = __ldg(a.fptr[0] + f[0] + 1);
+                }
+            }
+            const float v = __ldg(a.vals + k);
+            float x[VEC];
+            G_::load(a.fac[NM - 1], __ldg(a.fids[NM - 1] + k), ld, col, x);
+#pragma unroll
+            for (int i = 0; i < VEC; ++i) acc[NL - 1][i] = fmaf(v, x[i], acc[NL - 1][i]);
+        }
+        // chunk end: fold the open fibers (all hold leaf k1-1) and add the
+        // partial slice into the output.
+#pragma unroll
+        for (int l = NL - 1; l >= 1; --l) {
+            float x[VEC];
+            G_::load(a.fac[l], __ldg(a.fids[l] + f[l]), ld, col, x);
+#pragma unroll
+            for (int i = 0; i < VEC; ++i) acc[l - 1][i] = fmaf(x[i], acc[l][i], acc[l - 1][i]);
+        }
+        red_add_row<VEC>(a.out + (int64_t)__ldg(a.fids[0] + f[0]) * ld + col, acc[0]);
+    }
+}
+
+template <int NM, typename T>
+sptt_status launch_nm(const MttkrpArgs &a, int block, cudaStream_t st) {
+    auto kern = mttkrp_root_kernel<NM, T>;
+    int per_sm = 0;
+    SPTT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, 0));
+    if (per_sm < 1) per_sm = 1;
+    const int64_t groups_per_block = (int64_t)(block / 32) * a.gpw;
+    int64_t need = (a.nchunks + groups_per_block - 1) / groups_per_block;
+    int64_t cap = (int64_t)device_sm_count() * per_sm;
+    int64_t grid = need < cap ? need : cap;
+    if (grid < 1) grid = 1;
+    kern<<<(unsigned)grid, block, 0, st>>>(a);
+    SPTT_CHECK_LAUNCH("mttkrp_root_kernel");
+    return SPTT_OK;
+}
+
+template <typename T>
+sptt_status launch_t(int nm, const MttkrpArgs &a, int block, cudaStream_t st) {
+    switch (nm) {
+        case 2: return launch_nm<2, T>(a, block, st);
+        case 3: return launch_nm<3, T>(a, block, st);
+        case 4: return launch_nm<4, T>(a, block, st);
+        case 5: return launch_nm<5, T>(a, block, st);
+        default: return set_error(SPTT_ERR_UNSUPPORTED, "nmodes");
+    }
+}
+
+}  // namespace
+
+sptt_status mttkrp_launch(sptt_csf *csf, const void *const *factors, int32_t dtype, int32_t ld,
+                          float *out, const sptt_sched *sched, cudaStream_t st) {
+    const int N = csf->nmodes;
+    const int vec = (dtype == SPTT_BF16) ? 8 : 4;
+    const int64_t rows = csf->dims[csf->root];
+    SPTT_TRY(fill_zero_launch(out, (size_t)rows * ld * sizeof(float), st));
+    const int64_t nnz = csf->nfibs[N - 1];
+    if (nnz == 0) return SPTT_OK;
+    int32_t chunk = (sched && sched->chunk) ? sched->chunk : 64;
+    int block = (sched && sched->block) ? sched->block : 256;
+    SPTT_TRY(csf_ensure_partition(csf, chunk, st));
+    MttkrpArgs a{};
+    for (int l = 0; l < N; ++l) {
+        a.fptr[l] = csf->fptr[l];
+        a.fids[l] = csf->fids[l];
+        a.fac[l] = l ? factors[csf->order[l]] : nullptr;
+    }
+    a.vals = csf->vals;
+    a.part = csf->part;
+    a.nchunks = csf->part_nchunks;
+    a.nnz = nnz;
+    a.chunk = chunk;
+    a.ld = ld;
+    a.G = ld / vec;
+    a.gpw = 32 / a.G;
+    a.out = out;
+    if (dtype == SPTT_BF16) return launch_t<__nv_bfloat16>(N, a, block, st);
+    return launch_t<float>(N, a, block, st);
+}
+
+}  // namespace sptt
+
+using namespace sptt;
+
+extern "C" sptt_status sptt_mttkrp(const sptt_csf *csf, const void *const *factors, int32_t factor_dtype,
+                                   int32_t ld, float *out, const sptt_sched *sched, sptt_stream stream) {
+    clear_error();
+    if (!csf || !factors || !out) return set_error(SPTT_ERR_BAD_ARG, "csf, factors and out must be non-NULL");
+    if (factor_dtype != SPTT_F32 && factor_dtype != SPTT_BF16)
+        return set_error(SPTT_ERR_BAD_ARG, "factor_dtype must be SPTT_F32 or SPTT_BF16");
+    const int vec = factor_dtype == SPTT_BF16 ? 8 : 4;
+    const int max_ld = 32 * vec;
+    if (ld < vec || ld > max_ld || ld % vec)
+        return set_error(SPTT_ERR_BAD_ARG, "ld must be a multiple of " + std::to_string(vec) + " in [" +
+                                               std::to_string(vec) + ", " + std::to_string(max_ld) + "]");
+    if (reinterpret_cast<uintptr_t>(out) % 16) return set_error(SPTT_ERR_BAD_ARG, "out must be 16-byte aligned");
+    for (int l = 1; l < csf->nmodes; ++l) {
+        const void *p = factors[csf->order[l]];
+        if (!p) return set_error(SPTT_ERR_BAD_ARG, "a non-root factor is NULL");
+        if (reinterpret_cast<uintptr_t>(p) % 16) return set_error(SPTT_ERR_BAD_ARG, "factors must be 16-byte aligned");
+        if (p == out) return set_error(SPTT_ERR_BAD_ARG, "out aliases a factor");
+    }
+    if (sched) {
+        if (sched->chunk && (sched->chunk < 16 || sched->chunk > 4096 || (sched->chunk & (sched->chunk - 1))))
+            return set_error(SPTT_ERR_BAD_ARG, "sched->chunk must be a power of two in [16, 4096]");
+        if (sched->block && (sched->block < 32 || sched->block > 256 || sched->block % 32))
+            return set_error(SPTT_ERR_BAD_ARG, "sched->block must be a multiple of 32 in [32, 256]");
+    }
+    return mttkrp_launch(const_cast<sptt_csf *>(csf), factors, factor_dtype, ld, out, sched,
+                         reinterpret_cast<cudaStream_t>(stream));
+}
