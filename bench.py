@@ -1,0 +1,392 @@
+"""Benchmark: CP-ALS over CSF on the 3-mode power-law tensor of NETFLIX shape.
+
+Workload (default): 480,000 x 18,000 x 2,000, 1e8 distinct non-zeros, Zipf(1.1)
+per mode through a random permutation, values lognormal(0,1), rank 16, FP32
+factor gathers (FP32 accumulate, FP64 R x R solve). One step = one CP-ALS
+iteration (Algorithm 1): per mode an MTTKRP over the CSF rooted at that mode,
+the normal-equation solve, normalisation, then the fit, with the CSFs
+resident in HBM (they are built once, as the paper's pre-processing).
+
+value  = whole-job MTTKRP work rate, N_modes * nnz * R per iteration / time,
+         in Gnnz*R/s (summed over ranks: each rank runs an independent replica).
+e2e    = the same metric through the one-shot C-ABI call (sptt_cpd_als) from
+         pinned host buffers: host->device copy of the COO, sort/CSF builds,
+         the ALS iterations and the copy of the factors back, all timed.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MTTKRP Gnnz·R/s, %HBM peak; CP-ALS s/iter mixed vs FP32 at Δfit≤1e-4"
+UNIT = "Gnnz·R/s"
+WORKLOAD = "powerlaw3 480000x18000x2000 nnz=1e8 zipf1.1+perm lognormal(0,1)"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--rank", type=int, default=16)
+    p.add_argument("--nnz", type=int, default=100_000_000)
+    p.add_argument("--seed", type=int, default=2)
+    p.add_argument("--e2e-steps", type=int, default=2)
+    p.add_argument("--e2e-iters", type=int, default=20)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-extras", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# Clock sampling during the timed region
+# ---------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.path = tempfile.mktemp(prefix="clocks_", suffix=".csv")
+        self.proc = None
+        self.gpu = gpu_index
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        busy = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(busy), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the oracle as it stands, on a bounded sample
+# ---------------------------------------------------------------------------
+def cpu_oracle_rate(t_cpu_inds, t_cpu_vals, dims, R, seconds):
+    """Times one oracle CP-ALS iteration on a prefix sample sized for about
+    `seconds` of CPU work. Returns (Gnnz*R/s, sample description)."""
+    import numpy as np
+
+    import oracle
+    nnz = t_cpu_vals.shape[0]
+
+    def run(s):
+        inds = [np.ascontiguousarray(x[:s]) for x in t_cpu_inds]
+        vals = np.ascontiguousarray(t_cpu_vals[:s])
+        t0 = time.perf_counter()
+        oracle.cpd_als(inds, vals, dims, R, 1, seed=1, coalesce_first=False)
+        return time.perf_counter() - t0
+
+    s0 = min(nnz, 500_000)
+    t0 = run(s0)
+    s = int(min(nnz, max(s0, s0 * seconds / max(t0, 1e-3))))
+    t = run(s) if s != s0 else t0
+    rate = len(dims) * s * R / t / 1e9
+    return rate, t, s
+
+
+def reference_arm(args, rank, world):
+    """--impl reference: the FP64 oracle timed on the host cores, rank 0 only."""
+    if rank != 0:
+        return
+    import numpy as np
+    import torch
+
+    import tensorgen
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = tensorgen.powerlaw3(seed=args.seed, device=dev, nnz=args.nnz)
+    inds = [x.cpu().numpy() for x in t.inds]
+    vals = t.vals.cpu().numpy()
+    del t
+    import oracle
+    R = args.rank
+    # one step = one oracle CP-ALS iteration on a bounded prefix sample
+    budget = max(3.0, 150.0 / max(1, args.steps + args.warmup))
+    _, t1, s = cpu_oracle_rate(inds, vals, [480_000, 18_000, 2_000], R, min(budget, 15.0))
+    sub_i = [np.ascontiguousarray(x[:s]) for x in inds]
+    sub_v = np.ascontiguousarray(vals[:s])
+    dims = [480_000, 18_000, 2_000]
+    for _ in range(args.warmup):
+        oracle.cpd_als(sub_i, sub_v, dims, R, 1, seed=1, coalesce_first=False)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.cpd_als(sub_i, sub_v, dims, R, 1, seed=1, coalesce_first=False)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = 3 * s * R * args.steps / tot / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "rank": R, "sample_nnz": s},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "one CP-ALS iteration (3 MTTKRPs + solve + fit) of the FP64 C oracle "
+                                   "on the first %d non-zeros, single thread" % s},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# Our arm
+# ---------------------------------------------------------------------------
+def byte_model(csf, dims, R, distinct, s_f=4):
+    """Algorithmic bytes of one root-mode MTTKRP: values and leaf indices,
+    fids/fptr of the upper levels, each distinct factor row once per level,
+    and the output write."""
+    n = csf.nmodes
+    nnz = csf.nfibs[-1]
+    b = nnz * (4 + 4)
+    for l in range(n - 1):
+        b += csf.nfibs[l] * (4 + 4)
+    for l in range(1, n):
+        b += distinct[csf.order[l]] * R * s_f
+    b += dims[csf.root] * R * 4
+    return b
+
+
+def flop_model(csf, R):
+    nnz = csf.nfibs[-1]
+    return 2 * R * (nnz + sum(csf.nfibs[1:-1]))
+
+
+def ours(args, rank, world, local):
+    import torch
+
+    import paper_1812_05961_gb300 as sptt
+    import tensorgen
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    R = args.rank
+    t_gen = time.time()
+    t = tensorgen.powerlaw3(seed=args.seed + rank, device=dev, nnz=args.nnz)
+    torch.cuda.synchronize()
+    t_gen = time.time() - t_gen
+    dims = t.dims
+    nnz = t.nnz
+    distinct = [int(torch.unique(x).numel()) for x in t.inds]
+
+    # CSFs (one per root) are built inside the handle; build them here too for the byte model
+    csfs = [sptt.Csf(dims, t.inds, t.vals, r) for r in range(3)]
+    bytes_per = [byte_model(c, dims, R, distinct) for c in csfs]
+    flops_per = [flop_model(c, R) for c in csfs]
+    nfibs = [c.nfibs for c in csfs]
+    del csfs
+
+    t_build = time.time()
+    cpd = sptt.Cpd(dims, t.inds, t.vals, R, seed=1, profile=1)
+    t_build = time.time() - t_build
+    cpd.init()
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        cpd.iterate(1)
+    torch.cuda.synchronize()
+    cpd.timers()  # drain warm-up timer records
+    base_timers = cpd.timers()
+    l0 = sptt.sptt_debug_launch_count()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            cpd.iterate(1)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    launches = sptt.sptt_debug_launch_count() - l0
+    ms_total = ev0.elapsed_time(ev1)
+    tm = cpd.timers()
+    mttkrp_ms = tm["mttkrp"][0] - base_timers["mttkrp"][0]
+    mttkrp_n = tm["mttkrp"][1] - base_timers["mttkrp"][1]
+    routines = {k: (tm[k][0] - base_timers[k][0]) / args.steps for k in tm}
+    fit = cpd.fit()[0]
+    if dist:
+        mt = torch.tensor([ms_total], device=dev)
+        dist.all_reduce(mt, op=dist.ReduceOp.MAX)
+        ms_total = float(mt.item())
+    ms_step = ms_total / args.steps
+    units = 3 * nnz * R * args.steps * world
+    value = units / (ms_total * 1e-3) / 1e9
+
+    peak, peak_kind = measured_peaks()
+    # MTTKRP routine (zero-fill + kernel) per launch; the three roots differ,
+    # so the algorithmic bytes are summed over the modes and divided by the total time
+    alg_bytes = sum(bytes_per) * args.steps
+    achieved = alg_bytes / (mttkrp_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+                else "fallback 6.8 TB/s",
+                "bytes_per_launch": [int(b) for b in bytes_per],
+                "flops_per_launch": [int(f) for f in flops_per],
+                "avg_launch_ms": mttkrp_ms / max(mttkrp_n, 1),
+                "launches": mttkrp_n}
+
+    # e2e: the one-shot call from pinned host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        h_inds = [x.cpu().pin_memory() for x in t.inds]
+        h_vals = t.vals.cpu().pin_memory()
+        h_out = [torch.empty(d, R).pin_memory() for d in dims]
+        h_lam = torch.empty(R, dtype=torch.float64).pin_memory()
+        sptt.sptt_cpd_als(dims, h_inds, h_vals, R, 1, factors_out=h_out, lambda_out=h_lam, seed=1)
+        torch.cuda.synchronize()
+        times = []
+        for _ in range(args.e2e_steps):
+            t0 = time.perf_counter()
+            sptt.sptt_cpd_als(dims, h_inds, h_vals, R, args.e2e_iters, factors_out=h_out,
+                              lambda_out=h_lam, seed=1)
+            times.append(time.perf_counter() - t0)
+        e2e_t = sum(times) / len(times)
+        if dist:
+            tt = torch.tensor([e2e_t], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e2e_t = float(tt.item())
+        h2d = sum(x.numel() * 4 for x in h_inds) + h_vals.numel() * 4
+        d2h = sum(d * R * 4 for d in dims) + R * 8 + 8
+        e2e = {"value": 3 * nnz * R * args.e2e_iters * world / e2e_t / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "seconds_per_call": e2e_t, "als_iters_per_call": args.e2e_iters}
+        del h_inds, h_vals
+
+    extras = {}
+    if not args.no_extras:
+        # mixed precision vs FP32 at the same start, plus rank 32
+        res = {}
+        for name, prec, r in (("fp32_r16", sptt.SPTT_F32, R), ("bf16_r16", sptt.SPTT_BF16, R),
+                              ("fp32_r32", sptt.SPTT_F32, 32), ("bf16_r32", sptt.SPTT_BF16, 32)):
+            c = sptt.Cpd(dims, t.inds, t.vals, r, seed=1, precision=prec).init()
+            c.iterate(2)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            c.iterate(18)
+            b.record(stream)
+            torch.cuda.synchronize()
+            s_iter = a.elapsed_time(b) / 18 / 1e3
+            if prec == sptt.SPTT_BF16:
+                c.refine(1)
+            res[name] = {"s_per_iter": s_iter, "fit_after_20": c.fit()[0],
+                         "GnnzR_per_s": 3 * nnz * r / s_iter / 1e9}
+            del c
+        for r in (16, 32):
+            f32, b16 = res["fp32_r%d" % r], res["bf16_r%d" % r]
+            b16["delta_fit_vs_fp32"] = b16["fit_after_20"] - f32["fit_after_20"]
+            b16["speedup_vs_fp32"] = f32["s_per_iter"] / b16["s_per_iter"]
+        extras["precision_and_rank"] = res
+
+    cpu_base = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        ci = [x.cpu().numpy() for x in t.inds]
+        cv = t.vals.cpu().numpy()
+        rate, secs, s = cpu_oracle_rate(ci, cv, dims, R, args.cpu_seconds)
+        cpu_base = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                    "sample": "one CP-ALS iteration (3 MTTKRPs + solve + fit) of the FP64 C oracle on "
+                              "the first %d of the %d non-zeros, single thread, %.1f s" % (s, nnz, secs)}
+
+    clocks = clk.summary()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "rank": R, "step": "one CP-ALS iteration (3 mode updates + fit)",
+                       "l2": "inputs larger than L2 (CSF about 0.8 GB per mode)",
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "nfibs_per_root": nfibs, "gen_s": round(t_gen, 1), "cpd_create_s": round(t_build, 2)},
+            "roofline": roofline, "cpu_baseline": cpu_base, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clocks, "routines_ms_per_iter": routines, "fit": fit, "extras": extras,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        reference_arm(args, rank, world)
+        return
+    ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

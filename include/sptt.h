@@ -170,7 +170,8 @@ sptt_status sptt_mttkrp(const sptt_csf *csf, const void *const *factors, int32_t
  * G = A^T A over the first `rank` columns of A (device, rows x ld row-major
  * FP32, ld >= rank, ld multiple of 4), into G (device, rank x rank FP64,
  * row-major). Products are formed in FP32 and summed in FP32 over 64-row
- * tiles, the tile sums in FP64. Asynchronous. rank <= SPTT_MAX_RANK_ALS.
+ * tiles, the tile sums in FP64. A may be NULL when rows = 0 (G = 0).
+ * Asynchronous. rank <= SPTT_MAX_RANK_ALS.
  */
 sptt_status sptt_gram(const float *A, int64_t rows, int32_t rank, int32_t ld, double *G,
                       sptt_stream stream);
@@ -300,6 +301,10 @@ sptt_status sptt_cpd_als(const sptt_coo *coo, int32_t rank, int32_t max_iters, d
  * the device were out of memory; 0 disables. Process-wide.
  */
 void sptt_debug_fail_alloc_after(int64_t countdown);
+
+/* Number of CUDA kernels this library has launched in this process so far
+ * (every launch site counts once per launch). */
+int64_t sptt_debug_launch_count(void);
 
 #ifdef __cplusplus
 }

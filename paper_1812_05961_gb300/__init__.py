@@ -102,6 +102,7 @@ def lib() -> ctypes.CDLL:
             "sptt_cpd_als": (_ST, [ctypes.POINTER(sptt_coo), _I32, _I32, ctypes.c_double,
                                    ctypes.POINTER(sptt_opts), _P, _P, _P, _P, _P]),
             "sptt_debug_fail_alloc_after": (None, [_I64]),
+            "sptt_debug_launch_count": (_I64, []),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -339,6 +340,10 @@ def sptt_cpd_als(dims, inds, vals, rank: int, max_iters: int, tol: float = 0.0,
 
 def sptt_debug_fail_alloc_after(countdown: int):
     lib().sptt_debug_fail_alloc_after(countdown)
+
+
+def sptt_debug_launch_count() -> int:
+    return lib().sptt_debug_launch_count()
 
 
 # ---------------------------------------------------------------------------

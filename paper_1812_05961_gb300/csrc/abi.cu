@@ -12,6 +12,7 @@ namespace sptt {
 namespace {
 thread_local std::string g_last_error;
 std::atomic<int64_t> g_fail_alloc_countdown{0};
+std::atomic<int64_t> g_launches{0};
 std::mutex g_pool_mu;
 bool g_pool_ready[64] = {false};
 int g_sm_count[64] = {0};
@@ -29,6 +30,8 @@ sptt_status cuda_error(cudaError_t e, const char *what) {
 }
 
 void clear_error() { g_last_error.clear(); }
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 static int current_device() {
     int d = 0;
@@ -99,6 +102,8 @@ extern "C" const char *sptt_status_str(sptt_status s) {
 extern "C" const char *sptt_last_error(void) { return g_last_error.c_str(); }
 
 extern "C" int32_t sptt_version(void) { return 100; }
+
+extern "C" int64_t sptt_debug_launch_count(void) { return g_launches.load(); }
 
 extern "C" void sptt_debug_fail_alloc_after(int64_t countdown) {
     g_fail_alloc_countdown.store(countdown > 0 ? countdown : 0);

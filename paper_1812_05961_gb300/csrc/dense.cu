@@ -670,7 +670,7 @@ using namespace sptt;
 extern "C" sptt_status sptt_gram(const float *A, int64_t rows, int32_t rank, int32_t ld, double *G,
                                  sptt_stream stream) {
     clear_error();
-    if (!A || !G) return set_error(SPTT_ERR_BAD_ARG, "A and G must be non-NULL");
+    if (!G || (!A && rows > 0)) return set_error(SPTT_ERR_BAD_ARG, "A (when rows > 0) and G must be non-NULL");
     if (rows < 0) return set_error(SPTT_ERR_BAD_ARG, "rows < 0");
     if (rank < 1 || rank > SPTT_MAX_RANK_ALS) return set_error(SPTT_ERR_UNSUPPORTED, "rank must be in [1, 64]");
     if (ld < rank) return set_error(SPTT_ERR_BAD_ARG, "ld < rank");

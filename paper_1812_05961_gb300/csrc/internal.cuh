@@ -20,6 +20,7 @@ constexpr int kNumSMs = 152;  // GB300: 2 dies x 76 SMs (queried at run time whe
 sptt_status set_error(sptt_status s, const std::string &msg);
 sptt_status cuda_error(cudaError_t e, const char *what);
 void clear_error();
+void count_launch();
 
 #define SPTT_CUDA(call)                                        \
     do {                                                       \
@@ -27,8 +28,11 @@ void clear_error();
         if (e__ != cudaSuccess) return ::sptt::cuda_error(e__, #call); \
     } while (0)
 
+// Every kernel launch site is followed by this check, which also counts the
+// launch (sptt_debug_launch_count).
 #define SPTT_CHECK_LAUNCH(what)                                \
     do {                                                       \
+        ::sptt::count_launch();                                \
         cudaError_t e__ = cudaGetLastError();                  \
         if (e__ != cudaSuccess) return ::sptt::cuda_error(e__, what); \
     } while (0)
