@@ -239,6 +239,7 @@ def ours(args, rank, world, local):
     dims = t.dims
     nnz = t.nnz
     distinct = [int(torch.unique(x).numel()) for x in t.inds]
+    torch.cuda.empty_cache()  # drop the generator's temporaries
 
     # CSFs (one per root) are built inside the handle; build them here too for the byte model
     csfs = [sptt.Csf(dims, t.inds, t.vals, r) for r in range(3)]

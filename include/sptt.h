@@ -133,7 +133,8 @@ sptt_status sptt_csf_copy_level(const sptt_csf *csf, int32_t level, int32_t *fpt
  *   chunk       non-zeros per work unit of a lane group; power of two in
  *               [16, 4096]; 0 = default
  *   block       threads per CTA (multiple of 32, <= 256); 0 = default
- *   variant     0 = default kernel; other ids select alternative kernels
+ *   variant     0 = batched flag walk (default); 1 = plain walk; 2 = batched
+ *               flag walk limited to 128 registers (two CTAs per SM)
  */
 typedef struct {
     int32_t chunk;

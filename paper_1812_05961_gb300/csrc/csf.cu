@@ -145,6 +145,20 @@ __global__ void fill_levels_kernel(IdxPtrs s, LevelScan ls, int nlev, int64_t n)
     }
 }
 
+// lvl[k] = first level whose coordinate changes at k (0 for k = 0).
+__global__ void leaf_level_kernel(IdxPtrs s, int nlev, int64_t n, uint8_t *__restrict__ lvl) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        int d = 0;
+        if (k > 0) {
+            d = nlev - 1;
+            for (int l = 0; l < nlev; ++l)
+                if (s.p[l][k] != s.p[l][k - 1]) { d = l; break; }
+        }
+        lvl[k] = (uint8_t)d;
+    }
+}
+
 // part[c*(N-1) + l] = level-l fiber holding leaf c*chunk (binary search up the tree).
 struct FptrPtrs {
     const int32_t *p[kMaxModes];
@@ -232,6 +246,7 @@ void csf_destroy(sptt_csf *c) {
         if (c->fids[l]) cudaFree(c->fids[l]);
     }
     if (c->vals) cudaFree(c->vals);
+    if (c->lvl) cudaFree(c->lvl);
     if (c->part) cudaFree(c->part);
     delete c;
 }
@@ -443,6 +458,7 @@ sptt_status csf_build_device(const sptt_coo *coo, int32_t root, const int32_t *o
     }
     SPTT_CUDA(cudaMalloc(&c->fids[N - 1], (size_t)(u + 64) * sizeof(int32_t)));
     SPTT_CUDA(cudaMalloc(&c->vals, (size_t)(u + 64) * sizeof(float)));
+    SPTT_CUDA(cudaMalloc(&c->lvl, (size_t)(u + 64)));
     if (u > 0) {
         LevelScan ls{};
         for (int l = 0; l < N - 1; ++l) {
@@ -452,6 +468,8 @@ sptt_status csf_build_device(const sptt_coo *coo, int32_t root, const int32_t *o
         }
         fill_levels_kernel<<<grid_for(u), kThreads, 0, st>>>(s, ls, N, u);
         SPTT_CHECK_LAUNCH("fill_levels_kernel");
+        leaf_level_kernel<<<grid_for(u), kThreads, 0, st>>>(s, N, u, c->lvl);
+        SPTT_CHECK_LAUNCH("leaf_level_kernel");
         SPTT_CUDA(cudaMemcpyAsync(c->fids[N - 1], s.p[N - 1], u * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
         SPTT_CUDA(cudaMemcpyAsync(c->vals, sv, u * sizeof(float), cudaMemcpyDeviceToDevice, st));
     } else {

@@ -106,6 +106,10 @@ struct sptt_csf {
     int32_t *fptr[SPTT_MAX_MODES] = {nullptr};  // levels 0..N-2
     int32_t *fids[SPTT_MAX_MODES] = {nullptr};  // levels 0..N-1
     float *vals = nullptr;
+    // lvl[k] = the first tree level whose fiber changes at leaf k (0 for
+    // k = 0; N-1 when only the leaf index changes). Lets the MTTKRP walk
+    // find fiber boundaries from the leaf stream alone.
+    uint8_t *lvl = nullptr;
     // Work partition for the MTTKRP kernels: for leaf chunk c (leaves
     // [c*part_chunk, ...)), part[c*(N-1) + l] = the level-l fiber holding
     // the chunk's first leaf. Rebuilt when another chunk size is requested.

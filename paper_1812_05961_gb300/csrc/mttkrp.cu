@@ -30,6 +30,7 @@ struct MttkrpArgs {
     const int32_t *fids[kMaxModes];
     const void *fac[kMaxModes];  // by level; fac[0] unused
     const float *vals;
+    const uint8_t *lvl;
     const int32_t *part;
     int64_t nchunks;
     int64_t nnz;
@@ -82,6 +83,170 @@ __device__ __forceinline__ void red_add_row(float *dst, const float (&a)[VEC]) {
                      : "memory");
 }
 
+// A factor row segment as loaded (16 bytes: 4 FP32 or 8 BF16), widened to
+// FP32 only where it is used.
+template <typename T>
+struct Raw;
+
+template <>
+struct Raw<float> {
+    static constexpr int VEC = 4;
+    __device__ __forceinline__ static uint4 load(const void *base, int64_t row, int ld, int col) {
+        return __ldg(reinterpret_cast<const uint4 *>(static_cast<const float *>(base) + row * ld + col));
+    }
+    __device__ __forceinline__ static void widen(const uint4 &u, float (&x)[4]) {
+        x[0] = __uint_as_float(u.x); x[1] = __uint_as_float(u.y);
+        x[2] = __uint_as_float(u.z); x[3] = __uint_as_float(u.w);
+    }
+};
+
+template <>
+struct Raw<__nv_bfloat16> {
+    static constexpr int VEC = 8;
+    __device__ __forceinline__ static uint4 load(const void *base, int64_t row, int ld, int col) {
+        return __ldg(reinterpret_cast<const uint4 *>(static_cast<const __nv_bfloat16 *>(base) + row * ld + col));
+    }
+    __device__ __forceinline__ static void widen(const uint4 &u, float (&x)[8]) {
+        const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            x[2 * i] = __uint_as_float(w[i] << 16);
+            x[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u);
+        }
+    }
+};
+
+// Variant 0: batched walk driven by the per-leaf level flags.
+// Each lane group takes a chunk of leaves in batches of B = 8: the batch's
+// values, leaf indices and level flags arrive in three vector loads; then
+// every factor row the batch needs (the 8 leaf rows, and the rows of the
+// level-(N-2) fibers that start inside the batch, whose ids are consecutive)
+// is requested before any of them is used, so a group keeps up to 16 row
+// gathers in flight instead of walking one dependent load at a time. Rows of
+// fibers at levels above N-2 are requested when the fiber opens and used when
+// it closes.
+template <int NM, typename T, int MINB>
+__global__ void __launch_bounds__(256, MINB) mttkrp_flag_kernel(const MttkrpArgs a) {
+    using Rw = Raw<T>;
+    constexpr int VEC = Rw::VEC;
+    constexpr int NL = NM - 1;  // accumulator levels 0..NM-2
+    constexpr int LF = NM - 2;  // level of the leaves' parent fibers
+    constexpr int B = 8;
+    const int lane = threadIdx.x & 31;
+    const int gi = lane / a.G;
+    const int gl = lane - gi * a.G;
+    if (gi >= a.gpw) return;  // no warp collectives below
+    const int col = gl * VEC;
+    const int ld = a.ld;
+    const int64_t gwarp = (int64_t)(blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = (int64_t)(gridDim.x * blockDim.x) >> 5;
+
+    for (int64_t c = gwarp * a.gpw + gi; c < a.nchunks; c += nwarps * a.gpw) {
+        const int64_t k0 = c * (int64_t)a.chunk;
+        const int64_t k1 = (k0 + a.chunk < a.nnz) ? k0 + a.chunk : a.nnz;
+        int32_t f[NL];
+#pragma unroll
+        for (int l = 0; l < NL; ++l) f[l] = __ldg(a.part + c * NL + l);
+        float acc[NL][VEC];
+#pragma unroll
+        for (int l = 0; l < NL; ++l)
+#pragma unroll
+            for (int i = 0; i < VEC; ++i) acc[l][i] = 0.f;
+        uint4 rowc[NL];  // rows of the open fibers, levels 1..NL-1
+#pragma unroll
+        for (int l = 1; l < NL; ++l) rowc[l] = Rw::load(a.fac[l], __ldg(a.fids[l] + f[l]), ld, col);
+        int32_t fid0 = __ldg(a.fids[0] + f[0]);
+        bool first_slice = true;
+
+        for (int64_t kb = k0; kb < k1; kb += B) {
+            const float4 va = __ldg(reinterpret_cast<const float4 *>(a.vals + kb));
+            const float4 vb = __ldg(reinterpret_cast<const float4 *>(a.vals + kb + 4));
+            const int4 ia = __ldg(reinterpret_cast<const int4 *>(a.fids[NM - 1] + kb));
+            const int4 ib = __ldg(reinterpret_cast<const int4 *>(a.fids[NM - 1] + kb + 4));
+            const uint2 lw = __ldg(reinterpret_cast<const uint2 *>(a.lvl + kb));
+            const float v[B] = {va.x, va.y, va.z, va.w, vb.x, vb.y, vb.z, vb.w};
+            const int32_t li[B] = {ia.x, ia.y, ia.z, ia.w, ib.x, ib.y, ib.z, ib.w};
+            const int nvalid = (k1 - kb < B) ? (int)(k1 - kb) : B;
+            uint4 x[B];
+#pragma unroll
+            for (int j = 0; j < B; ++j)
+                if (j < nvalid) x[j] = Rw::load(a.fac[NM - 1], li[j], ld, col);
+            // leaves that open a new level-LF fiber (never the chunk's first leaf)
+            uint32_t sm = 0;
+#pragma unroll
+            for (int j = 0; j < B; ++j) {
+                const uint32_t d = ((j < 4 ? lw.x : lw.y) >> (8 * (j & 3))) & 0xffu;
+                if (j < nvalid && d <= (uint32_t)LF && (kb + j) != k0) sm |= 1u << j;
+            }
+            uint4 nr[B];
+            if (LF >= 1) {
+#pragma unroll
+                for (int j = 0; j < B; ++j)
+                    if ((sm >> j) & 1u) {
+                        const int pos = __popc(sm & ((1u << j) - 1u)) + 1;
+                        nr[j] = Rw::load(a.fac[LF], __ldg(a.fids[LF] + f[LF] + pos), ld, col);
+                    }
+            }
+#pragma unroll
+            for (int j = 0; j < B; ++j) {
+                if (j >= nvalid) break;
+                if ((sm >> j) & 1u) {
+                    const int d = (int)(((j < 4 ? lw.x : lw.y) >> (8 * (j & 3))) & 0xffu);
+                    if (LF >= 1) {
+                        float r[VEC];
+                        Rw::widen(rowc[LF], r);
+#pragma unroll
+                        for (int i = 0; i < VEC; ++i) {
+                            acc[LF - 1][i] = fmaf(r[i], acc[LF][i], acc[LF - 1][i]);
+                            acc[LF][i] = 0.f;
+                        }
+                        ++f[LF];
+                        rowc[LF] = nr[j];
+                    }
+#pragma unroll
+                    for (int l = LF - 1; l >= 1; --l) {
+                        if (d <= l) {
+                            float r[VEC];
+                            Rw::widen(rowc[l], r);
+#pragma unroll
+                            for (int i = 0; i < VEC; ++i) {
+                                acc[l - 1][i] = fmaf(r[i], acc[l][i], acc[l - 1][i]);
+                                acc[l][i] = 0.f;
+                            }
+                            ++f[l];
+                            rowc[l] = Rw::load(a.fac[l], __ldg(a.fids[l] + f[l]), ld, col);
+                        }
+                    }
+                    if (d == 0) {  // the slice is complete
+                        float *dst = a.out + (int64_t)fid0 * ld + col;
+                        if (first_slice) red_add_row<VEC>(dst, acc[0]);
+                        else store_row<VEC>(dst, acc[0]);
+                        first_slice = false;
+#pragma unroll
+                        for (int i = 0; i < VEC; ++i) acc[0][i] = 0.f;
+                        ++f[0];
+                        fid0 = __ldg(a.fids[0] + f[0]);
+                    }
+                }
+                float xr[VEC];
+                Rw::widen(x[j], xr);
+#pragma unroll
+                for (int i = 0; i < VEC; ++i) acc[LF][i] = fmaf(v[j], xr[i], acc[LF][i]);
+            }
+        }
+        // chunk end: fold the open fibers and add the partial slice
+#pragma unroll
+        for (int l = LF; l >= 1; --l) {
+            float r[VEC];
+            Rw::widen(rowc[l], r);
+#pragma unroll
+            for (int i = 0; i < VEC; ++i) acc[l - 1][i] = fmaf(r[i], acc[l][i], acc[l - 1][i]);
+        }
+        red_add_row<VEC>(a.out + (int64_t)fid0 * ld + col, acc[0]);
+    }
+}
+
+// Variant 1: the plain walk (one leaf at a time, fiber ends from fptr).
 template <int NM, typename T>
 __global__ void __launch_bounds__(256) mttkrp_root_kernel(const MttkrpArgs a) {
     using G_ = Gather<T>;
@@ -165,8 +330,9 @@ __global__ void __launch_bounds__(256) mttkrp_root_kernel(const MttkrpArgs a) {
 }
 
 template <int NM, typename T>
-sptt_status launch_nm(const MttkrpArgs &a, int block, cudaStream_t st) {
-    auto kern = mttkrp_root_kernel<NM, T>;
+sptt_status launch_nm(const MttkrpArgs &a, int block, int variant, cudaStream_t st) {
+    auto kern = variant == 1 ? mttkrp_root_kernel<NM, T>
+                : (variant == 2 ? mttkrp_flag_kernel<NM, T, 2> : mttkrp_flag_kernel<NM, T, 1>);
     int per_sm = 0;
     SPTT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, 0));
     if (per_sm < 1) per_sm = 1;
@@ -181,12 +347,12 @@ sptt_status launch_nm(const MttkrpArgs &a, int block, cudaStream_t st) {
 }
 
 template <typename T>
-sptt_status launch_t(int nm, const MttkrpArgs &a, int block, cudaStream_t st) {
+sptt_status launch_t(int nm, const MttkrpArgs &a, int block, int variant, cudaStream_t st) {
     switch (nm) {
-        case 2: return launch_nm<2, T>(a, block, st);
-        case 3: return launch_nm<3, T>(a, block, st);
-        case 4: return launch_nm<4, T>(a, block, st);
-        case 5: return launch_nm<5, T>(a, block, st);
+        case 2: return launch_nm<2, T>(a, block, variant, st);
+        case 3: return launch_nm<3, T>(a, block, variant, st);
+        case 4: return launch_nm<4, T>(a, block, variant, st);
+        case 5: return launch_nm<5, T>(a, block, variant, st);
         default: return set_error(SPTT_ERR_UNSUPPORTED, "nmodes");
     }
 }
@@ -201,8 +367,9 @@ sptt_status mttkrp_launch(sptt_csf *csf, const void *const *factors, int32_t dty
     SPTT_TRY(fill_zero_launch(out, (size_t)rows * ld * sizeof(float), st));
     const int64_t nnz = csf->nfibs[N - 1];
     if (nnz == 0) return SPTT_OK;
-    int32_t chunk = (sched && sched->chunk) ? sched->chunk : 64;
+    int32_t chunk = (sched && sched->chunk) ? sched->chunk : 128;
     int block = (sched && sched->block) ? sched->block : 256;
+    const int variant = sched ? sched->variant : 0;
     SPTT_TRY(csf_ensure_partition(csf, chunk, st));
     MttkrpArgs a{};
     for (int l = 0; l < N; ++l) {
@@ -211,6 +378,7 @@ sptt_status mttkrp_launch(sptt_csf *csf, const void *const *factors, int32_t dty
         a.fac[l] = l ? factors[csf->order[l]] : nullptr;
     }
     a.vals = csf->vals;
+    a.lvl = csf->lvl;
     a.part = csf->part;
     a.nchunks = csf->part_nchunks;
     a.nnz = nnz;
@@ -219,8 +387,8 @@ sptt_status mttkrp_launch(sptt_csf *csf, const void *const *factors, int32_t dty
     a.G = ld / vec;
     a.gpw = 32 / a.G;
     a.out = out;
-    if (dtype == SPTT_BF16) return launch_t<__nv_bfloat16>(N, a, block, st);
-    return launch_t<float>(N, a, block, st);
+    if (dtype == SPTT_BF16) return launch_t<__nv_bfloat16>(N, a, block, variant, st);
+    return launch_t<float>(N, a, block, variant, st);
 }
 
 }  // namespace sptt
@@ -250,6 +418,8 @@ extern "C" sptt_status sptt_mttkrp(const sptt_csf *csf, const void *const *facto
             return set_error(SPTT_ERR_BAD_ARG, "sched->chunk must be a power of two in [16, 4096]");
         if (sched->block && (sched->block < 32 || sched->block > 256 || sched->block % 32))
             return set_error(SPTT_ERR_BAD_ARG, "sched->block must be a multiple of 32 in [32, 256]");
+        if (sched->variant < 0 || sched->variant > 2)
+            return set_error(SPTT_ERR_BAD_ARG, "sched->variant must be in [0, 2]");
     }
     return mttkrp_launch(const_cast<sptt_csf *>(csf), factors, factor_dtype, ld, out, sched,
                          reinterpret_cast<cudaStream_t>(stream));

@@ -65,13 +65,28 @@ def test_mttkrp_padded_rank(R, ld, cuda_device):
 
 @pytest.mark.parametrize("chunk", [16, 32, 128, 512, 4096])
 @pytest.mark.parametrize("block", [64, 256])
-def test_mttkrp_schedules_agree(chunk, block, cuda_device):
-    dims = (400, 300, 200)
-    t = make(dims, 50000, seed=5, dist="zipf", s=1.3)
+@pytest.mark.parametrize("variant", [0, 1, 2])
+def test_mttkrp_schedules_agree(chunk, block, variant, cuda_device):
+    dims = (400, 300, 200, 20)
+    t = make(dims, 50003, seed=5, dist="zipf", s=1.3)
     F = rand_factors(dims, 16, seed=1)
-    for root in range(3):
-        M = _run(t, root, F, cuda_device, sched=(chunk, block, 0))
+    for root in range(4):
+        M = _run(t, root, F, cuda_device, sched=(chunk, block, variant))
         _check(M, t, F, root, 16, 1e-5)
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("nm", [2, 3, 4, 5])
+def test_mttkrp_variants_every_order(variant, nm, cuda_device):
+    dims = (90, 70, 50, 30, 10)[:nm]
+    t = make(dims, 20011, seed=nm, dist="zipf", s=1.2)
+    for dtype, ld in ((sptt.SPTT_F32, 8), (sptt.SPTT_BF16, 16)):
+        F = rand_factors(dims, ld, seed=nm + ld)
+        if dtype == sptt.SPTT_BF16:
+            F = [f.to(torch.bfloat16).float() for f in F]
+        for root in range(nm):
+            M = _run(t, root, F, cuda_device, dtype=dtype, sched=(64, 128, variant))
+            _check(M, t, F, root, ld, 1e-5)
 
 
 @pytest.mark.parametrize("ld", [8, 16, 32, 64])
