@@ -133,8 +133,10 @@ sptt_status sptt_csf_copy_level(const sptt_csf *csf, int32_t level, int32_t *fpt
  *   chunk       non-zeros per work unit of a lane group; power of two in
  *               [16, 4096]; 0 = default
  *   block       threads per CTA (multiple of 32, <= 256); 0 = default
- *   variant     0 = batched flag walk (default); 1 = plain walk; 2 = batched
- *               flag walk limited to 128 registers (two CTAs per SM)
+ *   variant     kernel variant: 0 = default; 1 = plain walk (fiber ends
+ *               from fptr, one leaf at a time); 2..5 = batched walk driven by
+ *               the per-leaf level flags with (batch, CTAs per SM) = (8, 2),
+ *               (4, 3), (4, 4), (8, 1)
  */
 typedef struct {
     int32_t chunk;

@@ -31,7 +31,7 @@ sptt_status cuda_error(cudaError_t e, const char *what) {
 
 void clear_error() { g_last_error.clear(); }
 
-void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_launch(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 static int current_device() {
     int d = 0;

@@ -17,6 +17,8 @@
 
 using namespace sptt;
 
+extern "C" int64_t sptt_debug_launch_count(void);
+
 namespace {
 constexpr int kFitHistory = 4096;
 
@@ -42,7 +44,11 @@ struct sptt_cpd {
     float *M = nullptr;
     double *normx2 = nullptr;
     double *fits = nullptr;  // device ring of fit values, kFitHistory entries
+    int64_t *iter_dev = nullptr;  // device iteration counter (indexes the ring)
     DenseWork w;
+    // one captured iteration per gather precision (index 1 = BF16)
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    int64_t graph_kernels[2] = {0, 0};
     int64_t iters = 0;       // iterations run since init
     // profiling
     std::vector<TimerRec> pending;
@@ -125,8 +131,45 @@ sptt_status run_iteration(sptt_cpd *c, bool bf16) {
     }
     {
         Timed t(c, 4);
-        SPTT_TRY(fit_launch(c->G, N, c->normx2, &c->w, c->fits + (c->iters % kFitHistory), c->st));
+        SPTT_TRY(fit_launch(c->G, N, c->normx2, &c->w, c->fits, kFitHistory, c->iter_dev, c->st));
     }
+    return SPTT_OK;
+}
+
+// Captures one iteration into a graph (built once per precision) and
+// replays it. Partitions are prepared before capture (their first build
+// allocates and synchronises).
+sptt_status run_iteration_graph(sptt_cpd *c, bool bf16) {
+    const int p = bf16 ? 1 : 0;
+    if (!c->graph[p]) {
+        const sptt_sched *sched = c->has_sched ? &c->sched : nullptr;
+        for (int n = 0; n < c->N; ++n) SPTT_TRY(mttkrp_prepare(c->csf[n], sched, c->st));
+        SPTT_CUDA(cudaStreamSynchronize(c->st));
+        cudaGraph_t g = nullptr;
+        SPTT_CUDA(cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
+        const int64_t l0 = sptt_debug_launch_count();
+        sptt_status s = run_iteration(c, bf16);
+        const int64_t l1 = sptt_debug_launch_count();
+        cudaError_t e = cudaStreamEndCapture(c->st, &g);
+        if (s != SPTT_OK) {
+            if (g) cudaGraphDestroy(g);
+            return s;
+        }
+        if (e != cudaSuccess) return cuda_error(e, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&c->graph[p], g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return cuda_error(e, "cudaGraphInstantiate");
+        c->graph_kernels[p] = l1 - l0;
+        count_launch(-(l1 - l0));  // capture launched nothing; replays are counted below
+    }
+    SPTT_CUDA(cudaGraphLaunch(c->graph[p], c->st));
+    count_launch(c->graph_kernels[p]);
+    return SPTT_OK;
+}
+
+sptt_status step(sptt_cpd *c, bool bf16) {
+    if (c->opts.use_graph && !c->opts.profile && c->st != nullptr) SPTT_TRY(run_iteration_graph(c, bf16));
+    else SPTT_TRY(run_iteration(c, bf16));
     c->iters += 1;
     return SPTT_OK;
 }
@@ -149,6 +192,9 @@ void destroy(sptt_cpd *c) {
     if (c->M) dev_free(c->M, c->st);
     if (c->normx2) dev_free(c->normx2, c->st);
     if (c->fits) dev_free(c->fits, c->st);
+    if (c->iter_dev) dev_free(c->iter_dev, c->st);
+    for (int p = 0; p < 2; ++p)
+        if (c->graph[p]) cudaGraphExecDestroy(c->graph[p]);
     dense_work_free(&c->w, c->st);
     for (auto &r : c->pending) {
         cudaEventDestroy(r.a);
@@ -219,6 +265,8 @@ extern "C" sptt_status sptt_cpd_create(const sptt_coo *coo, int32_t rank, const 
     SPTT_TRY(dev_alloc_n(&c->normx2, 1, st));
     SPTT_TRY(dev_alloc_n(&c->fits, kFitHistory, st));
     SPTT_TRY(fill_zero_launch(c->fits, kFitHistory * sizeof(double), st));
+    SPTT_TRY(dev_alloc_n(&c->iter_dev, 1, st));
+    SPTT_TRY(fill_zero_launch(c->iter_dev, sizeof(int64_t), st));
     SPTT_TRY(dense_work_alloc(&c->w, rank, c->ld, max_rows, st));
     const sptt_csf *c0 = c->csf[0];
     SPTT_TRY(sumsq_launch(c0->vals, c0->nfibs[c0->nmodes - 1], c->normx2, st));
@@ -248,6 +296,7 @@ extern "C" sptt_status sptt_cpd_init(sptt_cpd *c, const float *const *init) {
     }
     SPTT_TRY(fill_zero_launch(c->w.branch, 2 * sizeof(int32_t), st));
     SPTT_TRY(fill_zero_launch(c->fits, kFitHistory * sizeof(double), st));
+    SPTT_TRY(fill_zero_launch(c->iter_dev, sizeof(int64_t), st));
     c->iters = 0;
     SPTT_TRY(resolve_timers(c));
     for (int i = 0; i < SPTT_NUM_TIMERS; ++i) {
@@ -262,7 +311,7 @@ static sptt_status iterate(sptt_cpd *c, int32_t iters, double tol, bool bf16, in
     double prev = 0.0;
     if (tol > 0.0 && c->iters > 0) SPTT_TRY(read_fit(c, c->iters - 1, &prev));
     for (int32_t i = 0; i < iters; ++i) {
-        SPTT_TRY(run_iteration(c, bf16));
+        SPTT_TRY(step(c, bf16));
         if (done) *done = i + 1;
         if (tol > 0.0) {
             double f = 0.0;

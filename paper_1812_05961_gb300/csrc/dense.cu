@@ -402,10 +402,12 @@ __global__ void normalize_kernel(float *__restrict__ A, __nv_bfloat16 *__restric
     }
 }
 
-// fit = 1 - sqrt(max(0, |X|^2 + lambda^T (*_m G_m) lambda - 2 inner)) / |X|
+// fit = 1 - sqrt(max(0, |X|^2 + lambda^T (*_m G_m) lambda - 2 inner)) / |X|,
+// stored at ring[*counter % ring_len]; the counter is then advanced, so the
+// same launch can be replayed from a captured graph.
 __global__ void fit_kernel(GramPtrs g, int nmodes, int rank, const double *__restrict__ normx2,
                            const double *__restrict__ lambda, const double *__restrict__ inner,
-                           double *__restrict__ fit) {
+                           double *__restrict__ ring, int ring_len, int64_t *__restrict__ counter) {
     __shared__ double red[32];
     double s = 0.0;
     for (int e = threadIdx.x; e < rank * rank; e += blockDim.x) {
@@ -418,7 +420,9 @@ __global__ void fit_kernel(GramPtrs g, int nmodes, int rank, const double *__res
         const double nx = *normx2;
         double r2 = nx + s - 2.0 * (*inner);
         if (r2 < 0.0) r2 = 0.0;
-        *fit = (nx == 0.0) ? (r2 == 0.0 ? 1.0 : 0.0) : 1.0 - sqrt(r2) / sqrt(nx);
+        const int64_t it = *counter;
+        ring[it % ring_len] = (nx == 0.0) ? (r2 == 0.0 ? 1.0 : 0.0) : 1.0 - sqrt(r2) / sqrt(nx);
+        *counter = it + 1;
     }
 }
 
@@ -633,11 +637,11 @@ sptt_status normalize_launch(float *A, __nv_bfloat16 *A_bf16, int64_t rows, Dens
     return SPTT_OK;
 }
 
-sptt_status fit_launch(double *const *grams, int32_t nmodes, const double *normx2, DenseWork *w, double *fit_out,
-                       cudaStream_t st) {
+sptt_status fit_launch(double *const *grams, int32_t nmodes, const double *normx2, DenseWork *w, double *ring,
+                       int32_t ring_len, int64_t *counter, cudaStream_t st) {
     GramPtrs g{};
     for (int m = 0; m < nmodes; ++m) g.p[m] = grams[m];
-    fit_kernel<<<1, kThreads, 0, st>>>(g, nmodes, w->rank, normx2, w->lambda, w->inner, fit_out);
+    fit_kernel<<<1, kThreads, 0, st>>>(g, nmodes, w->rank, normx2, w->lambda, w->inner, ring, ring_len, counter);
     SPTT_CHECK_LAUNCH("fit_kernel");
     return SPTT_OK;
 }

@@ -20,7 +20,7 @@ constexpr int kNumSMs = 152;  // GB300: 2 dies x 76 SMs (queried at run time whe
 sptt_status set_error(sptt_status s, const std::string &msg);
 sptt_status cuda_error(cudaError_t e, const char *what);
 void clear_error();
-void count_launch();
+void count_launch(int64_t n = 1);
 
 #define SPTT_CUDA(call)                                        \
     do {                                                       \
@@ -143,6 +143,9 @@ sptt_status coo_to_device(const sptt_coo *coo, cudaStream_t st, DevCoo *out);
 // ---------------------------------------------------------------------------
 sptt_status mttkrp_launch(sptt_csf *csf, const void *const *factors, int32_t dtype, int32_t ld,
                           float *out, const sptt_sched *sched, cudaStream_t st);
+// Builds the work partition the launch will use (allocates on first use, so
+// call it before any stream capture).
+sptt_status mttkrp_prepare(sptt_csf *csf, const sptt_sched *sched, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // Dense kernels (dense.cu)
@@ -176,9 +179,10 @@ sptt_status finalize_launch(double *G_n, DenseWork *w, cudaStream_t st);
 // A *= 1/lambda (columns), optional BF16 shadow.
 sptt_status normalize_launch(float *A, __nv_bfloat16 *A_bf16, int64_t rows, DenseWork *w,
                              cudaStream_t st);
-// fit = 1 - sqrt(max(0, normx2 + lambda^T (*G) lambda - 2 inner)) / sqrt(normx2)
+// fit = 1 - sqrt(max(0, normx2 + lambda^T (*G) lambda - 2 inner)) / sqrt(normx2),
+// written to ring[*counter % ring_len], then ++*counter (device side).
 sptt_status fit_launch(double *const *grams, int32_t nmodes, const double *normx2, DenseWork *w,
-                       double *fit_out, cudaStream_t st);
+                       double *ring, int32_t ring_len, int64_t *counter, cudaStream_t st);
 sptt_status sumsq_launch(const float *vals, int64_t n, double *out, cudaStream_t st);
 sptt_status init_factor_launch(uint64_t seed, int32_t mode, int64_t rows, int32_t rank,
                                int32_t ld, float *A, cudaStream_t st);

@@ -125,13 +125,13 @@ struct Raw<__nv_bfloat16> {
 // gathers in flight instead of walking one dependent load at a time. Rows of
 // fibers at levels above N-2 are requested when the fiber opens and used when
 // it closes.
-template <int NM, typename T, int MINB>
+template <int NM, typename T, int B, int MINB>
 __global__ void __launch_bounds__(256, MINB) mttkrp_flag_kernel(const MttkrpArgs a) {
     using Rw = Raw<T>;
     constexpr int VEC = Rw::VEC;
     constexpr int NL = NM - 1;  // accumulator levels 0..NM-2
     constexpr int LF = NM - 2;  // level of the leaves' parent fibers
-    constexpr int B = 8;
+    static_assert(B == 4 || B == 8, "batch of 4 or 8 leaves");
     const int lane = threadIdx.x & 31;
     const int gi = lane / a.G;
     const int gl = lane - gi * a.G;
@@ -159,13 +159,26 @@ __global__ void __launch_bounds__(256, MINB) mttkrp_flag_kernel(const MttkrpArgs
         bool first_slice = true;
 
         for (int64_t kb = k0; kb < k1; kb += B) {
-            const float4 va = __ldg(reinterpret_cast<const float4 *>(a.vals + kb));
-            const float4 vb = __ldg(reinterpret_cast<const float4 *>(a.vals + kb + 4));
-            const int4 ia = __ldg(reinterpret_cast<const int4 *>(a.fids[NM - 1] + kb));
-            const int4 ib = __ldg(reinterpret_cast<const int4 *>(a.fids[NM - 1] + kb + 4));
-            const uint2 lw = __ldg(reinterpret_cast<const uint2 *>(a.lvl + kb));
-            const float v[B] = {va.x, va.y, va.z, va.w, vb.x, vb.y, vb.z, vb.w};
-            const int32_t li[B] = {ia.x, ia.y, ia.z, ia.w, ib.x, ib.y, ib.z, ib.w};
+            float v[B];
+            int32_t li[B];
+            uint32_t lw[2] = {0u, 0u};
+            {
+                const float4 va = __ldg(reinterpret_cast<const float4 *>(a.vals + kb));
+                const int4 ia = __ldg(reinterpret_cast<const int4 *>(a.fids[NM - 1] + kb));
+                v[0] = va.x; v[1] = va.y; v[2] = va.z; v[3] = va.w;
+                li[0] = ia.x; li[1] = ia.y; li[2] = ia.z; li[3] = ia.w;
+                if (B == 8) {
+                    const float4 vb = __ldg(reinterpret_cast<const float4 *>(a.vals + kb + 4));
+                    const int4 ib = __ldg(reinterpret_cast<const int4 *>(a.fids[NM - 1] + kb + 4));
+                    v[4 % B] = vb.x; v[5 % B] = vb.y; v[6 % B] = vb.z; v[7 % B] = vb.w;
+                    li[4 % B] = ib.x; li[5 % B] = ib.y; li[6 % B] = ib.z; li[7 % B] = ib.w;
+                    const uint2 l2 = __ldg(reinterpret_cast<const uint2 *>(a.lvl + kb));
+                    lw[0] = l2.x;
+                    lw[1] = l2.y;
+                } else {
+                    lw[0] = __ldg(reinterpret_cast<const uint32_t *>(a.lvl + kb));
+                }
+            }
             const int nvalid = (k1 - kb < B) ? (int)(k1 - kb) : B;
             uint4 x[B];
 #pragma unroll
@@ -175,7 +188,7 @@ __global__ void __launch_bounds__(256, MINB) mttkrp_flag_kernel(const MttkrpArgs
             uint32_t sm = 0;
 #pragma unroll
             for (int j = 0; j < B; ++j) {
-                const uint32_t d = ((j < 4 ? lw.x : lw.y) >> (8 * (j & 3))) & 0xffu;
+                const uint32_t d = (lw[j >> 2] >> (8 * (j & 3))) & 0xffu;
                 if (j < nvalid && d <= (uint32_t)LF && (kb + j) != k0) sm |= 1u << j;
             }
             uint4 nr[B];
@@ -191,7 +204,7 @@ __global__ void __launch_bounds__(256, MINB) mttkrp_flag_kernel(const MttkrpArgs
             for (int j = 0; j < B; ++j) {
                 if (j >= nvalid) break;
                 if ((sm >> j) & 1u) {
-                    const int d = (int)(((j < 4 ? lw.x : lw.y) >> (8 * (j & 3))) & 0xffu);
+                    const int d = (int)((lw[j >> 2] >> (8 * (j & 3))) & 0xffu);
                     if (LF >= 1) {
                         float r[VEC];
                         Rw::widen(rowc[LF], r);
@@ -331,8 +344,15 @@ __global__ void __launch_bounds__(256) mttkrp_root_kernel(const MttkrpArgs a) {
 
 template <int NM, typename T>
 sptt_status launch_nm(const MttkrpArgs &a, int block, int variant, cudaStream_t st) {
-    auto kern = variant == 1 ? mttkrp_root_kernel<NM, T>
-                : (variant == 2 ? mttkrp_flag_kernel<NM, T, 2> : mttkrp_flag_kernel<NM, T, 1>);
+    void (*kern)(const MttkrpArgs) = nullptr;
+    switch (variant) {
+        case 1: kern = mttkrp_root_kernel<NM, T>; break;
+        case 2: kern = mttkrp_flag_kernel<NM, T, 8, 2>; break;
+        case 3: kern = mttkrp_flag_kernel<NM, T, 4, 3>; break;
+        case 4: kern = mttkrp_flag_kernel<NM, T, 4, 4>; break;
+        case 5: kern = mttkrp_flag_kernel<NM, T, 8, 1>; break;
+        default: kern = mttkrp_flag_kernel<NM, T, 8, 2>; break;
+    }
     int per_sm = 0;
     SPTT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, 0));
     if (per_sm < 1) per_sm = 1;
@@ -359,6 +379,14 @@ sptt_status launch_t(int nm, const MttkrpArgs &a, int block, int variant, cudaSt
 
 }  // namespace
 
+constexpr int32_t kDefaultChunk = 128;
+
+sptt_status mttkrp_prepare(sptt_csf *csf, const sptt_sched *sched, cudaStream_t st) {
+    const int32_t chunk = (sched && sched->chunk) ? sched->chunk : kDefaultChunk;
+    if (csf->nfibs[csf->nmodes - 1] == 0) return SPTT_OK;
+    return csf_ensure_partition(csf, chunk, st);
+}
+
 sptt_status mttkrp_launch(sptt_csf *csf, const void *const *factors, int32_t dtype, int32_t ld,
                           float *out, const sptt_sched *sched, cudaStream_t st) {
     const int N = csf->nmodes;
@@ -367,7 +395,7 @@ sptt_status mttkrp_launch(sptt_csf *csf, const void *const *factors, int32_t dty
     SPTT_TRY(fill_zero_launch(out, (size_t)rows * ld * sizeof(float), st));
     const int64_t nnz = csf->nfibs[N - 1];
     if (nnz == 0) return SPTT_OK;
-    int32_t chunk = (sched && sched->chunk) ? sched->chunk : 128;
+    int32_t chunk = (sched && sched->chunk) ? sched->chunk : kDefaultChunk;
     int block = (sched && sched->block) ? sched->block : 256;
     const int variant = sched ? sched->variant : 0;
     SPTT_TRY(csf_ensure_partition(csf, chunk, st));
@@ -418,8 +446,8 @@ extern "C" sptt_status sptt_mttkrp(const sptt_csf *csf, const void *const *facto
             return set_error(SPTT_ERR_BAD_ARG, "sched->chunk must be a power of two in [16, 4096]");
         if (sched->block && (sched->block < 32 || sched->block > 256 || sched->block % 32))
             return set_error(SPTT_ERR_BAD_ARG, "sched->block must be a multiple of 32 in [32, 256]");
-        if (sched->variant < 0 || sched->variant > 2)
-            return set_error(SPTT_ERR_BAD_ARG, "sched->variant must be in [0, 2]");
+        if (sched->variant < 0 || sched->variant > 5)
+            return set_error(SPTT_ERR_BAD_ARG, "sched->variant must be in [0, 5]");
     }
     return mttkrp_launch(const_cast<sptt_csf *>(csf), factors, factor_dtype, ld, out, sched,
                          reinterpret_cast<cudaStream_t>(stream));

@@ -183,3 +183,23 @@ def test_profile_timers(cuda_device):
     tm = cpd.timers()
     assert tm["mttkrp"][1] == 9 and tm["cpd_fit"][1] == 3
     assert all(v[0] > 0 for v in tm.values())
+
+
+def test_graph_replay_matches_stream_launches(cuda_device):
+    dims = (150, 120, 90, 40)
+    t = make(dims, 30000, seed=12)
+    di, dv = to_dev(t, cuda_device)
+    a = sptt.Cpd(dims, di, dv, 12, seed=2).init()
+    b = sptt.Cpd(dims, di, dv, 12, seed=2, use_graph=1).init()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):  # graphs need a non-default stream
+        c = sptt.Cpd(dims, di, dv, 12, seed=2, use_graph=1).init()
+        l0 = sptt.sptt_debug_launch_count()
+        c.iterate(5)
+        l1 = sptt.sptt_debug_launch_count()
+    a.iterate(5)
+    b.iterate(5)
+    fa, fc = a.fit_history(), c.fit_history()
+    np.testing.assert_allclose(fc, fa, atol=1e-9)
+    np.testing.assert_allclose(b.fit_history(), fa, atol=1e-9)
+    assert l1 - l0 >= 5 * (4 * 6 + 1)  # every replayed kernel is counted

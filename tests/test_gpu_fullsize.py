@@ -1,0 +1,159 @@
+"""Parity at the benchmark's full sizes, in the launch configuration bench.py
+times (default schedule):
+
+  * the 3-mode power-law tensor of NETFLIX shape (480,000 x 18,000 x 2,000,
+    1e8 non-zeros), R = 16: CSF invariants that pin it to the sorted input,
+    MTTKRP of every root on sampled rows (the heaviest rows included) against
+    the oracle, and one CP-ALS iteration's fit against the oracle's;
+  * the 4-mode power-law tensor (2e6 x 5e5 x 5e4 x 1e3, 1.5e8 non-zeros),
+    R = 64: sampled MTTKRP rows with FP32 and BF16 gathers, and the
+    mixed-precision run (25 BF16 iterations + 1 FP32 refinement sweep) against
+    the FP32 run, |delta fit| <= 1e-4.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1812_05961_gb300 as sptt
+import tensorgen
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def p3(cuda_device):
+    t = tensorgen.powerlaw3(seed=2, device=cuda_device)
+    torch.cuda.empty_cache()
+    return t
+
+
+def _sample_rows(inds_mode, dim, k, seed):
+    counts = torch.bincount(inds_mode.long(), minlength=dim)
+    heavy = torch.topk(counts, 8).indices
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    rnd = torch.randint(0, dim, (k,), generator=g)
+    return torch.unique(torch.cat([heavy.cpu(), rnd])).numpy()
+
+
+def _csf_invariants(c, t, dev):
+    """The CSF is the sorted, duplicate-free input: fptr strictly increasing
+    and closed, children strictly increasing within each parent, leaf count =
+    nnz, and an order-independent checksum of (coords, value) equal to the
+    input's."""
+    n = c.nmodes
+    levels = []
+    for l in range(n):
+        fptr = torch.empty(c.nfibs[l] + 1 if l < n - 1 else 1, dtype=torch.int32, device=dev)
+        fids = torch.empty(c.nfibs[l], dtype=torch.int32, device=dev)
+        vals = torch.empty(c.nfibs[l], dtype=torch.float32, device=dev) if l == n - 1 else None
+        st = sptt.lib().sptt_csf_copy_level(c.handle, l, fptr.data_ptr() if l < n - 1 else None,
+                                            fids.data_ptr(), None if vals is None else vals.data_ptr(),
+                                            torch.cuda.current_stream().cuda_stream)
+        assert st == 0
+        levels.append((fptr, fids, vals))
+    assert c.nfibs[-1] == t.nnz
+    coords = [None] * n
+    coords[n - 1] = levels[n - 1][1].long()
+    owner = torch.arange(t.nnz, device=dev)
+    for l in range(n - 2, -1, -1):
+        fptr, fids, _ = levels[l]
+        d = torch.diff(fptr.long())
+        assert int(fptr[0]) == 0 and int(fptr[-1]) == c.nfibs[l + 1] and bool((d > 0).all())
+        parent = torch.repeat_interleave(torch.arange(c.nfibs[l], device=dev), d)
+        child = levels[l + 1][1].long()
+        same = parent[1:] == parent[:-1]
+        assert bool((child[1:][same] > child[:-1][same]).all())
+        owner = parent[owner]
+        coords[l] = fids.long()[owner]
+    assert bool((torch.diff(levels[0][1].long()) > 0).all())
+
+    def checksum(cols, vals):
+        h = torch.zeros_like(cols[0])
+        for x in cols:
+            h = (h * 1_000_003 + x) % (2 ** 61 - 1)
+        return int(((h * 31 + vals.double().mul(1e6).round().long()) % (2 ** 61 - 1)).sum())
+
+    by_mode = [None] * n
+    for l, m in enumerate(c.order):
+        by_mode[m] = coords[l]
+    assert checksum(by_mode, levels[n - 1][2]) == checksum([x.long() for x in t.inds], t.vals)
+
+
+def test_powerlaw3_csf_and_mttkrp_sampled(p3, cuda_device):
+    t = p3
+    R = 16
+    g = torch.Generator(device=cuda_device).manual_seed(5)
+    F = [torch.rand(d, R, device=cuda_device, generator=g) for d in t.dims]
+    inds_np = [x.cpu().numpy() for x in t.inds]
+    vals_np = t.vals.cpu().numpy()
+    Fo = [f.double().cpu().numpy() for f in F]
+    for root in range(3):
+        c = sptt.Csf(t.dims, t.inds, t.vals, root)
+        _csf_invariants(c, t, cuda_device)
+        M = c.mttkrp(F).cpu().double().numpy()
+        rows = _sample_rows(t.inds[root], t.dims[root], 48, root)
+        Mo, Ma = oracle.mttkrp(inds_np, vals_np, t.dims, Fo, root, with_abs=True, rows=rows)
+        err = np.abs(M[rows] - Mo[rows])
+        assert np.all(err <= 1e-5 * Ma[rows] + 1e-30), float((err / (Ma[rows] + 1e-30)).max())
+        rel = np.linalg.norm(M[rows] - Mo[rows]) / np.linalg.norm(Mo[rows])
+        assert rel <= 1e-5
+        del c
+
+
+def test_powerlaw3_one_iteration_fit(p3, cuda_device):
+    t = p3
+    R = 16
+    cpd = sptt.Cpd(t.dims, t.inds, t.vals, R, seed=1).init()
+    cpd.iterate(1)
+    fit = cpd.fit()[0]
+    inds_np = [x.cpu().numpy() for x in t.inds]
+    vals_np = t.vals.cpu().numpy()
+    ref = oracle.cpd_als(inds_np, vals_np, t.dims, R, 1, seed=1, coalesce_first=False)
+    assert abs(fit - ref["fits"][-1]) <= 1e-4, (fit, ref["fits"][-1])
+
+
+@pytest.fixture(scope="module")
+def p4(cuda_device):
+    t = tensorgen.powerlaw4(seed=3, device=cuda_device)
+    torch.cuda.empty_cache()
+    return t
+
+
+def test_powerlaw4_mttkrp_sampled_fp32_bf16(p4, cuda_device):
+    t = p4
+    R = 64
+    g = torch.Generator(device=cuda_device).manual_seed(7)
+    F = [torch.rand(d, R, device=cuda_device, generator=g) for d in t.dims]
+    Fb = [f.bfloat16() for f in F]
+    inds_np = [x.cpu().numpy() for x in t.inds]
+    vals_np = t.vals.cpu().numpy()
+    for root in range(4):
+        c = sptt.Csf(t.dims, t.inds, t.vals, root)
+        rows = _sample_rows(t.inds[root], t.dims[root], 24, root)
+        M = c.mttkrp(F).cpu().double().numpy()
+        Mb = c.mttkrp(Fb, factor_dtype=sptt.SPTT_BF16).cpu().double().numpy()
+        Mo, Ma = oracle.mttkrp(inds_np, vals_np, t.dims, [f.double().cpu().numpy() for f in F], root,
+                               with_abs=True, rows=rows)
+        assert np.all(np.abs(M[rows] - Mo[rows]) <= 1e-5 * Ma[rows] + 1e-30)
+        Mbo = oracle.mttkrp(inds_np, vals_np, t.dims, [f.double().cpu().numpy() for f in Fb], root,
+                            rows=rows)
+        assert np.linalg.norm(Mb[rows] - Mbo[rows]) <= 1e-5 * np.linalg.norm(Mbo[rows])
+        assert np.linalg.norm(Mb[rows] - Mo[rows]) <= 2e-2 * np.linalg.norm(Mo[rows])
+        del c
+
+
+def test_powerlaw4_mixed_precision_fit_matches_fp32(p4, cuda_device):
+    t = p4
+    R = 64
+    fits = {}
+    for prec in (sptt.SPTT_F32, sptt.SPTT_BF16):
+        cpd = sptt.Cpd(t.dims, t.inds, t.vals, R, seed=3, precision=prec).init()
+        if prec == sptt.SPTT_BF16:
+            cpd.iterate(25)
+            cpd.refine(1)
+        else:
+            cpd.iterate(26)
+        fits[prec] = cpd.fit()[0]
+        del cpd
+    assert abs(fits[sptt.SPTT_BF16] - fits[sptt.SPTT_F32]) <= 1e-4, fits

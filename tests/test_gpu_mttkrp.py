@@ -65,7 +65,7 @@ def test_mttkrp_padded_rank(R, ld, cuda_device):
 
 @pytest.mark.parametrize("chunk", [16, 32, 128, 512, 4096])
 @pytest.mark.parametrize("block", [64, 256])
-@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5])
 def test_mttkrp_schedules_agree(chunk, block, variant, cuda_device):
     dims = (400, 300, 200, 20)
     t = make(dims, 50003, seed=5, dist="zipf", s=1.3)
@@ -75,10 +75,10 @@ def test_mttkrp_schedules_agree(chunk, block, variant, cuda_device):
         _check(M, t, F, root, 16, 1e-5)
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5])
 @pytest.mark.parametrize("nm", [2, 3, 4, 5])
 def test_mttkrp_variants_every_order(variant, nm, cuda_device):
-    dims = (90, 70, 50, 30, 10)[:nm]
+    dims = (290, 170, 50, 30, 10)[:nm]
     t = make(dims, 20011, seed=nm, dist="zipf", s=1.2)
     for dtype, ld in ((sptt.SPTT_F32, 8), (sptt.SPTT_BF16, 16)):
         F = rand_factors(dims, ld, seed=nm + ld)
