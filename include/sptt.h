@@ -179,6 +179,26 @@ sptt_status sptt_mttkrp(const sptt_csf *csf, const void *const *factors, int32_t
 sptt_status sptt_gram(const float *A, int64_t rows, int32_t rank, int32_t ld, double *G,
                       sptt_stream stream);
 
+/*
+ * sptt_gram with no device allocation, for callers that cannot call
+ * cudaMalloc: code whose device memory is owned entirely by another
+ * allocator (a framework's caching allocator or a fixed arena), or a latency
+ * path where an allocation that may synchronise or grow a pool is not
+ * acceptable. (The paper has no counterpart; this is an interface variant.)
+ * Same arguments and result as sptt_gram. Its workspace is one static device
+ * array of 2^18 doubles (2 MiB) that every GPU loading the library holds until
+ * the process exits; no cudaMalloc, cudaFree or allocating library routine is
+ * called. The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress) and caches it, so make the first call for each
+ * device, with that device current, before any stream capture. All calls
+ * share the one array: calls that can overlap on the GPU (different streams
+ * without ordering between them) race on it and must be serialised by the
+ * caller. rank must be in [1, SPTT_MAX_RANK_ALS] (else SPTT_ERR_BAD_ARG).
+ * Asynchronous.
+ */
+sptt_status sptt_gram_noalloc(const float *A, int64_t rows, int32_t rank, int32_t ld, double *G,
+                              sptt_stream stream);
+
 /* ------------------------------------------------------------------------ */
 /* CP-ALS (Algorithm 1, N modes).                                           */
 /* ------------------------------------------------------------------------ */

@@ -86,6 +86,7 @@ def lib() -> ctypes.CDLL:
             "sptt_csf_copy_level": (_ST, [_P, _I32, _P, _P, _P, _P]),
             "sptt_mttkrp": (_ST, [_P, _P, _I32, _I32, _P, _P, _P]),
             "sptt_gram": (_ST, [_P, _I64, _I32, _I32, _P, _P]),
+            "sptt_gram_noalloc": (_ST, [_P, _I64, _I32, _I32, _P, _P]),
             "sptt_cpd_create": (_ST, [ctypes.POINTER(sptt_coo), _I32, ctypes.POINTER(sptt_opts), _P,
                                       ctypes.POINTER(_P)]),
             "sptt_cpd_free": (None, [_P]),
@@ -238,6 +239,14 @@ def sptt_gram(A: torch.Tensor, rank: int, G: Optional[torch.Tensor] = None, stre
         G = torch.empty((rank, rank), dtype=torch.float64, device=A.device)
     _check(lib().sptt_gram(A.data_ptr(), A.shape[0], rank, A.shape[1], G.data_ptr(), _stream(stream)),
            "sptt_gram")
+    return G
+
+
+def sptt_gram_noalloc(A: torch.Tensor, rank: int, G: torch.Tensor, stream=None):
+    """sptt_gram without device allocation (static device workspace; see
+    include/sptt.h). G must be a preallocated rank x rank float64 tensor."""
+    _check(lib().sptt_gram_noalloc(A.data_ptr(), A.shape[0], rank, A.shape[1], G.data_ptr(),
+                                   _stream(stream)), "sptt_gram_noalloc")
     return G
 
 
