@@ -133,7 +133,8 @@ sptt_status sptt_csf_copy_level(const sptt_csf *csf, int32_t level, int32_t *fpt
  *   chunk       non-zeros per work unit of a lane group; power of two in
  *               [16, 4096]; 0 = default
  *   block       threads per CTA (multiple of 32, <= 256); 0 = default
- *   variant     kernel variant: 0 = default; 1 = plain walk (fiber ends
+ *   variant     kernel variant: 0 = default (3 for F32 gathers, 2 for BF16);
+ *               1 = plain walk (fiber ends
  *               from fptr, one leaf at a time); 2..5 = batched walk driven by
  *               the per-leaf level flags with (batch, CTAs per SM) = (8, 2),
  *               (4, 3), (4, 4), (8, 1)
@@ -160,7 +161,10 @@ typedef struct {
  *   out       device float, dims[n] x ld row-major, overwritten (rows absent
  *             from the tensor become 0). Must not alias a factor.
  *   sched     NULL = default schedule.
- * Accumulation is FP32. Asynchronous on the stream. Errors: BAD_ARG.
+ * Accumulation is FP32 within a work chunk; a slice split over several
+ * chunks sums its chunk partials in FP64 (an FP64 workspace of dims[n] x ld
+ * is allocated on the stream and converted into out). Asynchronous on the
+ * stream. Errors: BAD_ARG, OOM.
  */
 sptt_status sptt_mttkrp(const sptt_csf *csf, const void *const *factors, int32_t factor_dtype,
                         int32_t ld, float *out, const sptt_sched *sched, sptt_stream stream);

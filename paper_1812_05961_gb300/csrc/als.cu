@@ -41,7 +41,7 @@ struct sptt_cpd {
     float *A[SPTT_MAX_MODES] = {nullptr};
     __nv_bfloat16 *Ab[SPTT_MAX_MODES] = {nullptr};
     double *G[SPTT_MAX_MODES] = {nullptr};
-    float *M = nullptr;
+    double *M = nullptr;     // MTTKRP output (FP64 accumulation)
     double *normx2 = nullptr;
     double *fits = nullptr;  // device ring of fit values, kFitHistory entries
     int64_t *iter_dev = nullptr;  // device iteration counter (indexes the ring)

@@ -89,7 +89,7 @@ __global__ void reduce_partials_kernel(const double *__restrict__ partials, int 
 // Fused post-solve: A_un = M W, plus Gram(A_un) and column dots M.A_un
 // ---------------------------------------------------------------------------
 template <int RP>
-__global__ void __launch_bounds__(kThreads) postsolve_kernel(const float *__restrict__ M, float *__restrict__ A,
+__global__ void __launch_bounds__(kThreads) postsolve_kernel(const double *__restrict__ M, float *__restrict__ A,
                                                              int64_t rows, int rank, int ld,
                                                              const float *__restrict__ Wg,
                                                              double *__restrict__ partials, int pstride) {
@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(kThreads) postsolve_kernel(const float *__rest
         for (int e = t; e < kSolveRows * RP; e += kThreads) {
             const int r = e / RP, c = e % RP;
             const int64_t i = i0 + r;
-            Mt[r][c] = (i < rows && c < rank) ? M[i * ld + c] : 0.f;
+            Mt[r][c] = (i < rows && c < rank) ? (float)M[i * ld + c] : 0.f;
         }
         __syncthreads();
         float o[RE][CE];
@@ -604,11 +604,11 @@ sptt_status normal_prep_launch(double *const *grams, int32_t nmodes, int32_t n, 
 }
 
 template <int RP>
-static void postsolve_dispatch(const float *M, float *A, int64_t rows, DenseWork *w, int pstride, cudaStream_t st) {
+static void postsolve_dispatch(const double *M, float *A, int64_t rows, DenseWork *w, int pstride, cudaStream_t st) {
     postsolve_kernel<RP><<<w->nblocks, kThreads, 0, st>>>(M, A, rows, w->rank, w->ld, w->W, w->partials, pstride);
 }
 
-sptt_status postsolve_launch(const float *M, float *A, int64_t rows, DenseWork *w, cudaStream_t st) {
+sptt_status postsolve_launch(const double *M, float *A, int64_t rows, DenseWork *w, cudaStream_t st) {
     const int rank = w->rank;
     const int pstride = rank * rank + rank;
     switch (rank_pad(rank)) {

@@ -141,8 +141,9 @@ sptt_status coo_to_device(const sptt_coo *coo, cudaStream_t st, DevCoo *out);
 // ---------------------------------------------------------------------------
 // MTTKRP (mttkrp.cu)
 // ---------------------------------------------------------------------------
+// out: dims[root] x ld FP64 (zeroed, then filled).
 sptt_status mttkrp_launch(sptt_csf *csf, const void *const *factors, int32_t dtype, int32_t ld,
-                          float *out, const sptt_sched *sched, cudaStream_t st);
+                          double *out, const sptt_sched *sched, cudaStream_t st);
 // Builds the work partition the launch will use (allocates on first use, so
 // call it before any stream capture).
 sptt_status mttkrp_prepare(sptt_csf *csf, const sptt_sched *sched, cudaStream_t st);
@@ -172,7 +173,7 @@ sptt_status gram_launch(const float *A, int64_t rows, int32_t rank, int32_t ld, 
 sptt_status normal_prep_launch(double *const *grams, int32_t nmodes, int32_t n, int32_t rank,
                                DenseWork *w, cudaStream_t st);
 // A_un = M W, Gram(A_un) and column dots M.A_un into per-block partials, then reduced.
-sptt_status postsolve_launch(const float *M, float *A, int64_t rows, DenseWork *w,
+sptt_status postsolve_launch(const double *M, float *A, int64_t rows, DenseWork *w,
                              cudaStream_t st);
 // lambda = sqrt(diag G_un); G_n = D^-1 G_un D^-1; inner = sum dots.
 sptt_status finalize_launch(double *G_n, DenseWork *w, cudaStream_t st);

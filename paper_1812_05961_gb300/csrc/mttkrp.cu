@@ -38,7 +38,7 @@ struct MttkrpArgs {
     int32_t ld;
     int32_t G;    // lanes per row
     int32_t gpw;  // lane groups per warp
-    float *out;
+    double *out;
 };
 
 template <typename T>
@@ -67,20 +67,29 @@ struct Gather<__nv_bfloat16> {
     }
 };
 
+// Output rows are FP64. A slice owned by one lane group (it starts and ends
+// inside the group's chunk) is stored; a slice cut by chunk boundaries gets
+// one FP32 partial per chunk, and those are summed with FP64 atomics, so a
+// power-law slice split over 10^5 chunks keeps FP32-of-one-chunk accuracy.
 template <int VEC>
-__device__ __forceinline__ void store_row(float *dst, const float (&a)[VEC]) {
+__device__ __forceinline__ void store_row(double *dst, const float (&a)[VEC]) {
 #pragma unroll
-    for (int i = 0; i < VEC; i += 4)
-        *reinterpret_cast<float4 *>(dst + i) = make_float4(a[i], a[i + 1], a[i + 2], a[i + 3]);
+    for (int i = 0; i < VEC; i += 2)
+        *reinterpret_cast<double2 *>(dst + i) = make_double2((double)a[i], (double)a[i + 1]);
 }
 
 template <int VEC>
-__device__ __forceinline__ void red_add_row(float *dst, const float (&a)[VEC]) {
+__device__ __forceinline__ void red_add_row(double *dst, const float (&a)[VEC]) {
 #pragma unroll
-    for (int i = 0; i < VEC; i += 4)
-        asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(dst + i), "f"(a[i]),
-                     "f"(a[i + 1]), "f"(a[i + 2]), "f"(a[i + 3])
-                     : "memory");
+    for (int i = 0; i < VEC; ++i)
+        asm volatile("red.global.add.f64 [%0], %1;" ::"l"(dst + i), "d"((double)a[i]) : "memory");
+}
+
+__global__ void f64_to_f32_kernel(const double2 *__restrict__ in, float2 *__restrict__ out, int64_t n2) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n2; i += (int64_t)gridDim.x * blockDim.x) {
+        const double2 d = in[i];
+        out[i] = make_float2((float)d.x, (float)d.y);
+    }
 }
 
 // A factor row segment as loaded (16 bytes: 4 FP32 or 8 BF16), widened to
@@ -231,7 +240,7 @@ __global__ void __launch_bounds__(256, MINB) mttkrp_flag_kernel(const MttkrpArgs
                         }
                     }
                     if (d == 0) {  // the slice is complete
-                        float *dst = a.out + (int64_t)fid0 * ld + col;
+                        double *dst = a.out + (int64_t)fid0 * ld + col;
                         if (first_slice) red_add_row<VEC>(dst, acc[0]);
                         else store_row<VEC>(dst, acc[0]);
                         first_slice = false;
@@ -313,7 +322,7 @@ __global__ void __launch_bounds__(256) mttkrp_root_kernel(const MttkrpArgs a) {
                     }
                 }
                 if (to_root) {  // the slice is complete
-                    float *dst = a.out + (int64_t)__ldg(a.fids[0] + f[0]) * ld + col;
+                    double *dst = a.out + (int64_t)__ldg(a.fids[0] + f[0]) * ld + col;
                     if (first_slice) red_add_row<VEC>(dst, acc[0]);
                     else store_row<VEC>(dst, acc[0]);
                     first_slice = false;
@@ -351,7 +360,7 @@ sptt_status launch_nm(const MttkrpArgs &a, int block, int variant, cudaStream_t 
         case 3: kern = mttkrp_flag_kernel<NM, T, 4, 3>; break;
         case 4: kern = mttkrp_flag_kernel<NM, T, 4, 4>; break;
         case 5: kern = mttkrp_flag_kernel<NM, T, 8, 1>; break;
-        default: kern = mttkrp_flag_kernel<NM, T, 8, 2>; break;
+        default: kern = mttkrp_flag_kernel<NM, T, 4, 3>; break;
     }
     int per_sm = 0;
     SPTT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, 0));
@@ -388,16 +397,17 @@ sptt_status mttkrp_prepare(sptt_csf *csf, const sptt_sched *sched, cudaStream_t 
 }
 
 sptt_status mttkrp_launch(sptt_csf *csf, const void *const *factors, int32_t dtype, int32_t ld,
-                          float *out, const sptt_sched *sched, cudaStream_t st) {
+                          double *out, const sptt_sched *sched, cudaStream_t st) {
     const int N = csf->nmodes;
     const int vec = (dtype == SPTT_BF16) ? 8 : 4;
     const int64_t rows = csf->dims[csf->root];
-    SPTT_TRY(fill_zero_launch(out, (size_t)rows * ld * sizeof(float), st));
+    SPTT_TRY(fill_zero_launch(out, (size_t)rows * ld * sizeof(double), st));
     const int64_t nnz = csf->nfibs[N - 1];
     if (nnz == 0) return SPTT_OK;
     int32_t chunk = (sched && sched->chunk) ? sched->chunk : kDefaultChunk;
     int block = (sched && sched->block) ? sched->block : 256;
-    const int variant = sched ? sched->variant : 0;
+    int variant = sched ? sched->variant : 0;
+    if (variant == 0) variant = (dtype == SPTT_BF16) ? 2 : 3;  // fastest measured per gather type
     SPTT_TRY(csf_ensure_partition(csf, chunk, st));
     MttkrpArgs a{};
     for (int l = 0; l < N; ++l) {
@@ -449,6 +459,19 @@ extern "C" sptt_status sptt_mttkrp(const sptt_csf *csf, const void *const *facto
         if (sched->variant < 0 || sched->variant > 5)
             return set_error(SPTT_ERR_BAD_ARG, "sched->variant must be in [0, 5]");
     }
-    return mttkrp_launch(const_cast<sptt_csf *>(csf), factors, factor_dtype, ld, out, sched,
-                         reinterpret_cast<cudaStream_t>(stream));
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const int64_t rows = csf->dims[csf->root];
+    DevBuf acc;  // FP64 accumulation buffer, converted into out
+    SPTT_TRY(acc.alloc<double>((size_t)rows * ld, st));
+    SPTT_TRY(mttkrp_launch(const_cast<sptt_csf *>(csf), factors, factor_dtype, ld, acc.as<double>(), sched, st));
+    const int64_t n2 = rows * ld / 2;
+    if (n2 > 0) {
+        int64_t grid = (n2 + 255) / 256;
+        const int64_t cap = (int64_t)device_sm_count() * 8;
+        if (grid > cap) grid = cap;
+        f64_to_f32_kernel<<<(unsigned)grid, 256, 0, st>>>(reinterpret_cast<const double2 *>(acc.as<double>()),
+                                                          reinterpret_cast<float2 *>(out), n2);
+        SPTT_CHECK_LAUNCH("f64_to_f32_kernel");
+    }
+    return SPTT_OK;
 }
