@@ -322,6 +322,57 @@ sptt_status sptt_cpd_als(const sptt_coo *coo, int32_t rank, int32_t max_iters, d
                          const sptt_opts *opts, sptt_stream stream, float *const *factors_out,
                          double *lambda_out, double *fit_out, int32_t *iters_out);
 
+/* ------------------------------------------------------------------------ */
+/* Batched CP-ALS: many small tensors in one persistent launch.             */
+/* ------------------------------------------------------------------------ */
+
+typedef struct sptt_batch sptt_batch;
+
+/*
+ * Prepare CP-ALS (Algorithm 1) for `count` independent tensors (each 2..4
+ * modes, any sizes) with one rank in [1, 32] (else SPTT_ERR_UNSUPPORTED):
+ * builds every tensor's CSF per mode, allocates factors and workspace, and
+ * lays out global work lists (MTTKRP chunks and row tiles of all tensors back
+ * to back). opts: seed (tensor t is initialised from seed + t), use_graph
+ * (replay runs from a captured CUDA graph), sched (chunk size). Synchronises.
+ */
+sptt_status sptt_batch_create(const sptt_coo *coos, int32_t count, int32_t rank, const sptt_opts *opts,
+                              sptt_stream stream, sptt_batch **out);
+void sptt_batch_free(sptt_batch *batch);
+
+/* U(0,1) Philox initial factors for every tensor (as sptt_cpd_init with
+ * seed opts.seed + t) and their Grams; resets the fit history. */
+sptt_status sptt_batch_init(sptt_batch *batch);
+
+/*
+ * Run `iters` ALS iterations of every tensor in ONE cooperative persistent
+ * kernel launch (phases separated by grid barriers whose waits are bounded in
+ * time). Synchronises and returns SPTT_ERR_TIMEOUT if a barrier wait ran out
+ * (the kernel then stops early; the results are invalid).
+ */
+sptt_status sptt_batch_run(sptt_batch *batch, int32_t iters);
+
+/* The last min(cap, iterations run, 4096) fits of tensor t, oldest first. */
+sptt_status sptt_batch_fit_history(sptt_batch *batch, int32_t t, double *fits, int32_t cap, int32_t *count);
+
+/* Factor `mode` of tensor t (dims x rank floats, host or device) and its
+ * lambda (rank doubles). Synchronise. */
+sptt_status sptt_batch_factor(sptt_batch *batch, int32_t t, int32_t mode, float *dst);
+sptt_status sptt_batch_lambda(sptt_batch *batch, int32_t t, double *lambda);
+
+/* Launch shape: grid (CTAs), and per mode position the number of MTTKRP
+ * chunks and row tiles in the global lists (arrays of SPTT_MAX_MODES; any
+ * output may be NULL). */
+sptt_status sptt_batch_info(sptt_batch *batch, int32_t *grid, int64_t *chunks, int64_t *tiles);
+
+/*
+ * Test hook for the bounded barrier: on the next runs, CTA `skip_block` leaves
+ * the kernel before its first barrier (so the others' waits run out), and
+ * every wait gives up after timeout_ns (<= 0: the default of 2 s).
+ * skip_block < 0 restores normal runs.
+ */
+sptt_status sptt_debug_batch_stall(sptt_batch *batch, int32_t skip_block, int64_t timeout_ns);
+
 /*
  * Fault injection for tests (host side only): the countdown-th device
  * allocation made by the library from now on fails with SPTT_ERR_OOM, as if

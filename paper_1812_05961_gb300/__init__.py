@@ -104,6 +104,15 @@ def lib() -> ctypes.CDLL:
                                    ctypes.POINTER(sptt_opts), _P, _P, _P, _P, _P]),
             "sptt_debug_fail_alloc_after": (None, [_I64]),
             "sptt_debug_launch_count": (_I64, []),
+            "sptt_batch_create": (_ST, [_P, _I32, _I32, ctypes.POINTER(sptt_opts), _P, ctypes.POINTER(_P)]),
+            "sptt_batch_free": (None, [_P]),
+            "sptt_batch_init": (_ST, [_P]),
+            "sptt_batch_run": (_ST, [_P, _I32]),
+            "sptt_batch_fit_history": (_ST, [_P, _I32, _P, _I32, _P]),
+            "sptt_batch_factor": (_ST, [_P, _I32, _I32, _P]),
+            "sptt_batch_lambda": (_ST, [_P, _I32, _P]),
+            "sptt_batch_info": (_ST, [_P, _P, _P, _P]),
+            "sptt_debug_batch_stall": (_ST, [_P, _I32, _I64]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -355,6 +364,61 @@ def sptt_debug_launch_count() -> int:
     return lib().sptt_debug_launch_count()
 
 
+def sptt_batch_create(tensors, rank: int, stream=None, **opts):
+    """tensors: list of (dims, inds, vals). Returns (handle, keepalive)."""
+    coos = [_Coo(d, i, v) for (d, i, v) in tensors]
+    arr = (sptt_coo * len(coos))(*[c.c for c in coos])
+    o, keep = _opts(**opts)
+    out = ctypes.c_void_p()
+    _check(lib().sptt_batch_create(ctypes.cast(arr, ctypes.c_void_p), len(coos), rank, ctypes.byref(o),
+                                   _stream(stream), ctypes.byref(out)), "sptt_batch_create")
+    del keep, coos
+    return out.value
+
+
+def sptt_batch_free(b: int):
+    lib().sptt_batch_free(b)
+
+
+def sptt_batch_init(b: int):
+    _check(lib().sptt_batch_init(b), "sptt_batch_init")
+
+
+def sptt_batch_run(b: int, iters: int):
+    _check(lib().sptt_batch_run(b, iters), "sptt_batch_run")
+
+
+def sptt_batch_fit_history(b: int, t: int, cap: int = 4096):
+    buf = (ctypes.c_double * cap)()
+    n = ctypes.c_int32()
+    _check(lib().sptt_batch_fit_history(b, t, buf, cap, ctypes.byref(n)), "sptt_batch_fit_history")
+    return list(buf[:n.value])
+
+
+def sptt_batch_factor(b: int, t: int, mode: int, rows: int, rank: int) -> torch.Tensor:
+    out = torch.empty((rows, rank), dtype=torch.float32)
+    _check(lib().sptt_batch_factor(b, t, mode, out.data_ptr()), "sptt_batch_factor")
+    return out
+
+
+def sptt_batch_lambda(b: int, t: int, rank: int) -> torch.Tensor:
+    out = torch.empty(rank, dtype=torch.float64)
+    _check(lib().sptt_batch_lambda(b, t, out.data_ptr()), "sptt_batch_lambda")
+    return out
+
+
+def sptt_batch_info(b: int):
+    grid = ctypes.c_int32()
+    chunks = (ctypes.c_int64 * SPTT_MAX_MODES)()
+    tiles = (ctypes.c_int64 * SPTT_MAX_MODES)()
+    _check(lib().sptt_batch_info(b, ctypes.byref(grid), chunks, tiles), "sptt_batch_info")
+    return grid.value, list(chunks), list(tiles)
+
+
+def sptt_debug_batch_stall(b: int, skip_block: int, timeout_ns: int):
+    _check(lib().sptt_debug_batch_stall(b, skip_block, timeout_ns), "sptt_debug_batch_stall")
+
+
 # ---------------------------------------------------------------------------
 # Owning wrappers
 # ---------------------------------------------------------------------------
@@ -382,6 +446,45 @@ class Csf:
     def close(self):
         if self.handle:
             sptt_csf_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Batched CP-ALS of many small tensors (freed with the object)."""
+
+    def __init__(self, tensors, rank: int, stream=None, **opts):
+        self.dims = [list(map(int, d)) for (d, _, _) in tensors]
+        self.rank = rank
+        self.handle = sptt_batch_create(tensors, rank, stream, **opts)
+
+    def init(self):
+        sptt_batch_init(self.handle)
+        return self
+
+    def run(self, iters: int):
+        sptt_batch_run(self.handle, iters)
+
+    def fit_history(self, t: int):
+        return sptt_batch_fit_history(self.handle, t)
+
+    def factor(self, t: int, mode: int):
+        return sptt_batch_factor(self.handle, t, mode, self.dims[t][mode], self.rank)
+
+    def lam(self, t: int):
+        return sptt_batch_lambda(self.handle, t, self.rank)
+
+    def info(self):
+        return sptt_batch_info(self.handle)
+
+    def close(self):
+        if self.handle:
+            sptt_batch_free(self.handle)
             self.handle = None
 
     def __del__(self):

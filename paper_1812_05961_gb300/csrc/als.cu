@@ -41,7 +41,8 @@ struct sptt_cpd {
     float *A[SPTT_MAX_MODES] = {nullptr};
     __nv_bfloat16 *Ab[SPTT_MAX_MODES] = {nullptr};
     double *G[SPTT_MAX_MODES] = {nullptr};
-    double *M = nullptr;     // MTTKRP output (FP64 accumulation)
+    float *M = nullptr;      // MTTKRP output, compact (one row per slice)
+    double *Mh = nullptr;    // FP64 rows of the heavy slices
     double *normx2 = nullptr;
     double *fits = nullptr;  // device ring of fit values, kFitHistory entries
     int64_t *iter_dev = nullptr;  // device iteration counter (indexes the ring)
@@ -113,20 +114,26 @@ sptt_status run_iteration(sptt_cpd *c, bool bf16) {
     for (int n = 0; n < N; ++n) {
         {
             Timed t(c, 0);
-            SPTT_TRY(mttkrp_launch(c->csf[n], fac, bf16 ? SPTT_BF16 : SPTT_F32, c->ld, c->M, sched, c->st));
+            SPTT_TRY(mttkrp_launch(c->csf[n], fac, bf16 ? SPTT_BF16 : SPTT_F32, c->ld, c->M, c->Mh, sched, c->st));
         }
         {
             Timed t(c, 1);
             SPTT_TRY(normal_prep_launch(c->G, N, n, c->rank, &c->w, c->st));
         }
+        const sptt_csf *cs = c->csf[n];
         {
             Timed t(c, 2);
-            SPTT_TRY(postsolve_launch(c->M, c->A[n], c->dims[n], &c->w, c->st));
+            // rows of mode n without a slice come out zero: clear A (and its
+            // BF16 copy) before the solve writes the rows that have one
+            SPTT_TRY(fill_zero_launch(c->A[n], (size_t)c->dims[n] * c->ld * sizeof(float), c->st));
+            if (c->Ab[n])
+                SPTT_TRY(fill_zero_launch(c->Ab[n], (size_t)c->dims[n] * c->ld * sizeof(__nv_bfloat16), c->st));
+            SPTT_TRY(postsolve_launch(c->M, c->Mh, cs->hidx, cs->fids[0], c->A[n], cs->nfibs[0], &c->w, c->st));
         }
         {
             Timed t(c, 3);
             SPTT_TRY(finalize_launch(c->G[n], &c->w, c->st));
-            SPTT_TRY(normalize_launch(c->A[n], c->Ab[n], c->dims[n], &c->w, c->st));
+            SPTT_TRY(normalize_launch(c->A[n], c->Ab[n], cs->fids[0], cs->nfibs[0], &c->w, c->st));
         }
     }
     {
@@ -190,6 +197,7 @@ void destroy(sptt_cpd *c) {
         if (c->G[m]) dev_free(c->G[m], c->st);
     }
     if (c->M) dev_free(c->M, c->st);
+    if (c->Mh) dev_free(c->Mh, c->st);
     if (c->normx2) dev_free(c->normx2, c->st);
     if (c->fits) dev_free(c->fits, c->st);
     if (c->iter_dev) dev_free(c->iter_dev, c->st);
@@ -249,10 +257,13 @@ extern "C" sptt_status sptt_cpd_create(const sptt_coo *coo, int32_t rank, const 
         SPTT_TRY(coo_to_device(coo, st, &dc));
         for (int m = 0; m < c->N; ++m) SPTT_TRY(csf_build_device(&dc.coo, m, nullptr, st, &c->csf[m]));
     }
-    int64_t max_rows = 0;
+    int64_t max_rows = 0, max_slices = 0, max_heavy = 0;
     for (int m = 0; m < c->N; ++m) {
         const int64_t rows = c->dims[m];
         if (rows > max_rows) max_rows = rows;
+        if (c->csf[m]->nfibs[0] > max_slices) max_slices = c->csf[m]->nfibs[0];
+        SPTT_TRY(mttkrp_prepare(c->csf[m], c->has_sched ? &c->sched : nullptr, st));
+        if (c->csf[m]->nheavy > max_heavy) max_heavy = c->csf[m]->nheavy;
         SPTT_TRY(dev_alloc_n(&c->A[m], (size_t)rows * c->ld, st));
         SPTT_TRY(fill_zero_launch(c->A[m], (size_t)rows * c->ld * sizeof(float), st));
         if (o.precision == SPTT_BF16) {
@@ -261,7 +272,8 @@ extern "C" sptt_status sptt_cpd_create(const sptt_coo *coo, int32_t rank, const 
         }
         SPTT_TRY(dev_alloc_n(&c->G[m], (size_t)rank * rank, st));
     }
-    SPTT_TRY(dev_alloc_n(&c->M, (size_t)max_rows * c->ld, st));
+    SPTT_TRY(dev_alloc_n(&c->M, (size_t)max_slices * c->ld, st));
+    SPTT_TRY(dev_alloc_n(&c->Mh, (size_t)max_heavy * c->ld, st));
     SPTT_TRY(dev_alloc_n(&c->normx2, 1, st));
     SPTT_TRY(dev_alloc_n(&c->fits, kFitHistory, st));
     SPTT_TRY(fill_zero_launch(c->fits, kFitHistory * sizeof(double), st));

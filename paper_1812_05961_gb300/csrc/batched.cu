@@ -1,0 +1,722 @@
+// Batched CP-ALS: many independent small tensors decomposed by one
+// persistent kernel (Algorithm 1 for each tensor), so a batch of hundreds of
+// uneven tensors costs one launch instead of tens of thousands.
+//
+// The kernel is launched cooperatively (every CTA resident) and walks the
+// same schedule for all tensors. For each iteration and each mode position
+// n, five phases separated by grid barriers:
+//   M  MTTKRP of mode n for every tensor that has it: the lane groups share
+//      one global list of work chunks (all tensors' chunks back to back), so
+//      large and small tensors are balanced together (walk.cuh);
+//   P  per tensor (one CTA each): V = Hadamard of the other Grams, W = V^+
+//      (FP64 Cholesky / pseudo-inverse, dense_dev.cuh);
+//   S  row solve A_un = M W over one global list of 32-row tiles, with the
+//      Gram of A_un and the fit's dots accumulated in FP64 (each CTA takes a
+//      contiguous run of tiles and flushes once per tensor it touches);
+//      M is cleared as it is read, ready for the next mode;
+//   F  per tensor: lambda, G_n, and (after the tensor's last mode) the fit;
+//   N  A_n *= 1/lambda over the tile list.
+//
+// The grid barrier waits are bounded: a CTA that waits longer than the
+// configured limit (globaltimer) sets the error word and the kernel returns;
+// every other CTA sees the word at its next wait and returns as well, so a
+// missing arrival ends in SPTT_ERR_TIMEOUT, never in a hung GPU.
+#include <vector>
+
+#include "dense_dev.cuh"
+#include "walk.cuh"
+
+namespace sptt {
+namespace {
+
+constexpr int kBThreads = 256;
+constexpr int kTileRows = 32;
+constexpr int kFitRing = 4096;
+
+struct BTensor {
+    int32_t nmodes;
+    int32_t pad_;
+    int64_t dims[kMaxModes];
+    walk::Args w[kMaxModes];  // per root mode (out = M)
+    const int32_t *fids0[kMaxModes];
+    int64_t nslices[kMaxModes];
+    float *A[kMaxModes];
+    double *G[kMaxModes];
+    float *M;           // compact MTTKRP output, max slices x ld, kept zero between uses
+    double *Mh;         // FP64 rows of heavy slices, max heavy x ld, kept zero between uses
+    const int32_t *hidx[kMaxModes];
+    double *gun;        // rank*rank + rank FP64 accumulators, kept zero between uses
+    float *W;           // rank*rank
+    double *lambda;     // rank
+    float *inv_lambda;  // rank
+    double *inner;      // 1
+    double *normx2;     // 1
+    double *fits;       // kFitRing
+    int32_t *branch;    // [0] pseudo-inverse updates, [1] all updates
+};
+
+struct BatchArgs {
+    const BTensor *T;
+    int32_t count, rank, ld, iters, max_modes;
+    const int64_t *chunk_prefix[kMaxModes];  // [count + 1] per mode position
+    const int64_t *tile_prefix[kMaxModes];   // [count + 1]
+    int64_t total_chunks[kMaxModes];
+    int64_t total_tiles[kMaxModes];
+    unsigned *bar;       // [0] arrivals, [1] generation
+    int32_t *err;        // error word (1 = a barrier wait timed out)
+    int64_t *it_base;    // iterations run before this launch (indexes the fit ring)
+    uint64_t timeout_ns;
+    int32_t skip_block;  // test hook: this CTA leaves before the first barrier (-1: none)
+    int32_t zero_first;  // clear A_n before its first update (rows without a slice end at 0)
+};
+
+__device__ __forceinline__ uint64_t globaltimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Grid barrier with a bounded wait. Returns false (on every thread of the
+// CTA) when the error word is set, by this CTA or another.
+__device__ bool grid_barrier(const BatchArgs &a) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *vgen = a.bar + 1;
+        volatile int32_t *verr = a.err;
+        int ok = 1;
+        const unsigned g = *vgen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(a.bar, 1u) + 1u;
+        if (arrived == gridDim.x) {
+            a.bar[0] = 0u;  // reset before release: nobody re-arrives until gen moves
+            __threadfence();
+            atomicAdd(a.bar + 1, 1u);
+        } else {
+            const uint64_t t0 = globaltimer();
+            while (*vgen == g) {
+                if (*verr) { ok = 0; break; }
+                if (globaltimer() - t0 > a.timeout_ns) {
+                    atomicOr(a.err, 1);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(256);
+            }
+        }
+        __threadfence();
+        s_ok = ok && (*verr == 0);
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// index t with prefix[t] <= x < prefix[t + 1]
+__device__ __forceinline__ int find_owner(const int64_t *prefix, int count, int64_t x) {
+    int lo = 0, hi = count;  // prefix[lo] <= x < prefix[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(prefix + mid) <= x) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+template <int RP>
+struct SolveSmem {
+    float W[RP][RP + 1];
+    float Mt[kTileRows][RP + 1];
+    float At[kTileRows][RP + 1];
+};
+
+template <int RP>
+__device__ void solve_phase(const BatchArgs &a, int n, SolveSmem<RP> &sm) {
+    constexpr int E = RP / 16;
+    constexpr int CE = RP / 16;
+    constexpr int RE = kTileRows / 16;
+    const int t = threadIdx.x, tr = t / 16, tc = t % 16;
+    const int rank = a.rank, ld = a.ld;
+    const int64_t total = a.total_tiles[n];
+    const int64_t per = (total + gridDim.x - 1) / gridDim.x;
+    const int64_t g0 = (int64_t)blockIdx.x * per;
+    const int64_t g1 = (g0 + per < total) ? g0 + per : total;
+    int cur = -1;
+    double accG[E][E];
+    double accD = 0.0;
+#pragma unroll
+    for (int x = 0; x < E; ++x)
+#pragma unroll
+        for (int y = 0; y < E; ++y) accG[x][y] = 0.0;
+    auto flush = [&](int tt) {
+        double *gun = a.T[tt].gun;
+#pragma unroll
+        for (int x = 0; x < E; ++x)
+#pragma unroll
+            for (int y = 0; y < E; ++y) {
+                const int r = tr * E + x, c = tc * E + y;
+                if (r < rank && c < rank) atomicAdd(gun + r * rank + c, accG[x][y]);
+                accG[x][y] = 0.0;
+            }
+        if (t < rank) atomicAdd(gun + rank * rank + t, accD);
+        accD = 0.0;
+    };
+    for (int64_t gt = g0; gt < g1; ++gt) {
+        const int tt = find_owner(a.tile_prefix[n], a.count, gt);
+        const BTensor &T = a.T[tt];
+        if (tt != cur) {
+            if (cur >= 0) flush(cur);
+            cur = tt;
+            __syncthreads();
+            for (int e = t; e < RP * RP; e += blockDim.x) {
+                const int r = e / RP, c = e % RP;
+                sm.W[r][c] = (r < rank && c < rank) ? T.W[r * rank + c] : 0.f;
+            }
+        }
+        const int64_t i0 = (gt - __ldg(a.tile_prefix[n] + tt)) * kTileRows;
+        const int64_t rows = T.nslices[n];
+        float *M = T.M;
+        const int32_t *hidx = T.hidx[n];
+        for (int e = t; e < kTileRows * RP; e += blockDim.x) {
+            const int r = e / RP, c = e % RP;
+            const int64_t i = i0 + r;
+            float v = 0.f;
+            if (i < rows && c < ld) {  // read the row, then leave M zero for the next mode
+                const int32_t h = __ldg(hidx + i);
+                if (h >= 0) {
+                    if (c < rank) v = (float)T.Mh[(int64_t)h * ld + c];
+                    T.Mh[(int64_t)h * ld + c] = 0.0;
+                } else {
+                    if (c < rank) v = M[i * ld + c];
+                }
+                M[i * ld + c] = 0.f;
+            }
+            sm.Mt[r][c] = v;
+        }
+        __syncthreads();
+        float o[RE][CE];
+#pragma unroll
+        for (int y = 0; y < RE; ++y)
+#pragma unroll
+            for (int x = 0; x < CE; ++x) o[y][x] = 0.f;
+        for (int k = 0; k < RP; ++k) {
+#pragma unroll
+            for (int y = 0; y < RE; ++y) {
+                const float mk = sm.Mt[tr * RE + y][k];
+#pragma unroll
+                for (int x = 0; x < CE; ++x) o[y][x] = fmaf(mk, sm.W[k][tc * CE + x], o[y][x]);
+            }
+        }
+        const int32_t *fids0 = T.fids0[n];
+        float *A = T.A[n];
+#pragma unroll
+        for (int y = 0; y < RE; ++y) {
+            const int r = tr * RE + y;
+            const int64_t i = i0 + r;
+            const int64_t dst = (i < rows) ? (int64_t)__ldg(fids0 + i) * ld : 0;
+#pragma unroll
+            for (int x = 0; x < CE; ++x) {
+                const int c = tc * CE + x;
+                sm.At[r][c] = o[y][x];
+                if (i < rows && c < ld) A[dst + c] = o[y][x];
+            }
+        }
+        __syncthreads();
+        float s[E][E];
+#pragma unroll
+        for (int x = 0; x < E; ++x)
+#pragma unroll
+            for (int y = 0; y < E; ++y) s[x][y] = 0.f;
+        for (int r = 0; r < kTileRows; ++r)
+#pragma unroll
+            for (int x = 0; x < E; ++x)
+#pragma unroll
+                for (int y = 0; y < E; ++y) s[x][y] = fmaf(sm.At[r][tr * E + x], sm.At[r][tc * E + y], s[x][y]);
+#pragma unroll
+        for (int x = 0; x < E; ++x)
+#pragma unroll
+            for (int y = 0; y < E; ++y) accG[x][y] += (double)s[x][y];
+        if (t < RP) {
+            float d = 0.f;
+            for (int r = 0; r < kTileRows; ++r) d = fmaf(sm.Mt[r][t], sm.At[r][t], d);
+            accD += (double)d;
+        }
+        __syncthreads();
+    }
+    if (cur >= 0) flush(cur);
+}
+
+__device__ void normalize_phase(const BatchArgs &a, int n) {
+    const int ld = a.ld, rank = a.rank, qpr = ld / 4;
+    const int64_t total = a.total_tiles[n];
+    for (int64_t gt = blockIdx.x; gt < total; gt += gridDim.x) {
+        const int tt = find_owner(a.tile_prefix[n], a.count, gt);
+        const BTensor &T = a.T[tt];
+        const int64_t i0 = (gt - __ldg(a.tile_prefix[n] + tt)) * kTileRows;
+        const int64_t rows = T.nslices[n];
+        for (int e = threadIdx.x; e < kTileRows * qpr; e += blockDim.x) {
+            const int64_t i = i0 + e / qpr;
+            if (i >= rows) continue;
+            const int c0 = (e % qpr) * 4;
+            float4 *p = reinterpret_cast<float4 *>(T.A[n] + (int64_t)__ldg(T.fids0[n] + i) * ld + c0);
+            float4 v = *p;
+            v.x = (c0 + 0 < rank) ? v.x * T.inv_lambda[c0 + 0] : 0.f;
+            v.y = (c0 + 1 < rank) ? v.y * T.inv_lambda[c0 + 1] : 0.f;
+            v.z = (c0 + 2 < rank) ? v.z * T.inv_lambda[c0 + 2] : 0.f;
+            v.w = (c0 + 3 < rank) ? v.w * T.inv_lambda[c0 + 3] : 0.f;
+            *p = v;
+        }
+    }
+}
+
+template <int RP>
+__global__ void __launch_bounds__(kBThreads, 2) batched_cpals_kernel(const BatchArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    double *prep_sm = reinterpret_cast<double *>(smem);
+    SolveSmem<RP> &solve_sm = *reinterpret_cast<SolveSmem<RP> *>(smem);
+    if ((int)blockIdx.x == a.skip_block) return;  // test hook: a CTA that never arrives
+    const int64_t it0 = *a.it_base;
+    const int lane = threadIdx.x & 31;
+    const int G = a.ld / 4;
+    const int gpw = 32 / G;
+    const int gi = lane / G;
+    const int col = (lane - gi * G) * 4;
+    const int64_t gwarp = (int64_t)(blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = (int64_t)(gridDim.x * blockDim.x) >> 5;
+    const int rank = a.rank;
+
+    for (int it = 0; it < a.iters; ++it) {
+        for (int n = 0; n < a.max_modes; ++n) {
+            // M: MTTKRP of mode n over the global chunk list
+            if (gi < gpw) {
+                for (int64_t gc = gwarp * gpw + gi; gc < a.total_chunks[n]; gc += nwarps * gpw) {
+                    const int tt = find_owner(a.chunk_prefix[n], a.count, gc);
+                    const BTensor &T = a.T[tt];
+                    const int64_t c = gc - __ldg(a.chunk_prefix[n] + tt);
+                    switch (T.nmodes) {
+                        case 2: walk::flag_chunk<2, float, 4>(T.w[n], c, col); break;
+                        case 3: walk::flag_chunk<3, float, 4>(T.w[n], c, col); break;
+                        default: walk::flag_chunk<4, float, 4>(T.w[n], c, col); break;
+                    }
+                }
+            }
+            if (!grid_barrier(a)) return;
+            // P: normal equations per tensor
+            for (int tt = blockIdx.x; tt < a.count; tt += gridDim.x) {
+                const BTensor &T = a.T[tt];
+                if (T.nmodes <= n) continue;
+                if (it == 0 && a.zero_first) {
+                    float4 *p = reinterpret_cast<float4 *>(T.A[n]);
+                    const int64_t nq = T.dims[n] * a.ld / 4;
+                    for (int64_t q = threadIdx.x; q < nq; q += blockDim.x) p[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+                dense::GramPtrs g{};
+                for (int m = 0; m < T.nmodes; ++m) g.p[m] = T.G[m];
+                dense::normal_prep_body(g, T.nmodes, n, rank, T.W, T.branch, prep_sm);
+                __syncthreads();
+            }
+            if (!grid_barrier(a)) return;
+            // S: row solve + Gram + dots
+            solve_phase<RP>(a, n, solve_sm);
+            if (!grid_barrier(a)) return;
+            // F: lambda, G_n, fit
+            for (int tt = blockIdx.x; tt < a.count; tt += gridDim.x) {
+                const BTensor &T = a.T[tt];
+                if (T.nmodes <= n) continue;
+                dense::finalize_body(T.gun, rank, T.G[n], T.lambda, T.inv_lambda, T.inner);
+                __syncthreads();
+                for (int e = threadIdx.x; e < rank * rank + rank; e += blockDim.x) T.gun[e] = 0.0;
+                if (n == T.nmodes - 1) {
+                    __shared__ double red[32];
+                    double s = 0.0;
+                    for (int e = threadIdx.x; e < rank * rank; e += blockDim.x) {
+                        double h = T.lambda[e / rank] * T.lambda[e % rank];
+                        for (int m = 0; m < T.nmodes; ++m) h *= T.G[m][e];
+                        s += h;
+                    }
+                    s = dense::block_sum_d(s, red);
+                    if (threadIdx.x == 0) {
+                        const double nx = *T.normx2;
+                        double r2 = nx + s - 2.0 * (*T.inner);
+                        if (r2 < 0.0) r2 = 0.0;
+                        T.fits[(it0 + it) % kFitRing] =
+                            (nx == 0.0) ? (r2 == 0.0 ? 1.0 : 0.0) : 1.0 - sqrt(r2) / sqrt(nx);
+                    }
+                }
+                __syncthreads();
+            }
+            if (!grid_barrier(a)) return;
+            // N: normalise the updated factor
+            normalize_phase(a, n);
+            if (!grid_barrier(a)) return;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *a.it_base = it0 + a.iters;
+}
+
+size_t batched_smem_bytes(int rank, int rp) {
+    const int half = (rank + 2) / 2;
+    const size_t prep = (3 * (size_t)rank * rank + 16 + 2 * half) * sizeof(double) + 2 * half * sizeof(int) + 64;
+    const size_t solve = rp == 16 ? sizeof(SolveSmem<16>) : sizeof(SolveSmem<32>);
+    return prep > solve ? prep : solve;
+}
+
+}  // namespace
+}  // namespace sptt
+
+using namespace sptt;
+
+struct sptt_batch {
+    int32_t count = 0, rank = 0, ld = 0, max_modes = 0;
+    sptt_opts opts{};
+    sptt_sched sched{};
+    bool has_sched = false;
+    cudaStream_t st = nullptr;
+    std::vector<sptt_csf *> csfs;       // count * max_modes (null where absent)
+    std::vector<BTensor> host;          // descriptors as copied to the device
+    std::vector<int64_t> m_elems;       // per tensor: elements of its compact M
+    std::vector<int64_t> mh_elems;      // per tensor: elements of its heavy rows
+    std::vector<void *> allocs;         // every device buffer owned by the batch
+    BTensor *d_tensors = nullptr;
+    int64_t *d_prefix = nullptr;        // 2 * max_modes * (count + 1)
+    int64_t total_chunks[kMaxModes] = {0};
+    int64_t total_tiles[kMaxModes] = {0};
+    unsigned *d_bar = nullptr;
+    int32_t *d_err = nullptr;
+    int64_t *d_it_base = nullptr;
+    double *partials = nullptr;         // Gram workspace for init
+    int32_t gram_blocks = 0;
+    int64_t iters_run = 0;
+    int grid = 0;
+    uint64_t timeout_ns = 2000000000ull;
+    int32_t skip_block = -1;
+    cudaGraphExec_t graph = nullptr;
+    int32_t graph_iters = -1;
+    bool zero_first = true;
+};
+
+namespace {
+
+void batch_destroy(sptt_batch *b) {
+    if (!b) return;
+    cudaStreamSynchronize(b->st);
+    for (auto *c : b->csfs)
+        if (c) csf_destroy(c);
+    for (void *p : b->allocs) dev_free(p, b->st);
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    cudaStreamSynchronize(b->st);
+    delete b;
+}
+
+template <typename T>
+sptt_status batch_alloc(sptt_batch *b, T **p, size_t n, bool zero) {
+    SPTT_TRY(dev_alloc_n(p, n, b->st));
+    b->allocs.push_back(*p);
+    if (zero) SPTT_TRY(fill_zero_launch(*p, n * sizeof(T), b->st));
+    return SPTT_OK;
+}
+
+sptt_status launch_batch(sptt_batch *b, int32_t iters) {
+    BatchArgs a{};
+    a.T = b->d_tensors;
+    a.count = b->count;
+    a.rank = b->rank;
+    a.ld = b->ld;
+    a.iters = iters;
+    a.max_modes = b->max_modes;
+    for (int n = 0; n < b->max_modes; ++n) {
+        a.chunk_prefix[n] = b->d_prefix + (2 * n) * (b->count + 1);
+        a.tile_prefix[n] = b->d_prefix + (2 * n + 1) * (b->count + 1);
+        a.total_chunks[n] = b->total_chunks[n];
+        a.total_tiles[n] = b->total_tiles[n];
+    }
+    a.bar = b->d_bar;
+    a.err = b->d_err;
+    a.it_base = b->d_it_base;
+    a.timeout_ns = b->timeout_ns;
+    a.skip_block = b->skip_block;
+    a.zero_first = b->zero_first ? 1 : 0;
+    SPTT_TRY(fill_zero_launch(b->d_bar, 2 * sizeof(unsigned), b->st));
+    SPTT_TRY(fill_zero_launch(b->d_err, sizeof(int32_t), b->st));
+    const int rp = b->rank <= 16 ? 16 : 32;
+    const size_t smem = batched_smem_bytes(b->rank, rp);
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(b->grid);
+    cfg.blockDim = dim3(kBThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = b->st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (rp == 16) SPTT_CUDA(cudaLaunchKernelEx(&cfg, batched_cpals_kernel<16>, a));
+    else SPTT_CUDA(cudaLaunchKernelEx(&cfg, batched_cpals_kernel<32>, a));
+    count_launch();
+    return SPTT_OK;
+}
+
+}  // namespace
+
+extern "C" sptt_status sptt_batch_create(const sptt_coo *coos, int32_t count, int32_t rank, const sptt_opts *opts,
+                                         sptt_stream stream, sptt_batch **out) {
+    clear_error();
+    if (!out || !coos) return set_error(SPTT_ERR_BAD_ARG, "coos and out must be non-NULL");
+    *out = nullptr;
+    if (count < 1) return set_error(SPTT_ERR_BAD_ARG, "count must be >= 1");
+    if (rank < 1 || rank > 32) return set_error(SPTT_ERR_UNSUPPORTED, "batched rank must be in [1, 32]");
+    sptt_batch *b = new sptt_batch();
+    struct Guard {
+        sptt_batch *b;
+        ~Guard() { if (b) batch_destroy(b); }
+    } guard{b};
+    if (opts) b->opts = *opts;
+    if (b->opts.sched) {
+        b->sched = *b->opts.sched;
+        b->has_sched = true;
+    }
+    b->opts.sched = nullptr;
+    b->st = reinterpret_cast<cudaStream_t>(stream);
+    b->count = count;
+    b->rank = rank;
+    b->ld = (rank + 3) / 4 * 4;
+    for (int t = 0; t < count; ++t) {
+        SPTT_TRY(coo_validate_shape(&coos[t]));
+        if (coos[t].nnz == 0) return set_error(SPTT_ERR_BAD_ARG, "every tensor needs a non-zero");
+        if (coos[t].nmodes > 4) return set_error(SPTT_ERR_UNSUPPORTED, "batched tensors have 2 to 4 modes");
+        if (coos[t].nmodes > b->max_modes) b->max_modes = coos[t].nmodes;
+    }
+    const sptt_sched *sched = b->has_sched ? &b->sched : nullptr;
+    b->csfs.assign((size_t)count * b->max_modes, nullptr);
+    b->host.resize(count);
+    std::vector<int64_t> prefix((size_t)2 * b->max_modes * (count + 1), 0);
+    int64_t max_rows = 0;
+    for (int t = 0; t < count; ++t) {
+        const sptt_coo &c = coos[t];
+        BTensor &T = b->host[t];
+        T = BTensor{};
+        T.nmodes = c.nmodes;
+        {
+            DevCoo dc;
+            SPTT_TRY(coo_to_device(&c, b->st, &dc));
+            for (int m = 0; m < c.nmodes; ++m) {
+                sptt_csf *cs = nullptr;
+                SPTT_TRY(csf_build_device(&dc.coo, m, nullptr, b->st, &cs));
+                b->csfs[(size_t)t * b->max_modes + m] = cs;
+                SPTT_TRY(mttkrp_prepare(cs, sched, b->st));
+            }
+        }
+        int64_t max_slices = 0, max_heavy = 0;
+        for (int m = 0; m < c.nmodes; ++m) {
+            T.dims[m] = c.dims[m];
+            if (c.dims[m] > max_rows) max_rows = c.dims[m];
+            SPTT_TRY(batch_alloc(b, &T.A[m], (size_t)c.dims[m] * b->ld, true));
+            SPTT_TRY(batch_alloc(b, &T.G[m], (size_t)rank * rank, true));
+            const sptt_csf *cs = b->csfs[(size_t)t * b->max_modes + m];
+            if (cs->nfibs[0] > max_slices) max_slices = cs->nfibs[0];
+            if (cs->nheavy > max_heavy) max_heavy = cs->nheavy;
+        }
+        SPTT_TRY(batch_alloc(b, &T.M, (size_t)max_slices * b->ld, true));
+        SPTT_TRY(batch_alloc(b, &T.Mh, (size_t)max_heavy * b->ld, true));
+        b->mh_elems.push_back(max_heavy * b->ld);
+        b->m_elems.push_back(max_slices * b->ld);
+        SPTT_TRY(batch_alloc(b, &T.gun, (size_t)rank * rank + rank, true));
+        SPTT_TRY(batch_alloc(b, &T.W, (size_t)rank * rank, true));
+        SPTT_TRY(batch_alloc(b, &T.lambda, (size_t)rank, true));
+        SPTT_TRY(batch_alloc(b, &T.inv_lambda, (size_t)rank, true));
+        SPTT_TRY(batch_alloc(b, &T.inner, 1, true));
+        SPTT_TRY(batch_alloc(b, &T.normx2, 1, true));
+        SPTT_TRY(batch_alloc(b, &T.fits, kFitRing, true));
+        SPTT_TRY(batch_alloc(b, &T.branch, 2, true));
+        for (int m = 0; m < c.nmodes; ++m) {
+            const sptt_csf *cs = b->csfs[(size_t)t * b->max_modes + m];
+            walk::Args &w = T.w[m];
+            w = walk::Args{};
+            for (int l = 0; l < c.nmodes; ++l) {
+                w.fptr[l] = cs->fptr[l];
+                w.fids[l] = cs->fids[l];
+                w.fac[l] = l ? T.A[cs->order[l]] : nullptr;
+            }
+            w.vals = cs->vals;
+            w.lvl = cs->lvl;
+            w.part = cs->part;
+            w.nchunks = cs->part_nchunks;
+            w.nnz = cs->nfibs[c.nmodes - 1];
+            w.chunk = cs->part_chunk;
+            w.ld = b->ld;
+            w.out = T.M;
+            w.heavy = T.Mh;
+            w.hidx = cs->hidx;
+            T.hidx[m] = cs->hidx;
+            T.fids0[m] = cs->fids[0];
+            T.nslices[m] = cs->nfibs[0];
+        }
+        const sptt_csf *c0 = b->csfs[(size_t)t * b->max_modes];
+        SPTT_TRY(sumsq_launch(c0->vals, c0->nfibs[c.nmodes - 1], T.normx2, b->st));
+    }
+    // global work lists: per mode position, chunk and tile prefix sums over the tensors
+    for (int n = 0; n < b->max_modes; ++n) {
+        int64_t *cp = prefix.data() + (2 * n) * (count + 1);
+        int64_t *tp = prefix.data() + (2 * n + 1) * (count + 1);
+        for (int t = 0; t < count; ++t) {
+            const BTensor &T = b->host[t];
+            const bool has = T.nmodes > n;
+            cp[t + 1] = cp[t] + (has ? T.w[n].nchunks : 0);
+            tp[t + 1] = tp[t] + (has ? (T.nslices[n] + kTileRows - 1) / kTileRows : 0);
+        }
+        b->total_chunks[n] = cp[count];
+        b->total_tiles[n] = tp[count];
+    }
+    SPTT_TRY(batch_alloc(b, &b->d_tensors, (size_t)count, false));
+    SPTT_CUDA(cudaMemcpyAsync(b->d_tensors, b->host.data(), sizeof(BTensor) * count, cudaMemcpyHostToDevice, b->st));
+    SPTT_TRY(batch_alloc(b, &b->d_prefix, prefix.size(), false));
+    SPTT_CUDA(cudaMemcpyAsync(b->d_prefix, prefix.data(), prefix.size() * sizeof(int64_t), cudaMemcpyHostToDevice,
+                              b->st));
+    SPTT_TRY(batch_alloc(b, &b->d_bar, 2, true));
+    SPTT_TRY(batch_alloc(b, &b->d_err, 1, true));
+    SPTT_TRY(batch_alloc(b, &b->d_it_base, 1, true));
+    b->gram_blocks = device_sm_count() * 2;
+    SPTT_TRY(batch_alloc(b, &b->partials, (size_t)b->gram_blocks * (rank * rank + rank), false));
+    // a grid that is fully resident (cooperative launch)
+    const int rp = rank <= 16 ? 16 : 32;
+    const size_t smem = batched_smem_bytes(rank, rp);
+    auto kern = rp == 16 ? batched_cpals_kernel<16> : batched_cpals_kernel<32>;
+    SPTT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    SPTT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBThreads, smem));
+    if (per_sm < 1) return set_error(SPTT_ERR_INTERNAL, "batched kernel does not fit on an SM");
+    b->grid = device_sm_count() * per_sm;
+    SPTT_CUDA(cudaStreamSynchronize(b->st));
+    guard.b = nullptr;
+    *out = b;
+    return SPTT_OK;
+}
+
+extern "C" void sptt_batch_free(sptt_batch *b) { batch_destroy(b); }
+
+extern "C" sptt_status sptt_batch_init(sptt_batch *b) {
+    clear_error();
+    if (!b) return set_error(SPTT_ERR_BAD_ARG, "batch is NULL");
+    for (int t = 0; t < b->count; ++t) {
+        const BTensor &T = b->host[t];
+        for (int m = 0; m < T.nmodes; ++m) {
+            SPTT_TRY(init_factor_launch(b->opts.seed + (uint64_t)t, m, T.dims[m], b->rank, b->ld, T.A[m], b->st));
+            SPTT_TRY(gram_launch(T.A[m], T.dims[m], b->rank, b->ld, T.G[m], b->partials, b->gram_blocks, b->st));
+        }
+        SPTT_TRY(fill_zero_launch(T.branch, 2 * sizeof(int32_t), b->st));
+        SPTT_TRY(fill_zero_launch(T.fits, kFitRing * sizeof(double), b->st));
+        // a run that stopped early may have left partial sums behind
+        SPTT_TRY(fill_zero_launch(T.M, (size_t)b->m_elems[t] * sizeof(float), b->st));
+        SPTT_TRY(fill_zero_launch(T.Mh, (size_t)b->mh_elems[t] * sizeof(double), b->st));
+        SPTT_TRY(fill_zero_launch(T.gun, ((size_t)b->rank * b->rank + b->rank) * sizeof(double), b->st));
+    }
+    SPTT_TRY(fill_zero_launch(b->d_it_base, sizeof(int64_t), b->st));
+    b->iters_run = 0;
+    b->zero_first = true;
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+        b->graph_iters = -1;
+    }
+    return SPTT_OK;
+}
+
+extern "C" sptt_status sptt_batch_run(sptt_batch *b, int32_t iters) {
+    clear_error();
+    if (!b) return set_error(SPTT_ERR_BAD_ARG, "batch is NULL");
+    if (iters < 1) return set_error(SPTT_ERR_BAD_ARG, "iters must be >= 1");
+    const bool graph = b->opts.use_graph && b->st != nullptr && b->skip_block < 0;
+    if (graph) {
+        // the graph replays runs after the first (factors already zeroed on empty rows)
+        if (b->zero_first) {
+            SPTT_TRY(launch_batch(b, iters));
+            b->zero_first = false;
+        } else {
+            if (!b->graph || b->graph_iters != iters) {
+                if (b->graph) cudaGraphExecDestroy(b->graph);
+                b->graph = nullptr;
+                cudaGraph_t g = nullptr;
+                SPTT_CUDA(cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal));
+                const int64_t l0 = sptt_debug_launch_count();
+                sptt_status s = launch_batch(b, iters);
+                const int64_t l1 = sptt_debug_launch_count();
+                cudaError_t e = cudaStreamEndCapture(b->st, &g);
+                if (s != SPTT_OK) {
+                    if (g) cudaGraphDestroy(g);
+                    return s;
+                }
+                if (e != cudaSuccess) return cuda_error(e, "cudaStreamEndCapture");
+                e = cudaGraphInstantiate(&b->graph, g, 0);
+                cudaGraphDestroy(g);
+                if (e != cudaSuccess) return cuda_error(e, "cudaGraphInstantiate");
+                b->graph_iters = iters;
+                count_launch(-(l1 - l0));
+            }
+            SPTT_CUDA(cudaGraphLaunch(b->graph, b->st));
+            count_launch(3);  // two clears and the persistent kernel
+        }
+    } else {
+        SPTT_TRY(launch_batch(b, iters));
+        b->zero_first = false;
+    }
+    b->iters_run += iters;
+    int32_t err = 0;
+    SPTT_CUDA(cudaMemcpyAsync(&err, b->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, b->st));
+    SPTT_CUDA(cudaStreamSynchronize(b->st));
+    if (err) return set_error(SPTT_ERR_TIMEOUT, "a grid barrier wait of the batched kernel ran out");
+    return SPTT_OK;
+}
+
+extern "C" sptt_status sptt_batch_fit_history(sptt_batch *b, int32_t t, double *fits, int32_t cap, int32_t *count) {
+    clear_error();
+    if (!b || !fits) return set_error(SPTT_ERR_BAD_ARG, "batch and fits must be non-NULL");
+    if (t < 0 || t >= b->count) return set_error(SPTT_ERR_BAD_ARG, "tensor index out of range");
+    const int64_t avail = b->iters_run < kFitRing ? b->iters_run : kFitRing;
+    const int64_t n = avail < cap ? avail : cap;
+    std::vector<double> ring(kFitRing);
+    SPTT_CUDA(cudaMemcpyAsync(ring.data(), b->host[t].fits, kFitRing * sizeof(double), cudaMemcpyDeviceToHost, b->st));
+    SPTT_CUDA(cudaStreamSynchronize(b->st));
+    for (int64_t j = 0; j < n; ++j) fits[j] = ring[(b->iters_run - n + j) % kFitRing];
+    if (count) *count = (int32_t)n;
+    return SPTT_OK;
+}
+
+extern "C" sptt_status sptt_batch_factor(sptt_batch *b, int32_t t, int32_t mode, float *dst) {
+    clear_error();
+    if (!b || !dst) return set_error(SPTT_ERR_BAD_ARG, "batch and dst must be non-NULL");
+    if (t < 0 || t >= b->count) return set_error(SPTT_ERR_BAD_ARG, "tensor index out of range");
+    const BTensor &T = b->host[t];
+    if (mode < 0 || mode >= T.nmodes) return set_error(SPTT_ERR_BAD_ARG, "mode out of range");
+    SPTT_CUDA(cudaMemcpy2DAsync(dst, b->rank * sizeof(float), T.A[mode], b->ld * sizeof(float),
+                                b->rank * sizeof(float), T.dims[mode], cudaMemcpyDefault, b->st));
+    SPTT_CUDA(cudaStreamSynchronize(b->st));
+    return SPTT_OK;
+}
+
+extern "C" sptt_status sptt_batch_lambda(sptt_batch *b, int32_t t, double *lambda) {
+    clear_error();
+    if (!b || !lambda) return set_error(SPTT_ERR_BAD_ARG, "batch and lambda must be non-NULL");
+    if (t < 0 || t >= b->count) return set_error(SPTT_ERR_BAD_ARG, "tensor index out of range");
+    SPTT_CUDA(cudaMemcpyAsync(lambda, b->host[t].lambda, b->rank * sizeof(double), cudaMemcpyDefault, b->st));
+    SPTT_CUDA(cudaStreamSynchronize(b->st));
+    return SPTT_OK;
+}
+
+extern "C" sptt_status sptt_batch_info(sptt_batch *b, int32_t *grid, int64_t *chunks, int64_t *tiles) {
+    clear_error();
+    if (!b) return set_error(SPTT_ERR_BAD_ARG, "batch is NULL");
+    if (grid) *grid = b->grid;
+    for (int n = 0; n < SPTT_MAX_MODES; ++n) {
+        if (chunks) chunks[n] = n < b->max_modes ? b->total_chunks[n] : 0;
+        if (tiles) tiles[n] = n < b->max_modes ? b->total_tiles[n] : 0;
+    }
+    return SPTT_OK;
+}
+
+extern "C" sptt_status sptt_debug_batch_stall(sptt_batch *b, int32_t skip_block, int64_t timeout_ns) {
+    clear_error();
+    if (!b) return set_error(SPTT_ERR_BAD_ARG, "batch is NULL");
+    if (skip_block >= b->grid) return set_error(SPTT_ERR_BAD_ARG, "skip_block >= grid size");
+    b->skip_block = skip_block < 0 ? -1 : skip_block;
+    b->timeout_ns = timeout_ns > 0 ? (uint64_t)timeout_ns : 2000000000ull;
+    return SPTT_OK;
+}

@@ -184,6 +184,29 @@ __global__ void partition_kernel(FptrPtrs fp, int nlev, int64_t nnz, int32_t chu
     }
 }
 
+// flag[f] = 1 if slice f's leaves span more than heavy_chunks chunks.
+__global__ void heavy_flags_kernel(FptrPtrs fp, int nlev, int64_t nslices, int32_t chunk, int heavy_chunks,
+                                   int32_t *__restrict__ flags) {
+    for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < nslices;
+         f += (int64_t)gridDim.x * blockDim.x) {
+        int64_t b = f, e = f + 1;
+        for (int l = 0; l < nlev - 1; ++l) {  // descend to the slice's leaf range [b, e)
+            b = fp.p[l][b];
+            e = fp.p[l][e];
+        }
+        const int64_t span = (e - 1) / chunk - b / chunk + 1;
+        flags[f] = span > heavy_chunks ? 1 : 0;
+    }
+}
+
+// hidx[f] = scan[f] where flagged, else -1.
+__global__ void heavy_index_kernel(const int32_t *__restrict__ flags, const int32_t *__restrict__ scan,
+                                   int64_t nslices, int32_t *__restrict__ hidx) {
+    for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < nslices;
+         f += (int64_t)gridDim.x * blockDim.x)
+        hidx[f] = flags[f] ? scan[f] : -1;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -248,6 +271,7 @@ void csf_destroy(sptt_csf *c) {
     if (c->vals) cudaFree(c->vals);
     if (c->lvl) cudaFree(c->lvl);
     if (c->part) cudaFree(c->part);
+    if (c->hidx) cudaFree(c->hidx);
     delete c;
 }
 
@@ -261,9 +285,11 @@ sptt_status csf_ensure_partition(sptt_csf *c, int32_t chunk, cudaStream_t st) {
         cudaFree(c->part);
         c->part = nullptr;
     }
+    if (!c->hidx) SPTT_CUDA(cudaMalloc(&c->hidx, (size_t)(c->nfibs[0] + 64) * sizeof(int32_t)));
     SPTT_CUDA(cudaMalloc(&c->part, (size_t)(nchunks * (N - 1) + 1) * sizeof(int32_t)));
     c->part_chunk = chunk;
     c->part_nchunks = nchunks;
+    c->nheavy = 0;
     if (nchunks == 0) return SPTT_OK;
     FptrPtrs fp{};
     for (int l = 0; l < N - 1; ++l) {
@@ -272,6 +298,19 @@ sptt_status csf_ensure_partition(sptt_csf *c, int32_t chunk, cudaStream_t st) {
     }
     partition_kernel<<<grid_for(nchunks), kThreads, 0, st>>>(fp, N, nnz, chunk, nchunks, c->part);
     SPTT_CHECK_LAUNCH("partition_kernel");
+    const int64_t ns = c->nfibs[0];
+    DevBuf flags, scan;
+    SPTT_TRY(flags.alloc<int32_t>(ns, st));
+    SPTT_TRY(scan.alloc<int32_t>(ns + 1, st));
+    heavy_flags_kernel<<<grid_for(ns), kThreads, 0, st>>>(fp, N, ns, chunk, kHeavyChunks, flags.as<int32_t>());
+    SPTT_CHECK_LAUNCH("heavy_flags_kernel");
+    SPTT_TRY(scan_exclusive_i32(flags.as<int32_t>(), scan.as<int32_t>(), ns, true, st));
+    heavy_index_kernel<<<grid_for(ns), kThreads, 0, st>>>(flags.as<int32_t>(), scan.as<int32_t>(), ns, c->hidx);
+    SPTT_CHECK_LAUNCH("heavy_index_kernel");
+    int32_t nh = 0;
+    SPTT_CUDA(cudaMemcpyAsync(&nh, scan.as<int32_t>() + ns, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    SPTT_CUDA(cudaStreamSynchronize(st));
+    c->nheavy = nh;
     return SPTT_OK;
 }
 

@@ -7,18 +7,18 @@
 // The row-wise work over I_n x R data runs on FP32 CUDA cores: products in
 // FP32, summed in FP32 over a tile of rows, tile sums accumulated in FP64
 // (GB300's FP64 pipe is too slow for I_n * R^2 FP64 FMAs).
-#include "internal.cuh"
+#include "dense_dev.cuh"
+#include "walk.cuh"
 
 namespace sptt {
 namespace {
 
+using dense::GramPtrs;
+using dense::block_sum_d;
+
 constexpr int kThreads = 256;
 constexpr int kGramRows = 64;   // rows per tile of the Gram kernel
 constexpr int kSolveRows = 32;  // rows per tile of the fused post-solve kernel
-
-struct GramPtrs {
-    const double *p[kMaxModes];
-};
 
 // ---------------------------------------------------------------------------
 // Gram: partials[block][a*rank+b] = sum over the block's rows of A[i,a] A[i,b]
@@ -86,10 +86,17 @@ __global__ void reduce_partials_kernel(const double *__restrict__ partials, int 
 }
 
 // ---------------------------------------------------------------------------
-// Fused post-solve: A_un = M W, plus Gram(A_un) and column dots M.A_un
+// Fused post-solve: A_un = M W, plus Gram(A_un) and column dots M.A_un.
+// M is compact (row f = slice f, whose mode index is fids0[f]); the result
+// rows are scattered to A[fids0[f]]. Rows of A with no slice are zero (the
+// caller zeroes A first), and contribute nothing to the Gram or the dots.
 // ---------------------------------------------------------------------------
 template <int RP>
-__global__ void __launch_bounds__(kThreads) postsolve_kernel(const double *__restrict__ M, float *__restrict__ A,
+__global__ void __launch_bounds__(kThreads) postsolve_kernel(const float *__restrict__ M,
+                                                             const double *__restrict__ heavy,
+                                                             const int32_t *__restrict__ hidx,
+                                                             const int32_t *__restrict__ fids0,
+                                                             float *__restrict__ A,
                                                              int64_t rows, int rank, int ld,
                                                              const float *__restrict__ Wg,
                                                              double *__restrict__ partials, int pstride) {
@@ -114,7 +121,7 @@ __global__ void __launch_bounds__(kThreads) postsolve_kernel(const double *__res
         for (int e = t; e < kSolveRows * RP; e += kThreads) {
             const int r = e / RP, c = e % RP;
             const int64_t i = i0 + r;
-            Mt[r][c] = (i < rows && c < rank) ? (float)M[i * ld + c] : 0.f;
+            Mt[r][c] = (i < rows && c < rank) ? walk::read_row(M, heavy, hidx, i, ld, c) : 0.f;
         }
         __syncthreads();
         float o[RE][CE];
@@ -138,11 +145,12 @@ __global__ void __launch_bounds__(kThreads) postsolve_kernel(const double *__res
         for (int y = 0; y < RE; ++y) {
             const int r = tr * RE + y;
             const int64_t i = i0 + r;
+            const int64_t dst = (i < rows) ? (int64_t)__ldg(fids0 + i) * ld : 0;
 #pragma unroll
             for (int x = 0; x < CE; ++x) {
                 const int c = tc * CE + x;
                 At[r][c] = o[y][x];
-                if (i < rows && c < ld) A[i * ld + c] = o[y][x];
+                if (i < rows && c < ld) A[dst + c] = o[y][x];
             }
         }
         __syncthreads();
@@ -188,207 +196,32 @@ __global__ void __launch_bounds__(kThreads) postsolve_kernel(const double *__res
 // ---------------------------------------------------------------------------
 // V = Hadamard_{m != n} G_m; W = V^dagger in FP64 (one CTA).
 // ---------------------------------------------------------------------------
-__device__ double block_sum_d(double v, double *red) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) red[warp] = v;
-    __syncthreads();
-    double s = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-    __syncthreads();
-    return s;
-}
-
 __global__ void __launch_bounds__(kThreads) normal_prep_kernel(GramPtrs g, int nmodes, int n, int rank,
                                                                float *__restrict__ W, int32_t *__restrict__ branch) {
     extern __shared__ double sm[];
-    const int R = rank, RR = R * R;
-    double *V = sm;            // Hadamard product (kept for the pinv branch)
-    double *S = sm + RR;       // Cholesky factor, or Jacobi working matrix
-    double *X = sm + 2 * RR;   // L^-1, or the Jacobi eigenvectors
-    double *misc = sm + 3 * RR;  // [0] threshold, [1] pd flag, [2..9] reduction scratch, [16..] rotations
-    const int t = threadIdx.x;
-    for (int e = t; e < RR; e += blockDim.x) {
-        double h = 1.0;
-        for (int m = 0; m < nmodes; ++m)
-            if (m != n) h *= g.p[m][e];
-        V[e] = h;
-        S[e] = h;
-    }
-    __syncthreads();
-    if (t == 0) {
-        double dmax = 0.0;
-        for (int i = 0; i < R; ++i) dmax = fmax(dmax, V[i * R + i]);
-        misc[0] = 1e-14 * dmax;
-        misc[1] = 1.0;
-    }
-    __syncthreads();
-    // Right-looking Cholesky of S (lower triangle), with the positive-definite test.
-    for (int j = 0; j < R; ++j) {
-        if (t == 0) {
-            const double d = S[j * R + j];
-            if (!(d > misc[0])) misc[1] = 0.0;
-            else S[j * R + j] = sqrt(d);
-        }
-        __syncthreads();
-        if (misc[1] == 0.0) break;
-        const double ljj = S[j * R + j];
-        for (int i = j + 1 + t; i < R; i += blockDim.x) S[i * R + j] /= ljj;
-        __syncthreads();
-        const int m = R - j - 1;
-        for (int e = t; e < m * m; e += blockDim.x) {
-            const int i = j + 1 + e / m, k = j + 1 + e % m;
-            if (k <= i) S[i * R + k] -= S[i * R + j] * S[k * R + j];
-        }
-        __syncthreads();
-    }
-    const bool pd = misc[1] != 0.0;
-    if (pd) {
-        // X = L^-1 (lower triangular), one column per thread
-        for (int c = t; c < R; c += blockDim.x) {
-            for (int i = 0; i < c; ++i) X[i * R + c] = 0.0;
-            for (int i = c; i < R; ++i) {
-                double s = (i == c) ? 1.0 : 0.0;
-                for (int k = c; k < i; ++k) s -= S[i * R + k] * X[k * R + c];
-                X[i * R + c] = s / S[i * R + i];
-            }
-        }
-        __syncthreads();
-        // V^-1 = L^-T L^-1
-        for (int e = t; e < RR; e += blockDim.x) {
-            const int a = e / R, b = e % R;
-            const int k0 = a > b ? a : b;
-            double s = 0.0;
-            for (int k = k0; k < R; ++k) s += X[k * R + a] * X[k * R + b];
-            W[e] = (float)s;
-        }
-    } else {
-        // Moore-Penrose pseudo-inverse by parallel cyclic Jacobi (round-robin
-        // pairing: Re/2 disjoint rotations per step, Re-1 steps per sweep).
-        for (int e = t; e < RR; e += blockDim.x) {
-            S[e] = V[e];
-            X[e] = (e / R == e % R) ? 1.0 : 0.0;
-        }
-        const int Re = (R + 1) & ~1;
-        const int half = Re / 2;
-        double *rc = misc + 16;           // cos per pair
-        double *rs = rc + half;           // sin per pair
-        int *rp = reinterpret_cast<int *>(rs + half);  // p per pair
-        int *rq = rp + half;                            // q per pair
-        __syncthreads();
-        for (int sweep = 0; sweep < 60; ++sweep) {
-            double off = 0.0, tot = 0.0;
-            for (int e = t; e < RR; e += blockDim.x) {
-                const double v = S[e] * S[e];
-                tot += v;
-                if (e / R != e % R) off += v;
-            }
-            off = block_sum_d(off, misc + 2);
-            tot = block_sum_d(tot, misc + 2);
-            if (off == 0.0 || off <= 1e-30 * tot) break;
-            for (int step = 0; step < Re - 1; ++step) {
-                for (int i = t; i < half; i += blockDim.x) {
-                    const int pa = i, pb = Re - 1 - i;
-                    const int p0 = pa == 0 ? 0 : ((pa - 1 + step) % (Re - 1)) + 1;
-                    const int q0 = pb == 0 ? 0 : ((pb - 1 + step) % (Re - 1)) + 1;
-                    const int p = p0 < q0 ? p0 : q0, q = p0 < q0 ? q0 : p0;
-                    double c = 1.0, s = 0.0;
-                    if (q < R) {
-                        const double apq = S[p * R + q];
-                        if (apq != 0.0) {
-                            const double theta = (S[q * R + q] - S[p * R + p]) / (2.0 * apq);
-                            const double tt = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-                            c = 1.0 / sqrt(tt * tt + 1.0);
-                            s = tt * c;
-                        }
-                    }
-                    rc[i] = c;
-                    rs[i] = s;
-                    rp[i] = p;
-                    rq[i] = q < R ? q : -1;
-                }
-                __syncthreads();
-                for (int e = t; e < R * half; e += blockDim.x) {  // S <- S J
-                    const int i = e / R, k = e % R;
-                    if (rq[i] < 0 || rs[i] == 0.0) continue;
-                    const int p = rp[i], q = rq[i];
-                    const double c = rc[i], s = rs[i];
-                    const double skp = S[k * R + p], skq = S[k * R + q];
-                    S[k * R + p] = c * skp - s * skq;
-                    S[k * R + q] = s * skp + c * skq;
-                }
-                __syncthreads();
-                for (int e = t; e < R * half; e += blockDim.x) {  // S <- J^T S, Q <- Q J
-                    const int i = e / R, k = e % R;
-                    if (rq[i] < 0 || rs[i] == 0.0) continue;
-                    const int p = rp[i], q = rq[i];
-                    const double c = rc[i], s = rs[i];
-                    const double spk = S[p * R + k], sqk = S[q * R + k];
-                    S[p * R + k] = c * spk - s * sqk;
-                    S[q * R + k] = s * spk + c * sqk;
-                    const double qkp = X[k * R + p], qkq = X[k * R + q];
-                    X[k * R + p] = c * qkp - s * qkq;
-                    X[k * R + q] = s * qkp + c * qkq;
-                }
-                __syncthreads();
-            }
-        }
-        if (t == 0) {
-            double wmax = 0.0;
-            for (int i = 0; i < R; ++i) wmax = fmax(wmax, fabs(S[i * R + i]));
-            misc[0] = (double)R * 2.220446049250313e-16 * wmax;
-        }
-        __syncthreads();
-        const double cut = misc[0];
-        for (int e = t; e < RR; e += blockDim.x) {
-            const int a = e / R, b = e % R;
-            double s = 0.0;
-            for (int k = 0; k < R; ++k) {
-                const double w = S[k * R + k];
-                if (fabs(w) > cut) s += X[a * R + k] * X[b * R + k] / w;
-            }
-            W[e] = (float)s;
-        }
-    }
-    if (t == 0) {
-        if (!pd) branch[0] += 1;
-        branch[1] += 1;
-    }
+    dense::normal_prep_body(g, nmodes, n, rank, W, branch, sm);
 }
 
 // lambda_r = sqrt(Gun_rr); G_n = D^-1 Gun D^-1; inner = sum of column dots.
 __global__ void finalize_kernel(const double *__restrict__ gun, int rank, double *__restrict__ Gn,
                                 double *__restrict__ lambda, float *__restrict__ inv_lambda,
                                 double *__restrict__ inner) {
-    __shared__ double inv[SPTT_MAX_RANK_ALS];
-    __shared__ double red[32];
-    const int t = threadIdx.x;
-    if (t < rank) {
-        const double d = gun[t * rank + t];
-        const double l = d > 0.0 ? sqrt(d) : 0.0;
-        lambda[t] = l;
-        inv[t] = l > 0.0 ? 1.0 / l : 0.0;
-        inv_lambda[t] = (float)inv[t];
-    }
-    __syncthreads();
-    for (int e = t; e < rank * rank; e += blockDim.x) {
-        const int a = e / rank, b = e % rank;
-        Gn[e] = gun[e] * inv[a] * inv[b];
-    }
-    double d = (t < rank) ? gun[rank * rank + t] : 0.0;
-    d = block_sum_d(d, red);
-    if (t == 0) *inner = d;
+    dense::finalize_body(gun, rank, Gn, lambda, inv_lambda, inner);
 }
 
-// Columns of A scaled by 1/lambda; padding columns zeroed; optional BF16 copy.
-__global__ void normalize_kernel(float *__restrict__ A, __nv_bfloat16 *__restrict__ Ab, int64_t rows, int ld,
-                                 int rank, const float *__restrict__ inv_lambda) {
-    const int64_t total4 = rows * ld / 4;
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total4;
-         q += (int64_t)gridDim.x * blockDim.x) {
+// Columns of A scaled by 1/lambda on the rows that hold a slice (the others
+// are zero already); padding columns zeroed; optional BF16 copy.
+__global__ void normalize_kernel(float *__restrict__ A, __nv_bfloat16 *__restrict__ Ab,
+                                 const int32_t *__restrict__ fids0, int64_t rows, int ld, int rank,
+                                 const float *__restrict__ inv_lambda) {
+    const int qpr = ld / 4;  // float4 groups per row
+    const int64_t total4 = rows * qpr;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total4;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t f = t / qpr;
+        const int c0 = (int)(t - f * qpr) * 4;
+        const int64_t q = ((int64_t)__ldg(fids0 + f) * ld + c0) / 4;
         float4 v = reinterpret_cast<float4 *>(A)[q];
-        const int c0 = (int)((q * 4) % ld);
         float x[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
         for (int j = 0; j < 4; ++j) x[j] = (c0 + j < rank) ? x[j] * inv_lambda[c0 + j] : 0.f;
@@ -604,17 +437,20 @@ sptt_status normal_prep_launch(double *const *grams, int32_t nmodes, int32_t n, 
 }
 
 template <int RP>
-static void postsolve_dispatch(const double *M, float *A, int64_t rows, DenseWork *w, int pstride, cudaStream_t st) {
-    postsolve_kernel<RP><<<w->nblocks, kThreads, 0, st>>>(M, A, rows, w->rank, w->ld, w->W, w->partials, pstride);
+static void postsolve_dispatch(const float *M, const double *heavy, const int32_t *hidx, const int32_t *fids0,
+                               float *A, int64_t rows, DenseWork *w, int pstride, cudaStream_t st) {
+    postsolve_kernel<RP><<<w->nblocks, kThreads, 0, st>>>(M, heavy, hidx, fids0, A, rows, w->rank, w->ld, w->W,
+                                                          w->partials, pstride);
 }
 
-sptt_status postsolve_launch(const double *M, float *A, int64_t rows, DenseWork *w, cudaStream_t st) {
+sptt_status postsolve_launch(const float *M, const double *heavy, const int32_t *hidx, const int32_t *fids0,
+                             float *A, int64_t rows, DenseWork *w, cudaStream_t st) {
     const int rank = w->rank;
     const int pstride = rank * rank + rank;
     switch (rank_pad(rank)) {
-        case 16: postsolve_dispatch<16>(M, A, rows, w, pstride, st); break;
-        case 32: postsolve_dispatch<32>(M, A, rows, w, pstride, st); break;
-        default: postsolve_dispatch<64>(M, A, rows, w, pstride, st); break;
+        case 16: postsolve_dispatch<16>(M, heavy, hidx, fids0, A, rows, w, pstride, st); break;
+        case 32: postsolve_dispatch<32>(M, heavy, hidx, fids0, A, rows, w, pstride, st); break;
+        default: postsolve_dispatch<64>(M, heavy, hidx, fids0, A, rows, w, pstride, st); break;
     }
     SPTT_CHECK_LAUNCH("postsolve_kernel");
     reduce_partials_kernel<<<(pstride + kThreads - 1) / kThreads, kThreads, 0, st>>>(w->partials, w->nblocks,
@@ -629,10 +465,11 @@ sptt_status finalize_launch(double *G_n, DenseWork *w, cudaStream_t st) {
     return SPTT_OK;
 }
 
-sptt_status normalize_launch(float *A, __nv_bfloat16 *A_bf16, int64_t rows, DenseWork *w, cudaStream_t st) {
+sptt_status normalize_launch(float *A, __nv_bfloat16 *A_bf16, const int32_t *fids0, int64_t rows, DenseWork *w,
+                             cudaStream_t st) {
     const int64_t q = rows * w->ld / 4;
     if (q == 0) return SPTT_OK;
-    normalize_kernel<<<grid_cap(q), kThreads, 0, st>>>(A, A_bf16, rows, w->ld, w->rank, w->inv_lambda);
+    normalize_kernel<<<grid_cap(q), kThreads, 0, st>>>(A, A_bf16, fids0, rows, w->ld, w->rank, w->inv_lambda);
     SPTT_CHECK_LAUNCH("normalize_kernel");
     return SPTT_OK;
 }

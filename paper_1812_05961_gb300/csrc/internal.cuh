@@ -12,6 +12,7 @@
 namespace sptt {
 
 constexpr int kMaxModes = SPTT_MAX_MODES;
+constexpr int kHeavyChunks = 8;
 constexpr int kNumSMs = 152;  // GB300: 2 dies x 76 SMs (queried at run time where it matters)
 
 // ---------------------------------------------------------------------------
@@ -116,6 +117,11 @@ struct sptt_csf {
     int32_t *part = nullptr;
     int32_t part_chunk = 0;
     int64_t part_nchunks = 0;
+    // Heavy slices: those whose leaves span more than kHeavyChunks chunks of
+    // the partition. hidx[f] = index of slice f among the heavy ones, or -1;
+    // their MTTKRP partials are summed in FP64 (see walk.cuh).
+    int32_t *hidx = nullptr;
+    int64_t nheavy = 0;
 };
 
 namespace sptt {
@@ -141,9 +147,10 @@ sptt_status coo_to_device(const sptt_coo *coo, cudaStream_t st, DevCoo *out);
 // ---------------------------------------------------------------------------
 // MTTKRP (mttkrp.cu)
 // ---------------------------------------------------------------------------
-// out: dims[root] x ld FP64 (zeroed, then filled).
+// out: compact FP32 (nfibs[0] x ld), heavy: FP64 (nheavy x ld); both are
+// zeroed here, then filled. Call mttkrp_prepare first (it sets nheavy).
 sptt_status mttkrp_launch(sptt_csf *csf, const void *const *factors, int32_t dtype, int32_t ld,
-                          double *out, const sptt_sched *sched, cudaStream_t st);
+                          float *out, double *heavy, const sptt_sched *sched, cudaStream_t st);
 // Builds the work partition the launch will use (allocates on first use, so
 // call it before any stream capture).
 sptt_status mttkrp_prepare(sptt_csf *csf, const sptt_sched *sched, cudaStream_t st);
@@ -172,14 +179,15 @@ sptt_status gram_launch(const float *A, int64_t rows, int32_t rank, int32_t ld, 
 // V = Hadamard_{m != n} grams[m]; W = V^dagger (FP64 Cholesky or pinv), stored FP32.
 sptt_status normal_prep_launch(double *const *grams, int32_t nmodes, int32_t n, int32_t rank,
                                DenseWork *w, cudaStream_t st);
-// A_un = M W, Gram(A_un) and column dots M.A_un into per-block partials, then reduced.
-sptt_status postsolve_launch(const double *M, float *A, int64_t rows, DenseWork *w,
-                             cudaStream_t st);
+// A_un[fids0[f]] = M[f] W over the rows f < rows of the compact M, with
+// Gram(A_un) and the column dots M.A_un into per-block partials, reduced.
+sptt_status postsolve_launch(const float *M, const double *heavy, const int32_t *hidx, const int32_t *fids0,
+                             float *A, int64_t rows, DenseWork *w, cudaStream_t st);
 // lambda = sqrt(diag G_un); G_n = D^-1 G_un D^-1; inner = sum dots.
 sptt_status finalize_launch(double *G_n, DenseWork *w, cudaStream_t st);
-// A *= 1/lambda (columns), optional BF16 shadow.
-sptt_status normalize_launch(float *A, __nv_bfloat16 *A_bf16, int64_t rows, DenseWork *w,
-                             cudaStream_t st);
+// A[fids0[f]] *= 1/lambda (columns) for f < rows, optional BF16 shadow.
+sptt_status normalize_launch(float *A, __nv_bfloat16 *A_bf16, const int32_t *fids0, int64_t rows,
+                             DenseWork *w, cudaStream_t st);
 // fit = 1 - sqrt(max(0, normx2 + lambda^T (*G) lambda - 2 inner)) / sqrt(normx2),
 // written to ring[*counter % ring_len], then ++*counter (device side).
 sptt_status fit_launch(double *const *grams, int32_t nmodes, const double *normx2, DenseWork *w,

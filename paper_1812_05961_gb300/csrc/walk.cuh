@@ -1,0 +1,304 @@
+// Device-side walk of one work chunk of a CSF tree for the root-mode MTTKRP
+// (Section III; Algorithm 1 lines 5, 8, 11). Shared by the standalone MTTKRP
+// kernels and the batched CP-ALS kernel.
+//
+// For the CSF rooted at mode n with level order (n, o_1, ..., o_{N-1}):
+//   M[i, :] = sum_{level-1 fibers f of slice i} A^(o_1)[j_f, :] *
+//             ( ... sum_{leaves k of the level-(N-2) fiber} v_k A^(o_{N-1})[k_idx, :])
+// The Khatri-Rao product is never formed: each fiber's partial sum is
+// multiplied by its factor row once.
+//
+// Mapping (in place of the paper's thread-per-slice loops with a lock pool
+// or privatised outputs, Section IV-A and V-D-2):
+//   * a lane group of G = ld / VEC lanes owns one output row; lane g holds
+//     columns [g*VEC, g*VEC + VEC) (VEC = 4 for FP32 factors, 8 for BF16) and
+//     gathers them with one 16-byte load per factor row;
+//   * the leaves are cut into equal chunks; the CSF's partition gives, per
+//     chunk, the fiber at every level holding the chunk's first leaf, and a
+//     lane group walks its chunk in order with one register accumulator per
+//     tree level, so the work is balanced whatever the slice sizes;
+//   * the output is compact: row f of M is slice f of the tree (the slice's
+//     mode index is fids[0][f]). A slice that starts and ends inside one
+//     chunk is owned by its lane group and stored (FP32). A slice cut by chunk
+//     boundaries gets one FP32 partial per chunk, added into the zeroed
+//     output with red.global.add.v4.f32 (no lock, no spin). A heavy slice (one
+//     spanning more than kHeavyChunks chunks: the power-law head, up to 10^5
+//     chunks) instead adds its partials with red.global.add.f64 into its own
+//     FP64 row heavy[hidx[f]], so its sum keeps the accuracy of one chunk's
+//     FP32 partial; readers take that row in place of row f.
+#pragma once
+
+#include "internal.cuh"
+
+namespace sptt {
+namespace walk {
+
+struct Args {
+    const int32_t *fptr[kMaxModes];  // levels 0..N-2 (used by the plain walk only)
+    const int32_t *fids[kMaxModes];  // levels 0..N-1
+    const void *fac[kMaxModes];      // by level; fac[0] unused
+    const float *vals;
+    const uint8_t *lvl;              // per-leaf first changed level
+    const int32_t *part;             // [nchunks][N-1]
+    int64_t nchunks;
+    int64_t nnz;
+    int32_t chunk;
+    int32_t ld;
+    float *out;                      // compact: nfibs[0] x ld, zeroed
+    double *heavy;                   // nheavy x ld, zeroed
+    const int32_t *hidx;             // per slice: heavy row index or -1
+};
+
+// A factor row segment as loaded (16 bytes: 4 FP32 or 8 BF16), widened to
+// FP32 only where it is used.
+template <typename T>
+struct Raw;
+
+template <>
+struct Raw<float> {
+    static constexpr int VEC = 4;
+    __device__ __forceinline__ static uint4 load(const void *base, int64_t row, int ld, int col) {
+        return __ldg(reinterpret_cast<const uint4 *>(static_cast<const float *>(base) + row * ld + col));
+    }
+    __device__ __forceinline__ static void widen(const uint4 &u, float (&x)[4]) {
+        x[0] = __uint_as_float(u.x);
+        x[1] = __uint_as_float(u.y);
+        x[2] = __uint_as_float(u.z);
+        x[3] = __uint_as_float(u.w);
+    }
+};
+
+template <>
+struct Raw<__nv_bfloat16> {
+    static constexpr int VEC = 8;
+    __device__ __forceinline__ static uint4 load(const void *base, int64_t row, int ld, int col) {
+        return __ldg(reinterpret_cast<const uint4 *>(static_cast<const __nv_bfloat16 *>(base) + row * ld + col));
+    }
+    __device__ __forceinline__ static void widen(const uint4 &u, float (&x)[8]) {
+        const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {  // bf16 -> f32 is exact: the bits move to the top half
+            x[2 * i] = __uint_as_float(w[i] << 16);
+            x[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u);
+        }
+    }
+};
+
+// Slice f is complete and owned by this lane group.
+template <int VEC>
+__device__ __forceinline__ void store_owned(const Args &a, int64_t f, int col, const float (&x)[VEC]) {
+    float *dst = a.out + f * a.ld + col;
+#pragma unroll
+    for (int i = 0; i < VEC; i += 4)
+        *reinterpret_cast<float4 *>(dst + i) = make_float4(x[i], x[i + 1], x[i + 2], x[i + 3]);
+}
+
+// A partial of slice f, which other chunks also touch.
+template <int VEC>
+__device__ __forceinline__ void add_partial(const Args &a, int64_t f, int col, const float (&x)[VEC]) {
+    const int32_t h = __ldg(a.hidx + f);
+    if (h >= 0) {
+        double *dst = a.heavy + (int64_t)h * a.ld + col;
+#pragma unroll
+        for (int i = 0; i < VEC; ++i)
+            asm volatile("red.global.add.f64 [%0], %1;" ::"l"(dst + i), "d"((double)x[i]) : "memory");
+    } else {
+        float *dst = a.out + f * a.ld + col;
+#pragma unroll
+        for (int i = 0; i < VEC; i += 4)
+            asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(dst + i), "f"(x[i]),
+                         "f"(x[i + 1]), "f"(x[i + 2]), "f"(x[i + 3])
+                         : "memory");
+    }
+}
+
+// Row f of the finished MTTKRP, column c.
+__device__ __forceinline__ float read_row(const float *out, const double *heavy, const int32_t *hidx, int64_t f,
+                                          int ld, int c) {
+    const int32_t h = __ldg(hidx + f);
+    return h >= 0 ? (float)heavy[(int64_t)h * ld + c] : out[f * ld + c];
+}
+
+// parent += row * child (element-wise); child = 0.
+template <typename T>
+__device__ __forceinline__ void fold(float (&parent)[Raw<T>::VEC], float (&child)[Raw<T>::VEC], const uint4 &row) {
+    float r[Raw<T>::VEC];
+    Raw<T>::widen(row, r);
+#pragma unroll
+    for (int i = 0; i < Raw<T>::VEC; ++i) {
+        parent[i] = fmaf(r[i], child[i], parent[i]);
+        child[i] = 0.f;
+    }
+}
+
+// The batched walk driven by the per-leaf level flags. A lane group takes
+// its chunk in batches of B leaves: the batch's values, leaf indices and
+// level flags arrive in vector loads; then every factor row the batch needs
+// (the B leaf rows, and the rows of the level-(N-2) fibers that open inside
+// the batch, whose ids are consecutive) is requested before any is used.
+// Rows of fibers at higher levels are requested when the fiber opens and
+// used when it closes.
+template <int NM, typename T, int B>
+__device__ __forceinline__ void flag_chunk(const Args &a, int64_t c, int col) {
+    using Rw = Raw<T>;
+    constexpr int VEC = Rw::VEC;
+    constexpr int NL = NM - 1;  // accumulator levels 0..NM-2
+    constexpr int LF = NM - 2;  // level of the leaves' parent fibers
+    static_assert(B == 4 || B == 8, "batch of 4 or 8 leaves");
+    const int ld = a.ld;
+    const int64_t k0 = c * (int64_t)a.chunk;
+    const int64_t k1 = (k0 + a.chunk < a.nnz) ? k0 + a.chunk : a.nnz;
+    int32_t f[NL];
+#pragma unroll
+    for (int l = 0; l < NL; ++l) f[l] = __ldg(a.part + c * NL + l);
+    float acc[NL][VEC];
+#pragma unroll
+    for (int l = 0; l < NL; ++l)
+#pragma unroll
+        for (int i = 0; i < VEC; ++i) acc[l][i] = 0.f;
+    uint4 rowc[NL];  // rows of the open fibers, levels 1..NL-1
+#pragma unroll
+    for (int l = 1; l < NL; ++l) rowc[l] = Rw::load(a.fac[l], __ldg(a.fids[l] + f[l]), ld, col);
+    bool first_slice = true;
+
+    for (int64_t kb = k0; kb < k1; kb += B) {
+        float v[B];
+        int32_t li[B];
+        uint32_t lw[2] = {0u, 0u};
+        {
+            const float4 va = __ldg(reinterpret_cast<const float4 *>(a.vals + kb));
+            const int4 ia = __ldg(reinterpret_cast<const int4 *>(a.fids[NM - 1] + kb));
+            v[0] = va.x; v[1] = va.y; v[2] = va.z; v[3] = va.w;
+            li[0] = ia.x; li[1] = ia.y; li[2] = ia.z; li[3] = ia.w;
+            if (B == 8) {
+                const float4 vb = __ldg(reinterpret_cast<const float4 *>(a.vals + kb + 4));
+                const int4 ib = __ldg(reinterpret_cast<const int4 *>(a.fids[NM - 1] + kb + 4));
+                v[4 % B] = vb.x; v[5 % B] = vb.y; v[6 % B] = vb.z; v[7 % B] = vb.w;
+                li[4 % B] = ib.x; li[5 % B] = ib.y; li[6 % B] = ib.z; li[7 % B] = ib.w;
+                const uint2 l2 = __ldg(reinterpret_cast<const uint2 *>(a.lvl + kb));
+                lw[0] = l2.x;
+                lw[1] = l2.y;
+            } else {
+                lw[0] = __ldg(reinterpret_cast<const uint32_t *>(a.lvl + kb));
+            }
+        }
+        const int nvalid = (k1 - kb < B) ? (int)(k1 - kb) : B;
+        uint4 x[B];
+#pragma unroll
+        for (int j = 0; j < B; ++j)
+            if (j < nvalid) x[j] = Rw::load(a.fac[NM - 1], li[j], ld, col);
+        // leaves that open a new level-LF fiber (never the chunk's first leaf)
+        uint32_t sm = 0;
+#pragma unroll
+        for (int j = 0; j < B; ++j) {
+            const uint32_t d = (lw[j >> 2] >> (8 * (j & 3))) & 0xffu;
+            if (j < nvalid && d <= (uint32_t)LF && (kb + j) != k0) sm |= 1u << j;
+        }
+        uint4 nr[B];
+        if (LF >= 1) {
+#pragma unroll
+            for (int j = 0; j < B; ++j)
+                if ((sm >> j) & 1u) {
+                    const int pos = __popc(sm & ((1u << j) - 1u)) + 1;
+                    nr[j] = Rw::load(a.fac[LF], __ldg(a.fids[LF] + f[LF] + pos), ld, col);
+                }
+        }
+#pragma unroll
+        for (int j = 0; j < B; ++j) {
+            if (j >= nvalid) break;
+            if ((sm >> j) & 1u) {
+                const int d = (int)((lw[j >> 2] >> (8 * (j & 3))) & 0xffu);
+                if (LF >= 1) {
+                    fold<T>(acc[LF - 1], acc[LF], rowc[LF]);
+                    ++f[LF];
+                    rowc[LF] = nr[j];
+                }
+#pragma unroll
+                for (int l = LF - 1; l >= 1; --l) {
+                    if (d <= l) {
+                        fold<T>(acc[l - 1], acc[l], rowc[l]);
+                        ++f[l];
+                        rowc[l] = Rw::load(a.fac[l], __ldg(a.fids[l] + f[l]), ld, col);
+                    }
+                }
+                if (d == 0) {  // the slice is complete
+                    if (first_slice) add_partial<VEC>(a, f[0], col, acc[0]);
+                    else store_owned<VEC>(a, f[0], col, acc[0]);
+                    first_slice = false;
+#pragma unroll
+                    for (int i = 0; i < VEC; ++i) acc[0][i] = 0.f;
+                    ++f[0];
+                }
+            }
+            float xr[VEC];
+            Rw::widen(x[j], xr);
+#pragma unroll
+            for (int i = 0; i < VEC; ++i) acc[LF][i] = fmaf(v[j], xr[i], acc[LF][i]);
+        }
+    }
+    // chunk end: fold the open fibers and add the partial slice
+#pragma unroll
+    for (int l = LF; l >= 1; --l) fold<T>(acc[l - 1], acc[l], rowc[l]);
+    add_partial<VEC>(a, f[0], col, acc[0]);
+}
+
+// The plain walk: one leaf at a time, fiber ends read from fptr.
+template <int NM, typename T>
+__device__ __forceinline__ void plain_chunk(const Args &a, int64_t c, int col) {
+    using Rw = Raw<T>;
+    constexpr int VEC = Rw::VEC;
+    constexpr int NL = NM - 1;
+    const int ld = a.ld;
+    const int64_t k0 = c * (int64_t)a.chunk;
+    const int64_t k1 = (k0 + a.chunk < a.nnz) ? k0 + a.chunk : a.nnz;
+    int32_t f[NL], end[NL];
+#pragma unroll
+    for (int l = 0; l < NL; ++l) {
+        f[l] = __ldg(a.part + c * NL + l);
+        end[l] = __ldg(a.fptr[l] + f[l] + 1);
+    }
+    float acc[NL][VEC];
+#pragma unroll
+    for (int l = 0; l < NL; ++l)
+#pragma unroll
+        for (int i = 0; i < VEC; ++i) acc[l][i] = 0.f;
+    bool first_slice = true;
+    for (int64_t k = k0; k < k1; ++k) {
+        if (k != k0 && k == end[NL - 1]) {
+            // leaf k opens a new level-(N-2) fiber: close the finished fibers
+            // bottom-up, folding each into its parent with the fiber's row
+            bool to_root = true;
+#pragma unroll
+            for (int l = NL - 1; l >= 1; --l) {
+                fold<T>(acc[l - 1], acc[l], Rw::load(a.fac[l], __ldg(a.fids[l] + f[l]), ld, col));
+                ++f[l];
+                end[l] = __ldg(a.fptr[l] + f[l] + 1);
+                if (f[l] != end[l - 1]) {
+                    to_root = false;
+                    break;
+                }
+            }
+            if (to_root) {  // the slice is complete
+                if (first_slice) add_partial<VEC>(a, f[0], col, acc[0]);
+                else store_owned<VEC>(a, f[0], col, acc[0]);
+                first_slice = false;
+#pragma unroll
+                for (int i = 0; i < VEC; ++i) acc[0][i] = 0.f;
+                ++f[0];
+                end[0] = __ldg(a.fptr[0] + f[0] + 1);
+            }
+        }
+        const float v = __ldg(a.vals + k);
+        float x[VEC];
+        Rw::widen(Rw::load(a.fac[NM - 1], __ldg(a.fids[NM - 1] + k), ld, col), x);
+#pragma unroll
+        for (int i = 0; i < VEC; ++i) acc[NL - 1][i] = fmaf(v, x[i], acc[NL - 1][i]);
+    }
+#pragma unroll
+    for (int l = NL - 1; l >= 1; --l)
+        fold<T>(acc[l - 1], acc[l], Rw::load(a.fac[l], __ldg(a.fids[l] + f[l]), ld, col));
+    add_partial<VEC>(a, f[0], col, acc[0]);
+}
+
+}  // namespace walk
+}  // namespace sptt
