@@ -143,6 +143,8 @@ typedef struct {
     int32_t chunk;
     int32_t block;
     int32_t variant;
+    int32_t order;  /* CSF level order below the root for CP-ALS plans: 0 = ascending
+                       length (default), 1 = descending; ignored by sptt_mttkrp */
 } sptt_sched;
 
 /*
@@ -217,8 +219,14 @@ sptt_status sptt_gram_noalloc(const float *A, int64_t rows, int32_t rank, int32_
  *                 precision = SPTT_BF16; ignored for F32)
  *   use_graph     1: run each iteration as one captured CUDA graph
  *   profile       1: record per-routine CUDA-event timers (sptt_cpd_timers)
- *   sched         per-kernel schedule override (NULL = default)
+ *   sched         schedule of every mode's MTTKRP (NULL = default)
+ *   mode_sched    array of nmodes schedules, one per root mode (overrides sched)
+ *   plan          0: use sched / mode_sched; 1: choose each mode's schedule with
+ *                 the autotuner (sptt_autotune); 2: choose it with the learned
+ *                 scheduler `mlp` (sptt_mlp_predict on sptt_csf_features)
+ *   mlp           the trained scheduler for plan = 2
  */
+typedef struct sptt_mlp sptt_mlp;
 typedef struct {
     uint64_t seed;
     int32_t precision;
@@ -226,6 +234,9 @@ typedef struct {
     int32_t use_graph;
     int32_t profile;
     const sptt_sched *sched;
+    const sptt_sched *mode_sched;
+    int32_t plan;
+    const sptt_mlp *mlp;
 } sptt_opts;
 
 typedef struct sptt_cpd sptt_cpd;
@@ -321,6 +332,61 @@ sptt_status sptt_cpd_timers(sptt_cpd *cpd, double *ms, int64_t *counts);
 sptt_status sptt_cpd_als(const sptt_coo *coo, int32_t rank, int32_t max_iters, double tol,
                          const sptt_opts *opts, sptt_stream stream, float *const *factors_out,
                          double *lambda_out, double *fit_out, int32_t *iters_out);
+
+/* ------------------------------------------------------------------------ */
+/* Schedule selection: candidates, autotuner, learned scheduler.            */
+/* (Not in the paper, whose code picks locks vs privatisation by a rule.)   */
+/* ------------------------------------------------------------------------ */
+
+/* The candidate MTTKRP schedules (order x variant x chunk); copies up to cap
+ * of them into out (may be NULL) and returns how many there are (16). */
+int32_t sptt_sched_candidates(sptt_sched *out, int32_t cap);
+
+/* Exhaustive autotuner: times the MTTKRP rooted at `root` under every
+ * candidate schedule (random factors of `rank` columns, dtype SPTT_F32 or
+ * SPTT_BF16), median of `reps` runs after one warm-up, into ms[candidate]
+ * (host, one float per candidate). Builds the CSF in both orders.
+ * Synchronises. */
+sptt_status sptt_autotune(const sptt_coo *coo, int32_t root, int32_t rank, int32_t dtype, int32_t reps,
+                          float *ms, sptt_stream stream);
+
+/* The 16 statistics the learned scheduler reads for one CSF and rank (host
+ * output): log2 nnz, modes, log2 rank, log2 of the root / level-1 / leaf
+ * mode lengths, log2 slices, log2 leaf-parent fibers, log2 leaves per
+ * leaf-parent fiber and per slice, log2 largest slice, share of non-zeros in
+ * slices of >= 1024 leaves, share of one-leaf slices, log2 of the leaf and
+ * level-1 factor table bytes, slice-size histogram entropy / 5 (a device
+ * histogram kernel). Synchronises. */
+sptt_status sptt_csf_features(const sptt_csf *csf, int32_t rank, float *feat, sptt_stream stream);
+
+/* The learned scheduler: an MLP 16 -> 64 (ReLU) -> 64 (ReLU) -> 16 in FP32
+ * that predicts, per candidate, log2(time / best time) from the 16
+ * statistics (standardised with the training set's mean and scale). */
+sptt_status sptt_mlp_create(uint64_t seed, sptt_mlp **out);
+void sptt_mlp_free(sptt_mlp *mlp);
+/* Number of parameters (packed W1[64][16], b1, W2[64][64], b2, W3[16][64], b3). */
+int32_t sptt_mlp_nparams(void);
+/* Copy the parameters and the feature mean / scale (16 each) out of / into
+ * the model (host or device buffers; any may be NULL). Synchronous. */
+sptt_status sptt_mlp_get(const sptt_mlp *mlp, float *params, float *mu, float *sd);
+sptt_status sptt_mlp_set(sptt_mlp *mlp, const float *params, const float *mu, const float *sd);
+/* Y[n][16] = MLP(X[n][16]) (device buffers). Asynchronous. */
+sptt_status sptt_mlp_forward(const sptt_mlp *mlp, const float *X, int64_t n, float *Y, sptt_stream stream);
+/* Loss 1/(16 n) sum (Y - T)^2 over the batch and its gradient (nparams
+ * floats, host or device). X, T device. Synchronises. */
+sptt_status sptt_mlp_loss_grad(sptt_mlp *mlp, const float *X, const float *T, int64_t n, float *loss,
+                               float *grad, sptt_stream stream);
+/* `steps` full-batch Adam steps (lr; beta 0.9 / 0.999) on (X, T) (device);
+ * the first call also sets the feature mean / scale from X. loss_history
+ * (host or device, steps floats, may be NULL) receives each step's loss.
+ * Synchronises. */
+sptt_status sptt_mlp_train(sptt_mlp *mlp, const float *X, const float *T, int64_t n, int32_t steps, float lr,
+                           float *loss_history, sptt_stream stream);
+/* Candidate choice (argmin of the predicted times) for n feature rows
+ * (host); pred (host, n x 16, may be NULL) receives the predictions.
+ * Synchronises. */
+sptt_status sptt_mlp_predict(const sptt_mlp *mlp, const float *feat, int64_t n, int32_t *choice, float *pred,
+                             sptt_stream stream);
 
 /* ------------------------------------------------------------------------ */
 /* Batched CP-ALS: many small tensors in one persistent launch.             */

@@ -81,6 +81,11 @@ def _load():
                                            ctypes.POINTER(_i32p), _f32p, ctypes.c_int32,
                                            ctypes.c_int32, ctypes.c_double, ctypes.POINTER(_f64p),
                                            _f64p, _f64p]
+            lib.oracle_mlp_forward.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _f64p,
+                                               ctypes.c_int64, _f64p, _f64p]
+            lib.oracle_mlp_loss_grad.restype = ctypes.c_double
+            lib.oracle_mlp_loss_grad.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _f64p,
+                                                 ctypes.c_int64, _f64p, _f64p, _f64p]
             _lib = lib
     return _lib
 
@@ -329,3 +334,32 @@ def cpd_als(inds, vals, dims, rank: int, max_iters: int, tol: float = 0.0, seed:
                             _p(vals, _f32p), rank, max_iters, float(tol),
                             _ptr_array(fac, _f64p, _f64p), _p(lam, _f64p), _p(fits, _f64p))
     return {"factors": fac, "lam": lam, "fits": fits[:it].copy(), "iters": int(it)}
+
+
+# --------------------------------------------------------------------------
+# Scheduler MLP (FP64 reference for the GPU training kernels)
+# --------------------------------------------------------------------------
+
+def mlp_nparams(nin, nh, nout):
+    return nh * nin + nh + nh * nh + nh + nout * nh + nout
+
+
+def mlp_forward(P, x, nin, nh, nout):
+    lib = _load()
+    P = _c(P, np.float64)
+    x = _c(x, np.float64).reshape(-1, nin)
+    y = np.zeros((x.shape[0], nout), np.float64)
+    lib.oracle_mlp_forward(nin, nh, nout, _p(P, _f64p), x.shape[0], _p(x, _f64p), _p(y, _f64p))
+    return y
+
+
+def mlp_loss_grad(P, x, t, nin, nh, nout):
+    """MSE loss 1/(n*nout) sum (y - t)^2 and its gradient (same layout as P)."""
+    lib = _load()
+    P = _c(P, np.float64)
+    x = _c(x, np.float64).reshape(-1, nin)
+    t = _c(t, np.float64).reshape(-1, nout)
+    G = np.zeros_like(P)
+    L = lib.oracle_mlp_loss_grad(nin, nh, nout, _p(P, _f64p), x.shape[0], _p(x, _f64p), _p(t, _f64p),
+                                 _p(G, _f64p))
+    return L, G

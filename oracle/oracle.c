@@ -510,3 +510,92 @@ int32_t oracle_cpd_als(int32_t nmodes, int64_t nnz, const int64_t *dims,
     free(M_last);
     return it;
 }
+
+/* ------------------------------------------------------------------------ */
+/* The scheduler's MLP, FP64 reference (the learned scheduler is not in the */
+/* paper; this is the reference its GPU training kernels are checked with). */
+/* in -> h (ReLU) -> h (ReLU) -> out, parameters packed as                   */
+/* W1[h][in], b1[h], W2[h][h], b2[h], W3[out][h], b3[out] (row-major).       */
+/* ------------------------------------------------------------------------ */
+
+static void mlp_layer(const double *W, const double *b, const double *x, int nin, int nout, int relu,
+                      double *pre, double *y) {
+    for (int o = 0; o < nout; ++o) {
+        double s = b[o];
+        for (int i = 0; i < nin; ++i) s += W[o * nin + i] * x[i];
+        if (pre) pre[o] = s;
+        y[o] = (relu && s < 0.0) ? 0.0 : s;
+    }
+}
+
+/* y[n][nout] = MLP(x[n][nin]) */
+void oracle_mlp_forward(int32_t nin, int32_t nh, int32_t nout, const double *P, int64_t n, const double *x,
+                        double *y) {
+    const double *W1 = P, *b1 = W1 + nh * nin, *W2 = b1 + nh, *b2 = W2 + nh * nh, *W3 = b2 + nh,
+                 *b3 = W3 + nout * nh;
+    double *h1 = (double *)malloc((size_t)nh * sizeof(double));
+    double *h2 = (double *)malloc((size_t)nh * sizeof(double));
+    for (int64_t s = 0; s < n; ++s) {
+        mlp_layer(W1, b1, x + s * nin, nin, nh, 1, NULL, h1);
+        mlp_layer(W2, b2, h1, nh, nh, 1, NULL, h2);
+        mlp_layer(W3, b3, h2, nh, nout, 0, NULL, y + s * nout);
+    }
+    free(h1);
+    free(h2);
+}
+
+/*
+ * Loss L = 1/(n*nout) * sum (y - t)^2 over the batch and its gradient with
+ * respect to every parameter (back-propagation), into G (same layout as P).
+ * Returns L.
+ */
+double oracle_mlp_loss_grad(int32_t nin, int32_t nh, int32_t nout, const double *P, int64_t n, const double *x,
+                            const double *t, double *G) {
+    const int np = nh * nin + nh + nh * nh + nh + nout * nh + nout;
+    const double *W1 = P, *b1 = W1 + nh * nin, *W2 = b1 + nh, *b2 = W2 + nh * nh, *W3 = b2 + nh,
+                 *b3 = W3 + nout * nh;
+    double *gW1 = G, *gb1 = gW1 + nh * nin, *gW2 = gb1 + nh, *gb2 = gW2 + nh * nh, *gW3 = gb2 + nh,
+           *gb3 = gW3 + nout * nh;
+    memset(G, 0, (size_t)np * sizeof(double));
+    double *p1 = (double *)malloc((size_t)nh * sizeof(double)), *h1 = (double *)malloc((size_t)nh * sizeof(double));
+    double *p2 = (double *)malloc((size_t)nh * sizeof(double)), *h2 = (double *)malloc((size_t)nh * sizeof(double));
+    double *y = (double *)malloc((size_t)nout * sizeof(double)), *dy = (double *)malloc((size_t)nout * sizeof(double));
+    double *d2 = (double *)malloc((size_t)nh * sizeof(double)), *d1 = (double *)malloc((size_t)nh * sizeof(double));
+    const double scale = 1.0 / ((double)n * nout);
+    double loss = 0.0;
+    for (int64_t s = 0; s < n; ++s) {
+        const double *xs = x + s * nin, *ts = t + s * nout;
+        mlp_layer(W1, b1, xs, nin, nh, 1, p1, h1);
+        mlp_layer(W2, b2, h1, nh, nh, 1, p2, h2);
+        mlp_layer(W3, b3, h2, nh, nout, 0, NULL, y);
+        for (int o = 0; o < nout; ++o) {
+            const double e = y[o] - ts[o];
+            loss += e * e * scale;
+            dy[o] = 2.0 * e * scale;
+        }
+        for (int o = 0; o < nout; ++o) {
+            gb3[o] += dy[o];
+            for (int j = 0; j < nh; ++j) gW3[o * nh + j] += dy[o] * h2[j];
+        }
+        for (int j = 0; j < nh; ++j) {
+            double s2 = 0.0;
+            for (int o = 0; o < nout; ++o) s2 += dy[o] * W3[o * nh + j];
+            d2[j] = p2[j] > 0.0 ? s2 : 0.0;
+        }
+        for (int j = 0; j < nh; ++j) {
+            gb2[j] += d2[j];
+            for (int i = 0; i < nh; ++i) gW2[j * nh + i] += d2[j] * h1[i];
+        }
+        for (int i = 0; i < nh; ++i) {
+            double s1 = 0.0;
+            for (int j = 0; j < nh; ++j) s1 += d2[j] * W2[j * nh + i];
+            d1[i] = p1[i] > 0.0 ? s1 : 0.0;
+        }
+        for (int i = 0; i < nh; ++i) {
+            gb1[i] += d1[i];
+            for (int k = 0; k < nin; ++k) gW1[i * nin + k] += d1[i] * xs[k];
+        }
+    }
+    free(p1); free(h1); free(p2); free(h2); free(y); free(dy); free(d2); free(d1);
+    return loss;
+}

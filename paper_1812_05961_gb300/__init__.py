@@ -47,13 +47,19 @@ class sptt_coo(ctypes.Structure):
 
 
 class sptt_sched(ctypes.Structure):
-    _fields_ = [("chunk", ctypes.c_int32), ("block", ctypes.c_int32), ("variant", ctypes.c_int32)]
+    _fields_ = [("chunk", ctypes.c_int32), ("block", ctypes.c_int32), ("variant", ctypes.c_int32),
+                ("order", ctypes.c_int32)]
+
+    def as_tuple(self):
+        return (self.chunk, self.block, self.variant, self.order)
 
 
 class sptt_opts(ctypes.Structure):
     _fields_ = [("seed", ctypes.c_uint64), ("precision", ctypes.c_int32),
                 ("refine_iters", ctypes.c_int32), ("use_graph", ctypes.c_int32),
-                ("profile", ctypes.c_int32), ("sched", ctypes.POINTER(sptt_sched))]
+                ("profile", ctypes.c_int32), ("sched", ctypes.POINTER(sptt_sched)),
+                ("mode_sched", ctypes.POINTER(sptt_sched)), ("plan", ctypes.c_int32),
+                ("mlp", ctypes.c_void_p)]
 
 
 _lib = None
@@ -104,6 +110,18 @@ def lib() -> ctypes.CDLL:
                                    ctypes.POINTER(sptt_opts), _P, _P, _P, _P, _P]),
             "sptt_debug_fail_alloc_after": (None, [_I64]),
             "sptt_debug_launch_count": (_I64, []),
+            "sptt_sched_candidates": (_I32, [_P, _I32]),
+            "sptt_autotune": (_ST, [ctypes.POINTER(sptt_coo), _I32, _I32, _I32, _I32, _P, _P]),
+            "sptt_csf_features": (_ST, [_P, _I32, _P, _P]),
+            "sptt_mlp_create": (_ST, [ctypes.c_uint64, ctypes.POINTER(_P)]),
+            "sptt_mlp_free": (None, [_P]),
+            "sptt_mlp_nparams": (_I32, []),
+            "sptt_mlp_get": (_ST, [_P, _P, _P, _P]),
+            "sptt_mlp_set": (_ST, [_P, _P, _P, _P]),
+            "sptt_mlp_forward": (_ST, [_P, _P, _I64, _P, _P]),
+            "sptt_mlp_loss_grad": (_ST, [_P, _P, _P, _I64, _P, _P, _P]),
+            "sptt_mlp_train": (_ST, [_P, _P, _P, _I64, _I32, ctypes.c_float, _P, _P]),
+            "sptt_mlp_predict": (_ST, [_P, _P, _I64, _P, _P, _P]),
             "sptt_batch_create": (_ST, [_P, _I32, _I32, ctypes.POINTER(sptt_opts), _P, ctypes.POINTER(_P)]),
             "sptt_batch_free": (None, [_P]),
             "sptt_batch_init": (_ST, [_P]),
@@ -166,12 +184,23 @@ class _Coo:
                           self.vals_t.data_ptr(), 1 if on_dev else 0)
 
 
-def _opts(seed=0, precision=SPTT_F32, refine_iters=0, use_graph=0, profile=0, sched=None):
-    o = sptt_opts(seed, precision, refine_iters, use_graph, profile, None)
-    keep = None
+def _sched(s):
+    return s if isinstance(s, sptt_sched) else sptt_sched(*s)
+
+
+def _opts(seed=0, precision=SPTT_F32, refine_iters=0, use_graph=0, profile=0, sched=None,
+          mode_sched=None, plan=0, mlp=None):
+    o = sptt_opts(seed, precision, refine_iters, use_graph, profile, None, None, plan,
+                  None if mlp is None else (mlp.handle if hasattr(mlp, "handle") else mlp))
+    keep = []
     if sched is not None:
-        keep = sptt_sched(*sched) if not isinstance(sched, sptt_sched) else sched
-        o.sched = ctypes.pointer(keep)
+        one = _sched(sched)
+        keep.append(one)
+        o.sched = ctypes.pointer(one)
+    if mode_sched is not None:
+        arr = (sptt_sched * len(mode_sched))(*[_sched(x) for x in mode_sched])
+        keep.append(arr)
+        o.mode_sched = ctypes.cast(arr, ctypes.POINTER(sptt_sched))
     return o, keep
 
 
@@ -237,7 +266,7 @@ def sptt_mttkrp(csf: int, factors: Sequence[Optional[torch.Tensor]], out: torch.
             raise ValueError("factors must be contiguous with ld = out.shape[1] columns")
     s = None
     if sched is not None:
-        s = sptt_sched(*sched) if not isinstance(sched, sptt_sched) else sched
+        s = _sched(sched)
     _check(lib().sptt_mttkrp(csf, arr, factor_dtype, ld, out.data_ptr(),
                              None if s is None else ctypes.byref(s), _stream(stream)), "sptt_mttkrp")
     return out
@@ -417,6 +446,106 @@ def sptt_batch_info(b: int):
 
 def sptt_debug_batch_stall(b: int, skip_block: int, timeout_ns: int):
     _check(lib().sptt_debug_batch_stall(b, skip_block, timeout_ns), "sptt_debug_batch_stall")
+
+
+def sptt_sched_candidates():
+    n = lib().sptt_sched_candidates(None, 0)
+    arr = (sptt_sched * n)()
+    lib().sptt_sched_candidates(arr, n)
+    return [arr[i].as_tuple() for i in range(n)]
+
+
+def sptt_autotune(dims, inds, vals, root: int, rank: int, dtype: int = SPTT_F32, reps: int = 3, stream=None):
+    """Median time (ms) of the root-mode MTTKRP under every candidate schedule."""
+    coo = _Coo(dims, inds, vals)
+    n = lib().sptt_sched_candidates(None, 0)
+    ms = (ctypes.c_float * n)()
+    _check(lib().sptt_autotune(ctypes.byref(coo.c), root, rank, dtype, reps, ms, _stream(stream)),
+           "sptt_autotune")
+    return list(ms)
+
+
+def sptt_csf_features(csf: int, rank: int, stream=None):
+    f = (ctypes.c_float * 16)()
+    _check(lib().sptt_csf_features(csf, rank, f, _stream(stream)), "sptt_csf_features")
+    return list(f)
+
+
+def sptt_mlp_create(seed: int = 0) -> int:
+    out = ctypes.c_void_p()
+    _check(lib().sptt_mlp_create(ctypes.c_uint64(seed), ctypes.byref(out)), "sptt_mlp_create")
+    return out.value
+
+
+def sptt_mlp_free(m: int):
+    lib().sptt_mlp_free(m)
+
+
+def sptt_mlp_nparams() -> int:
+    return lib().sptt_mlp_nparams()
+
+
+def sptt_mlp_get(m: int):
+    P = torch.empty(sptt_mlp_nparams(), dtype=torch.float32)
+    mu = torch.empty(16, dtype=torch.float32)
+    sd = torch.empty(16, dtype=torch.float32)
+    _check(lib().sptt_mlp_get(m, P.data_ptr(), mu.data_ptr(), sd.data_ptr()), "sptt_mlp_get")
+    return P, mu, sd
+
+
+def sptt_mlp_set(m: int, params=None, mu=None, sd=None):
+    keep = [None if x is None else x.contiguous().to(torch.float32) for x in (params, mu, sd)]
+    _check(lib().sptt_mlp_set(m, *[_ptr(x) for x in keep]), "sptt_mlp_set")
+
+
+def sptt_mlp_forward(m: int, X: torch.Tensor, stream=None) -> torch.Tensor:
+    Y = torch.empty((X.shape[0], 16), dtype=torch.float32, device=X.device)
+    _check(lib().sptt_mlp_forward(m, X.data_ptr(), X.shape[0], Y.data_ptr(), _stream(stream)),
+           "sptt_mlp_forward")
+    return Y
+
+
+def sptt_mlp_loss_grad(m: int, X: torch.Tensor, T: torch.Tensor, stream=None):
+    loss = ctypes.c_float()
+    G = torch.empty(sptt_mlp_nparams(), dtype=torch.float32)
+    _check(lib().sptt_mlp_loss_grad(m, X.data_ptr(), T.data_ptr(), X.shape[0], ctypes.byref(loss),
+                                    G.data_ptr(), _stream(stream)), "sptt_mlp_loss_grad")
+    return loss.value, G
+
+
+def sptt_mlp_train(m: int, X: torch.Tensor, T: torch.Tensor, steps: int, lr: float = 1e-3, stream=None):
+    hist = torch.empty(max(steps, 1), dtype=torch.float32)
+    _check(lib().sptt_mlp_train(m, X.data_ptr(), T.data_ptr(), X.shape[0], steps, ctypes.c_float(lr),
+                                hist.data_ptr(), _stream(stream)), "sptt_mlp_train")
+    return hist[:steps]
+
+
+def sptt_mlp_predict(m: int, feats, stream=None):
+    F = torch.as_tensor(feats, dtype=torch.float32).reshape(-1, 16).contiguous()
+    n = F.shape[0]
+    choice = (ctypes.c_int32 * n)()
+    pred = torch.empty((n, 16), dtype=torch.float32)
+    _check(lib().sptt_mlp_predict(m, F.data_ptr(), n, choice, pred.data_ptr(), _stream(stream)),
+           "sptt_mlp_predict")
+    return list(choice), pred
+
+
+class Mlp:
+    """The learned scheduler (freed with the object)."""
+
+    def __init__(self, seed: int = 0):
+        self.handle = sptt_mlp_create(seed)
+
+    def close(self):
+        if self.handle:
+            sptt_mlp_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ---------------------------------------------------------------------------

@@ -34,8 +34,8 @@ struct sptt_cpd {
     int32_t rank = 0;
     int32_t ld = 0;
     sptt_opts opts{};
-    sptt_sched sched{};
-    bool has_sched = false;
+    sptt_sched msched[SPTT_MAX_MODES] = {};  // schedule of each mode's MTTKRP
+    bool has_msched[SPTT_MAX_MODES] = {false};
     cudaStream_t st = nullptr;
     sptt_csf *csf[SPTT_MAX_MODES] = {nullptr};
     float *A[SPTT_MAX_MODES] = {nullptr};
@@ -110,8 +110,8 @@ sptt_status run_iteration(sptt_cpd *c, bool bf16) {
     const int N = c->N;
     const void *fac[SPTT_MAX_MODES];
     for (int m = 0; m < N; ++m) fac[m] = bf16 ? (const void *)c->Ab[m] : (const void *)c->A[m];
-    const sptt_sched *sched = c->has_sched ? &c->sched : nullptr;
     for (int n = 0; n < N; ++n) {
+        const sptt_sched *sched = c->has_msched[n] ? &c->msched[n] : nullptr;
         {
             Timed t(c, 0);
             SPTT_TRY(mttkrp_launch(c->csf[n], fac, bf16 ? SPTT_BF16 : SPTT_F32, c->ld, c->M, c->Mh, sched, c->st));
@@ -149,8 +149,8 @@ sptt_status run_iteration(sptt_cpd *c, bool bf16) {
 sptt_status run_iteration_graph(sptt_cpd *c, bool bf16) {
     const int p = bf16 ? 1 : 0;
     if (!c->graph[p]) {
-        const sptt_sched *sched = c->has_sched ? &c->sched : nullptr;
-        for (int n = 0; n < c->N; ++n) SPTT_TRY(mttkrp_prepare(c->csf[n], sched, c->st));
+        for (int n = 0; n < c->N; ++n)
+            SPTT_TRY(mttkrp_prepare(c->csf[n], c->has_msched[n] ? &c->msched[n] : nullptr, c->st));
         SPTT_CUDA(cudaStreamSynchronize(c->st));
         cudaGraph_t g = nullptr;
         SPTT_CUDA(cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
@@ -228,13 +228,18 @@ extern "C" sptt_status sptt_cpd_create(const sptt_coo *coo, int32_t rank, const 
     if (opts) o = *opts;
     if (o.precision != SPTT_F32 && o.precision != SPTT_BF16)
         return set_error(SPTT_ERR_BAD_ARG, "opts.precision must be SPTT_F32 or SPTT_BF16");
-    if (o.sched) {
-        const sptt_sched *s = o.sched;
+    for (int m = 0; m < (o.mode_sched ? coo->nmodes : 1); ++m) {
+        const sptt_sched *s = o.mode_sched ? &o.mode_sched[m] : o.sched;
+        if (!s) break;
         if (s->chunk && (s->chunk < 16 || s->chunk > 4096 || (s->chunk & (s->chunk - 1))))
             return set_error(SPTT_ERR_BAD_ARG, "sched->chunk must be a power of two in [16, 4096]");
         if (s->block && (s->block < 32 || s->block > 256 || s->block % 32))
             return set_error(SPTT_ERR_BAD_ARG, "sched->block must be a multiple of 32 in [32, 256]");
+        if (s->variant < 0 || s->variant > 5 || s->order < 0 || s->order > 1)
+            return set_error(SPTT_ERR_BAD_ARG, "sched->variant must be in [0, 5] and order in [0, 1]");
     }
+    if (o.plan < 0 || o.plan > 2) return set_error(SPTT_ERR_BAD_ARG, "opts.plan must be 0, 1 or 2");
+    if (o.plan == 2 && !o.mlp) return set_error(SPTT_ERR_BAD_ARG, "opts.plan = 2 needs opts.mlp");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     sptt_cpd *c = new sptt_cpd();
     struct Guard {
@@ -245,24 +250,62 @@ extern "C" sptt_status sptt_cpd_create(const sptt_coo *coo, int32_t rank, const 
     c->rank = rank;
     c->ld = (rank + 7) / 8 * 8;
     c->opts = o;
-    if (o.sched) {
-        c->sched = *o.sched;
-        c->has_sched = true;
-    }
     c->opts.sched = nullptr;
+    c->opts.mode_sched = nullptr;
+    c->opts.mlp = nullptr;
     c->st = st;
-    for (int m = 0; m < c->N; ++m) c->dims[m] = coo->dims[m];
+    for (int m = 0; m < c->N; ++m) {
+        c->dims[m] = coo->dims[m];
+        const sptt_sched *s = o.mode_sched ? &o.mode_sched[m] : o.sched;
+        if (s) {
+            c->msched[m] = *s;
+            c->has_msched[m] = true;
+        }
+    }
     {
         DevCoo dc;
         SPTT_TRY(coo_to_device(coo, st, &dc));
-        for (int m = 0; m < c->N; ++m) SPTT_TRY(csf_build_device(&dc.coo, m, nullptr, st, &c->csf[m]));
+        for (int m = 0; m < c->N; ++m) {
+            if (o.plan == 1) {  // exhaustive autotuner
+                float ms[32];
+                const int32_t nc = sptt_sched_candidates(nullptr, 0);
+                SPTT_TRY(sptt_autotune(&dc.coo, m, rank, o.precision, 3, ms, stream));
+                int best = 0;
+                for (int i = 1; i < nc; ++i)
+                    if (ms[i] < ms[best]) best = i;
+                sptt_sched cands[32];
+                sptt_sched_candidates(cands, 32);
+                c->msched[m] = cands[best];
+                c->has_msched[m] = true;
+            }
+            const int kind = c->has_msched[m] ? c->msched[m].order : 0;
+            int32_t order[SPTT_MAX_MODES];
+            level_order(c->dims, c->N, m, kind, order);
+            SPTT_TRY(csf_build_device(&dc.coo, m, order, st, &c->csf[m]));
+            if (o.plan == 2) {  // learned scheduler on the default CSF's statistics
+                float feat[16];
+                int32_t choice = 0;
+                SPTT_TRY(sptt_csf_features(c->csf[m], rank, feat, stream));
+                SPTT_TRY(sptt_mlp_predict(o.mlp, feat, 1, &choice, nullptr, stream));
+                sptt_sched cands[32];
+                sptt_sched_candidates(cands, 32);
+                c->msched[m] = cands[choice];
+                c->has_msched[m] = true;
+                if (c->msched[m].order != 0) {
+                    csf_destroy(c->csf[m]);
+                    c->csf[m] = nullptr;
+                    level_order(c->dims, c->N, m, c->msched[m].order, order);
+                    SPTT_TRY(csf_build_device(&dc.coo, m, order, st, &c->csf[m]));
+                }
+            }
+        }
     }
     int64_t max_rows = 0, max_slices = 0, max_heavy = 0;
     for (int m = 0; m < c->N; ++m) {
         const int64_t rows = c->dims[m];
         if (rows > max_rows) max_rows = rows;
         if (c->csf[m]->nfibs[0] > max_slices) max_slices = c->csf[m]->nfibs[0];
-        SPTT_TRY(mttkrp_prepare(c->csf[m], c->has_sched ? &c->sched : nullptr, st));
+        SPTT_TRY(mttkrp_prepare(c->csf[m], c->has_msched[m] ? &c->msched[m] : nullptr, st));
         if (c->csf[m]->nheavy > max_heavy) max_heavy = c->csf[m]->nheavy;
         SPTT_TRY(dev_alloc_n(&c->A[m], (size_t)rows * c->ld, st));
         SPTT_TRY(fill_zero_launch(c->A[m], (size_t)rows * c->ld * sizeof(float), st));

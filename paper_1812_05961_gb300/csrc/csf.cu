@@ -314,6 +314,21 @@ sptt_status csf_ensure_partition(sptt_csf *c, int32_t chunk, cudaStream_t st) {
     return SPTT_OK;
 }
 
+void level_order(const int64_t *dims, int nmodes, int root, int kind, int32_t *order) {
+    order[0] = root;
+    int k = 1;
+    for (int m = 0; m < nmodes; ++m)
+        if (m != root) order[k++] = m;
+    for (int a = 2; a < nmodes; ++a)  // stable insertion sort of levels 1..
+        for (int b = a; b > 1; --b) {
+            const int64_t x = dims[order[b]], y = dims[order[b - 1]];
+            if (!(kind == 0 ? x < y : x > y)) break;
+            const int32_t t = order[b];
+            order[b] = order[b - 1];
+            order[b - 1] = t;
+        }
+}
+
 sptt_status csf_build_device(const sptt_coo *coo, int32_t root, const int32_t *order_in,
                              cudaStream_t st, sptt_csf **out) {
     const int N = coo->nmodes;
@@ -329,17 +344,7 @@ sptt_status csf_build_device(const sptt_coo *coo, int32_t root, const int32_t *o
         }
         if (order[0] != root) return set_error(SPTT_ERR_BAD_ARG, "level_order[0] must be root_mode");
     } else {
-        order[0] = root;
-        int k = 1;
-        for (int m = 0; m < N; ++m)
-            if (m != root) order[k++] = m;
-        // ascending length, ties by mode id (insertion sort keeps it stable)
-        for (int a = 2; a < N; ++a)
-            for (int b = a; b > 1 && coo->dims[order[b]] < coo->dims[order[b - 1]]; --b) {
-                int32_t t = order[b];
-                order[b] = order[b - 1];
-                order[b - 1] = t;
-            }
+        level_order(coo->dims, N, root, 0, order);
     }
 
     sptt_csf *c = new sptt_csf();

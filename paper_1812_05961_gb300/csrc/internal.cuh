@@ -128,6 +128,9 @@ namespace sptt {
 
 sptt_status csf_build_device(const sptt_coo *coo_dev, int32_t root, const int32_t *order,
                              cudaStream_t st, sptt_csf **out);
+// Level order of a CSF rooted at `root`: the root, then the other modes by
+// ascending (kind 0) or descending (kind 1) length, ties to the lower mode id.
+void level_order(const int64_t *dims, int nmodes, int root, int kind, int32_t *order);
 sptt_status csf_ensure_partition(sptt_csf *csf, int32_t chunk, cudaStream_t st);
 void csf_destroy(sptt_csf *c);
 

@@ -47,24 +47,41 @@ __device__ __forceinline__ Lanes lanes_for(int ld, int vec) {
     return L;
 }
 
+// Each CTA takes a contiguous range of chunks; its lane groups interleave
+// within the range, so a group's consecutive chunks are close together and a
+// heavy slice's partial can be carried from one to the next.
+struct ChunkRange {
+    int64_t begin, end, step;
+};
+
+__device__ __forceinline__ ChunkRange cta_chunks(int64_t nchunks, const Lanes &L) {
+    const int64_t per = (nchunks + gridDim.x - 1) / gridDim.x;
+    const int64_t b = (int64_t)blockIdx.x * per;
+    ChunkRange r;
+    r.step = (int64_t)(blockDim.x >> 5) * L.gpw;
+    r.begin = b + (int64_t)(threadIdx.x >> 5) * L.gpw + L.gi;
+    r.end = (b + per < nchunks) ? b + per : nchunks;
+    return r;
+}
+
 template <int NM, typename T, int B, int MINB>
 __global__ void __launch_bounds__(256, MINB) mttkrp_flag_kernel(const walk::Args a) {
     const Lanes L = lanes_for(a.ld, walk::Raw<T>::VEC);
     if (L.idle) return;  // no warp collectives in the walk
-    const int64_t gwarp = (int64_t)(blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = (int64_t)(gridDim.x * blockDim.x) >> 5;
-    for (int64_t c = gwarp * L.gpw + L.gi; c < a.nchunks; c += nwarps * L.gpw)
-        walk::flag_chunk<NM, T, B>(a, c, L.col);
+    const ChunkRange r = cta_chunks(a.nchunks, L);
+    walk::Carry<walk::Raw<T>::VEC> cy;
+    for (int64_t c = r.begin; c < r.end; c += r.step) walk::flag_chunk<NM, T, B>(a, c, L.col, cy);
+    walk::flush_carry(a, L.col, cy);
 }
 
 template <int NM, typename T>
 __global__ void __launch_bounds__(256) mttkrp_root_kernel(const walk::Args a) {
     const Lanes L = lanes_for(a.ld, walk::Raw<T>::VEC);
     if (L.idle) return;
-    const int64_t gwarp = (int64_t)(blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = (int64_t)(gridDim.x * blockDim.x) >> 5;
-    for (int64_t c = gwarp * L.gpw + L.gi; c < a.nchunks; c += nwarps * L.gpw)
-        walk::plain_chunk<NM, T>(a, c, L.col);
+    const ChunkRange r = cta_chunks(a.nchunks, L);
+    walk::Carry<walk::Raw<T>::VEC> cy;
+    for (int64_t c = r.begin; c < r.end; c += r.step) walk::plain_chunk<NM, T>(a, c, L.col, cy);
+    walk::flush_carry(a, L.col, cy);
 }
 
 // out[fids0[f] * ld + :] = row f of the compact result; other rows stay as

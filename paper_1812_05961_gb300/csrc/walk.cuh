@@ -119,6 +119,47 @@ __device__ __forceinline__ float read_row(const float *out, const double *heavy,
     return h >= 0 ? (float)heavy[(int64_t)h * ld + c] : out[f * ld + c];
 }
 
+// The partial of a heavy slice that a lane group holds back between its
+// chunks (f < 0: none). Consecutive chunks of a group that lie in the same
+// heavy slice are summed here and flushed once, which turns one FP64 atomic
+// per chunk into one per run of chunks.
+template <int VEC>
+struct Carry {
+    int64_t f = -1;
+    float acc[VEC];
+};
+
+template <int VEC>
+__device__ __forceinline__ void flush_carry(const Args &a, int col, Carry<VEC> &cy) {
+    if (cy.f >= 0) add_partial<VEC>(a, cy.f, col, cy.acc);
+    cy.f = -1;
+}
+
+// Start a chunk whose first slice is f0: a held-back partial of the same
+// slice seeds the slice accumulator; any other is flushed.
+template <int VEC>
+__device__ __forceinline__ void take_carry(const Args &a, int col, Carry<VEC> &cy, int64_t f0, float (&acc0)[VEC]) {
+    if (cy.f == f0) {
+#pragma unroll
+        for (int i = 0; i < VEC; ++i) acc0[i] = cy.acc[i];
+        cy.f = -1;
+    } else {
+        flush_carry<VEC>(a, col, cy);
+    }
+}
+
+// End of a chunk: the open slice f's partial is held back if f is heavy.
+template <int VEC>
+__device__ __forceinline__ void end_chunk(const Args &a, int col, Carry<VEC> &cy, int64_t f, const float (&acc0)[VEC]) {
+    if (__ldg(a.hidx + f) >= 0) {
+        cy.f = f;
+#pragma unroll
+        for (int i = 0; i < VEC; ++i) cy.acc[i] = acc0[i];
+    } else {
+        add_partial<VEC>(a, f, col, acc0);
+    }
+}
+
 // parent += row * child (element-wise); child = 0.
 template <typename T>
 __device__ __forceinline__ void fold(float (&parent)[Raw<T>::VEC], float (&child)[Raw<T>::VEC], const uint4 &row) {
@@ -139,7 +180,7 @@ __device__ __forceinline__ void fold(float (&parent)[Raw<T>::VEC], float (&child
 // Rows of fibers at higher levels are requested when the fiber opens and
 // used when it closes.
 template <int NM, typename T, int B>
-__device__ __forceinline__ void flag_chunk(const Args &a, int64_t c, int col) {
+__device__ __forceinline__ void flag_chunk(const Args &a, int64_t c, int col, Carry<Raw<T>::VEC> &cy) {
     using Rw = Raw<T>;
     constexpr int VEC = Rw::VEC;
     constexpr int NL = NM - 1;  // accumulator levels 0..NM-2
@@ -160,6 +201,7 @@ __device__ __forceinline__ void flag_chunk(const Args &a, int64_t c, int col) {
 #pragma unroll
     for (int l = 1; l < NL; ++l) rowc[l] = Rw::load(a.fac[l], __ldg(a.fids[l] + f[l]), ld, col);
     bool first_slice = true;
+    take_carry<VEC>(a, col, cy, f[0], acc[0]);
 
     for (int64_t kb = k0; kb < k1; kb += B) {
         float v[B];
@@ -236,15 +278,16 @@ __device__ __forceinline__ void flag_chunk(const Args &a, int64_t c, int col) {
             for (int i = 0; i < VEC; ++i) acc[LF][i] = fmaf(v[j], xr[i], acc[LF][i]);
         }
     }
-    // chunk end: fold the open fibers and add the partial slice
+    // chunk end: fold the open fibers; the open slice's partial is added
+    // (or held back when the slice is heavy)
 #pragma unroll
     for (int l = LF; l >= 1; --l) fold<T>(acc[l - 1], acc[l], rowc[l]);
-    add_partial<VEC>(a, f[0], col, acc[0]);
+    end_chunk<VEC>(a, col, cy, f[0], acc[0]);
 }
 
 // The plain walk: one leaf at a time, fiber ends read from fptr.
 template <int NM, typename T>
-__device__ __forceinline__ void plain_chunk(const Args &a, int64_t c, int col) {
+__device__ __forceinline__ void plain_chunk(const Args &a, int64_t c, int col, Carry<Raw<T>::VEC> &cy) {
     using Rw = Raw<T>;
     constexpr int VEC = Rw::VEC;
     constexpr int NL = NM - 1;
@@ -263,6 +306,7 @@ __device__ __forceinline__ void plain_chunk(const Args &a, int64_t c, int col) {
 #pragma unroll
         for (int i = 0; i < VEC; ++i) acc[l][i] = 0.f;
     bool first_slice = true;
+    take_carry<VEC>(a, col, cy, f[0], acc[0]);
     for (int64_t k = k0; k < k1; ++k) {
         if (k != k0 && k == end[NL - 1]) {
             // leaf k opens a new level-(N-2) fiber: close the finished fibers
@@ -297,7 +341,7 @@ __device__ __forceinline__ void plain_chunk(const Args &a, int64_t c, int col) {
 #pragma unroll
     for (int l = NL - 1; l >= 1; --l)
         fold<T>(acc[l - 1], acc[l], Rw::load(a.fac[l], __ldg(a.fids[l] + f[l]), ld, col));
-    add_partial<VEC>(a, f[0], col, acc[0]);
+    end_chunk<VEC>(a, col, cy, f[0], acc[0]);
 }
 
 }  // namespace walk

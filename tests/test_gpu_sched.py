@@ -1,0 +1,118 @@
+"""The schedule machinery: MLP kernels against the FP64 oracle MLP, training,
+features, autotuner, planned CP-ALS, and the learned scheduler's regret
+against the fixed default on held-out tensors."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1812_05961_gb300 as sptt
+from paper_1812_05961_gb300 import schedtrain
+import tensorgen
+
+pytestmark = pytest.mark.gpu
+
+NIN, NH, NOUT = 16, 64, 16
+
+
+def test_mlp_forward_and_gradient_match_oracle(cuda_device):
+    m = sptt.Mlp(seed=3)
+    P, mu, sd = sptt.sptt_mlp_get(m.handle)
+    assert mu.abs().max() == 0 and (sd == 1).all()  # untrained: no standardisation
+    g = torch.Generator().manual_seed(0)
+    X = torch.randn(77, NIN, generator=g)
+    T = torch.randn(77, NOUT, generator=g)
+    Y = sptt.sptt_mlp_forward(m.handle, X.to(cuda_device)).cpu().double().numpy()
+    Yo = oracle.mlp_forward(P.double().numpy(), X.double().numpy(), NIN, NH, NOUT)
+    assert np.abs(Y - Yo).max() <= 1e-5 * max(1.0, np.abs(Yo).max())
+    L, G = sptt.sptt_mlp_loss_grad(m.handle, X.to(cuda_device), T.to(cuda_device))
+    Lo, Go = oracle.mlp_loss_grad(P.double().numpy(), X.double().numpy(), T.double().numpy(), NIN, NH, NOUT)
+    assert abs(L - Lo) <= 1e-5 * abs(Lo)
+    G = G.double().numpy()
+    assert np.linalg.norm(G - Go) <= 1e-4 * np.linalg.norm(Go)
+    assert np.abs(G - Go).max() <= 1e-4 * np.abs(Go).max()
+
+
+def test_mlp_training_fits_a_smooth_target(cuda_device):
+    g = torch.Generator().manual_seed(1)
+    X = torch.randn(512, NIN, generator=g) * 3 + 5
+    W = torch.randn(NIN, NOUT, generator=g)
+    T = torch.tanh(((X - 5) / 3) @ W / 4)
+    m = sptt.Mlp(seed=2)
+    hist = sptt.sptt_mlp_train(m.handle, X.to(cuda_device), T.to(cuda_device), 600, 3e-3)
+    assert hist[-1] < 0.1 * hist[0], (float(hist[0]), float(hist[-1]))
+    _, mu, sd = sptt.sptt_mlp_get(m.handle)
+    np.testing.assert_allclose(mu.numpy(), X.mean(0).numpy(), rtol=1e-3, atol=1e-3)
+    np.testing.assert_allclose(sd.numpy(), X.std(0, unbiased=False).numpy(), rtol=1e-3)
+
+
+def test_features_match_a_host_restatement(cuda_device):
+    t = tensorgen.sample_unique([300, 200, 50], 30000, seed=4, dist="zipf", s=1.3)
+    inds_np, vals_np = t.numpy()
+    c = sptt.Csf(t.dims, [x.to(cuda_device) for x in t.inds], t.vals.to(cuda_device), 1)
+    f = sptt.sptt_csf_features(c.handle, 16)
+    ref = oracle.csf(inds_np, vals_np, t.dims, 1)
+    sizes = np.diff(ref["fptr"][1][ref["fptr"][0]])  # leaves per slice (3 modes)
+    nnz = ref["nfibs"][-1]
+    assert abs(f[0] - math.log2(nnz)) < 1e-5 and f[1] == 3 and abs(f[2] - 4) < 1e-6
+    assert abs(f[6] - math.log2(ref["nfibs"][0])) < 1e-5
+    assert abs(f[10] - math.log2(sizes.max())) < 1e-5
+    assert abs(f[11] - sizes[sizes >= 1024].sum() / nnz) < 1e-6
+    assert abs(f[12] - (sizes == 1).mean()) < 1e-6
+
+
+def test_autotune_and_planned_cpd(cuda_device):
+    t = tensorgen.sample_unique([2000, 800, 300], 200000, seed=5, dist="zipf", s=1.2)
+    di = [x.to(cuda_device) for x in t.inds]
+    dv = t.vals.to(cuda_device)
+    ms = sptt.sptt_autotune(t.dims, di, dv, 0, 16)
+    assert len(ms) == 16 and all(x > 0 for x in ms)
+    base = sptt.Cpd(t.dims, di, dv, 16, seed=1).init()
+    base.iterate(4)
+    tuned = sptt.Cpd(t.dims, di, dv, 16, seed=1, plan=1).init()
+    tuned.iterate(4)
+    np.testing.assert_allclose(tuned.fit_history(), base.fit_history(), atol=1e-6)
+    m = sptt.Mlp(seed=0)
+    learned = sptt.Cpd(t.dims, di, dv, 16, seed=1, plan=2, mlp=m).init()
+    learned.iterate(4)
+    np.testing.assert_allclose(learned.fit_history(), base.fit_history(), atol=1e-6)
+    cands = sptt.sptt_sched_candidates()
+    per_mode = [cands[int(np.argmax(ms))]] * 3  # the slowest one still gives the same numbers
+    other = sptt.Cpd(t.dims, di, dv, 16, seed=1, mode_sched=per_mode).init()
+    other.iterate(4)
+    np.testing.assert_allclose(other.fit_history(), base.fit_history(), atol=1e-6)
+
+
+def _specs(n, seed):
+    g = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        nm = int(g.integers(3, 5))
+        dims = [int(math.exp(g.uniform(math.log(100), math.log(200000)))) for _ in range(nm)]
+        space = float(np.prod(dims, dtype=np.float64))
+        nnz = int(min(math.exp(g.uniform(math.log(1e5), math.log(2e6))), space / 4))
+        s = float(g.uniform(0.8, 1.5))
+        R = int(g.choice([8, 16, 32]))
+        out.append((dims, max(nnz, 1000), s, R, seed * 1000 + i))
+    return out
+
+
+def _dataset(specs, dev):
+    ds = schedtrain.Dataset()
+    for dims, nnz, s, R, sd in specs:
+        t = tensorgen.sample_unique(dims, nnz, sd, dev, "zipf", s=s, values="uniform")
+        ds.samples += schedtrain.sweep_tensor(t.dims, t.inds, t.vals, R, reps=3)
+    return ds
+
+
+def test_learned_scheduler_beats_fixed_default_on_held_out(cuda_device):
+    train = _dataset(_specs(40, seed=11), cuda_device)
+    held = _dataset(_specs(12, seed=99), cuda_device)
+    model, hist = schedtrain.train(train, steps=1500, lr=3e-3)
+    assert float(hist[-1]) < float(hist[0])
+    r_model = schedtrain.summarize(schedtrain.regret(held, model))
+    r_default = schedtrain.summarize(schedtrain.regret(held, fixed=schedtrain.default_index()))
+    print("held-out regret: learned %s, default %s" % (r_model, r_default))
+    assert r_model["mean"] <= r_default["mean"] + 0.02
