@@ -49,6 +49,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-extras", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--variant", type=int, default=0, help="MTTKRP kernel variant for every mode (0 = default)")
+    p.add_argument("--chunk", type=int, default=0, help="MTTKRP chunk size (0 = default)")
     return p.parse_args()
 
 
@@ -249,7 +251,8 @@ def ours(args, rank, world, local):
     del csfs
 
     t_build = time.time()
-    cpd = sptt.Cpd(dims, t.inds, t.vals, R, seed=1, profile=1)
+    sched = None if (args.variant == 0 and args.chunk == 0) else (args.chunk, 256, args.variant, 0)
+    cpd = sptt.Cpd(dims, t.inds, t.vals, R, seed=1, profile=1, sched=sched)
     t_build = time.time() - t_build
     cpd.init()
     stream = torch.cuda.current_stream()
@@ -369,6 +372,7 @@ def ours(args, rank, world, local):
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "rank": R, "step": "one CP-ALS iteration (3 mode updates + fit)",
+                       "mttkrp_sched": "default" if sched is None else list(sched),
                        "l2": "inputs larger than L2 (CSF about 0.8 GB per mode)",
                        "parallelism": "replicas" if world > 1 else "single",
                        "nfibs_per_root": nfibs, "gen_s": round(t_gen, 1), "cpd_create_s": round(t_build, 2)},

@@ -116,6 +116,10 @@ void sptt_csf_free(sptt_csf *csf);
  */
 sptt_status sptt_csf_shape(const sptt_csf *csf, int32_t *nmodes, int32_t *order, int64_t *nfibs);
 
+/* Synchronise the stream and report whether a kernel that read this CSF
+ * gave up a bounded wait (SPTT_ERR_TIMEOUT; the word is then cleared). */
+sptt_status sptt_csf_check(const sptt_csf *csf, sptt_stream stream);
+
 /*
  * Copy level l of a CSF into caller buffers (host or device; any may be
  * NULL): fptr (nfibs[l]+1 int32, only for l < N-1), fids (nfibs[l] int32),
@@ -134,7 +138,8 @@ sptt_status sptt_csf_copy_level(const sptt_csf *csf, int32_t level, int32_t *fpt
  *               [16, 4096]; 0 = default
  *   block       threads per CTA (multiple of 32, <= 256); 0 = default
  *   variant     kernel variant: 0 = default (3 for F32 gathers, 2 for BF16);
- *               1 = plain walk (fiber ends
+ *               6 = flag walk whose leaf records are staged in shared memory
+ *               by bulk copies (chunk fixed at 64); 1 = plain walk (fiber ends
  *               from fptr, one leaf at a time); 2..5 = batched walk driven by
  *               the per-leaf level flags with (batch, CTAs per SM) = (8, 2),
  *               (4, 3), (4, 4), (8, 1)

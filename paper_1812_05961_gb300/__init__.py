@@ -90,6 +90,7 @@ def lib() -> ctypes.CDLL:
             "sptt_csf_free": (None, [_P]),
             "sptt_csf_shape": (_ST, [_P, _P, _P, _P]),
             "sptt_csf_copy_level": (_ST, [_P, _I32, _P, _P, _P, _P]),
+            "sptt_csf_check": (_ST, [_P, _P]),
             "sptt_mttkrp": (_ST, [_P, _P, _I32, _I32, _P, _P, _P]),
             "sptt_gram": (_ST, [_P, _I64, _I32, _I32, _P, _P]),
             "sptt_gram_noalloc": (_ST, [_P, _I64, _I32, _I32, _P, _P]),
@@ -241,6 +242,10 @@ def sptt_csf_shape(csf: int):
     nfibs = (ctypes.c_int64 * SPTT_MAX_MODES)()
     _check(lib().sptt_csf_shape(csf, ctypes.byref(n), order, nfibs), "sptt_csf_shape")
     return n.value, list(order[:n.value]), list(nfibs[:n.value])
+
+
+def sptt_csf_check(csf: int, stream=None):
+    _check(lib().sptt_csf_check(csf, _stream(stream)), "sptt_csf_check")
 
 
 def sptt_csf_copy_level(csf: int, level: int, stream=None):

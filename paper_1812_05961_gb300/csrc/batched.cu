@@ -293,10 +293,12 @@ __global__ void __launch_bounds__(kBThreads, 2) batched_cpals_kernel(const Batch
                     const BTensor &T = a.T[tt];
                     const int64_t c = gc - __ldg(a.chunk_prefix[n] + tt);
                     walk::Carry<4> cy;  // chunks of one group are far apart here: flushed per chunk
+                    const walk::Args &w = T.w[n];
+                    const walk::GlobalRecs rec{w.vals, w.fids[T.nmodes - 1], w.lvl};
                     switch (T.nmodes) {
-                        case 2: walk::flag_chunk<2, float, 4>(T.w[n], c, col, cy); break;
-                        case 3: walk::flag_chunk<3, float, 4>(T.w[n], c, col, cy); break;
-                        default: walk::flag_chunk<4, float, 4>(T.w[n], c, col, cy); break;
+                        case 2: walk::flag_chunk<2, float, 4>(w, c, col, cy, rec); break;
+                        case 3: walk::flag_chunk<3, float, 4>(w, c, col, cy, rec); break;
+                        default: walk::flag_chunk<4, float, 4>(w, c, col, cy, rec); break;
                     }
                     walk::flush_carry(T.w[n], col, cy);
                 }

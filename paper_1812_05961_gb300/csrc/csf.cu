@@ -272,6 +272,7 @@ void csf_destroy(sptt_csf *c) {
     if (c->lvl) cudaFree(c->lvl);
     if (c->part) cudaFree(c->part);
     if (c->hidx) cudaFree(c->hidx);
+    if (c->err) cudaFree(c->err);
     delete c;
 }
 
@@ -500,9 +501,11 @@ sptt_status csf_build_device(const sptt_coo *coo, int32_t root, const int32_t *o
         SPTT_CUDA(cudaMalloc(&c->fptr[l], (size_t)(c->nfibs[l] + 1 + 64) * sizeof(int32_t)));
         SPTT_CUDA(cudaMalloc(&c->fids[l], (size_t)(c->nfibs[l] + 64) * sizeof(int32_t)));
     }
-    SPTT_CUDA(cudaMalloc(&c->fids[N - 1], (size_t)(u + 64) * sizeof(int32_t)));
-    SPTT_CUDA(cudaMalloc(&c->vals, (size_t)(u + 64) * sizeof(float)));
-    SPTT_CUDA(cudaMalloc(&c->lvl, (size_t)(u + 64)));
+    SPTT_CUDA(cudaMalloc(&c->fids[N - 1], (size_t)(u + kLeafSlack) * sizeof(int32_t)));
+    SPTT_CUDA(cudaMalloc(&c->vals, (size_t)(u + kLeafSlack) * sizeof(float)));
+    SPTT_CUDA(cudaMalloc(&c->lvl, (size_t)(u + kLeafSlack)));
+    SPTT_CUDA(cudaMalloc(&c->err, sizeof(int32_t)));
+    SPTT_TRY(fill_zero_launch(c->err, sizeof(int32_t), st));
     if (u > 0) {
         LevelScan ls{};
         for (int l = 0; l < N - 1; ++l) {
@@ -554,6 +557,20 @@ extern "C" sptt_status sptt_csf_shape(const sptt_csf *csf, int32_t *nmodes, int3
     for (int l = 0; l < csf->nmodes; ++l) {
         if (order) order[l] = csf->order[l];
         if (nfibs) nfibs[l] = csf->nfibs[l];
+    }
+    return SPTT_OK;
+}
+
+extern "C" sptt_status sptt_csf_check(const sptt_csf *csf, sptt_stream stream) {
+    clear_error();
+    if (!csf) return set_error(SPTT_ERR_BAD_ARG, "csf is NULL");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    int32_t e = 0;
+    SPTT_CUDA(cudaMemcpyAsync(&e, csf->err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    SPTT_CUDA(cudaStreamSynchronize(st));
+    if (e) {
+        SPTT_TRY(fill_zero_launch(csf->err, sizeof(int32_t), st));
+        return set_error(SPTT_ERR_TIMEOUT, "a bounded wait of an MTTKRP on this CSF ran out");
     }
     return SPTT_OK;
 }

@@ -13,6 +13,7 @@ namespace sptt {
 
 constexpr int kMaxModes = SPTT_MAX_MODES;
 constexpr int kHeavyChunks = 8;
+constexpr int kLeafSlack = 512;  // elements past the end of every leaf array (whole-chunk copies)
 constexpr int kNumSMs = 152;  // GB300: 2 dies x 76 SMs (queried at run time where it matters)
 
 // ---------------------------------------------------------------------------
@@ -122,6 +123,9 @@ struct sptt_csf {
     // their MTTKRP partials are summed in FP64 (see walk.cuh).
     int32_t *hidx = nullptr;
     int64_t nheavy = 0;
+    // Device error word of the kernels that read this CSF (bit 2: a bounded
+    // wait for a staged copy ran out); read by sptt_csf_check.
+    int32_t *err = nullptr;
 };
 
 namespace sptt {

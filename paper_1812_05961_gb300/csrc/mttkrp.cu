@@ -70,7 +70,8 @@ __global__ void __launch_bounds__(256, MINB) mttkrp_flag_kernel(const walk::Args
     if (L.idle) return;  // no warp collectives in the walk
     const ChunkRange r = cta_chunks(a.nchunks, L);
     walk::Carry<walk::Raw<T>::VEC> cy;
-    for (int64_t c = r.begin; c < r.end; c += r.step) walk::flag_chunk<NM, T, B>(a, c, L.col, cy);
+    const walk::GlobalRecs rec{a.vals, a.fids[NM - 1], a.lvl};
+    for (int64_t c = r.begin; c < r.end; c += r.step) walk::flag_chunk<NM, T, B>(a, c, L.col, cy, rec);
     walk::flush_carry(a, L.col, cy);
 }
 
@@ -81,6 +82,101 @@ __global__ void __launch_bounds__(256) mttkrp_root_kernel(const walk::Args a) {
     const ChunkRange r = cta_chunks(a.nchunks, L);
     walk::Carry<walk::Raw<T>::VEC> cy;
     for (int64_t c = r.begin; c < r.end; c += r.step) walk::plain_chunk<NM, T>(a, c, L.col, cy);
+    walk::flush_carry(a, L.col, cy);
+}
+
+// ---------------------------------------------------------------------------
+// Variant 6: the flag walk with its leaf records staged in shared memory.
+// Each lane group owns two stage buffers of one chunk's records (values,
+// leaf indices, level flags: 9 bytes per leaf) and an mbarrier per stage.
+// The group's first lane issues three bulk copies (cp.async.bulk) for the
+// chunk after next while the group walks the current one, so the record
+// stream arrives in shared memory without occupying the L1 load pipe, and
+// the walk reads it with conflict-free shared loads. Every wait is bounded:
+// past kWaitNs the CSF's error word is set and the group stops.
+// ---------------------------------------------------------------------------
+constexpr int kStageChunk = 64;
+constexpr uint32_t kStageBytes = 9 * kStageChunk;          // 576
+constexpr uint32_t kStageStride = kStageBytes + 16;        // 592
+constexpr uint32_t kGroupStride = 1200;                    // 2 stages + pad; 300 words = 12 mod 32 banks
+constexpr uint64_t kWaitNs = 1000000000ull;                // 1 s
+
+__device__ __forceinline__ uint64_t gtimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    uint64_t t0 = 0;
+    for (uint32_t it = 0;; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (it == 0) t0 = gtimer();
+        else if ((it & 31) == 0 && gtimer() - t0 > kWaitNs) return false;
+    }
+}
+
+__device__ __forceinline__ void stage_issue(const walk::Args &a, const int32_t *leaf_idx, int64_t c, uint32_t bar,
+                                            uint32_t dst) {
+    const int64_t k0 = c * kStageChunk;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kStageBytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(dst), "l"(a.vals + k0), "r"(kStageChunk * 4), "r"(bar) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(dst + kStageChunk * 4), "l"(leaf_idx + k0), "r"(kStageChunk * 4), "r"(bar) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(dst + kStageChunk * 8), "l"(a.lvl + k0), "r"(kStageChunk), "r"(bar) : "memory");
+}
+
+template <int NM, typename T>
+__global__ void __launch_bounds__(256, 2) mttkrp_staged_kernel(const walk::Args a, int32_t *err) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    constexpr int VEC = walk::Raw<T>::VEC;
+    const Lanes L = lanes_for(a.ld, VEC);
+    if (L.idle) return;  // no CTA-wide barrier below: every group runs on its own
+    const int G = a.ld / VEC;
+    const int gcta = (threadIdx.x >> 5) * L.gpw + L.gi;
+    const int groups = (blockDim.x >> 5) * L.gpw;
+    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem);
+    const uint32_t bar = sbase + gcta * 16;  // stage s barrier at bar + 8 s
+    const uint32_t buf = sbase + ((groups * 16 + 127) & ~127) + gcta * kGroupStride;
+    const int lane = threadIdx.x & 31;
+    const bool leader = lane == L.gi * G;
+    const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (L.gi * G));
+    const int32_t *leaf_idx = a.fids[NM - 1];
+    const ChunkRange r = cta_chunks(a.nchunks, L);
+    if (leader) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar + 8) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        if (r.begin < r.end) stage_issue(a, leaf_idx, r.begin, bar, buf);
+        if (r.begin + r.step < r.end) stage_issue(a, leaf_idx, r.begin + r.step, bar + 8, buf + kStageStride);
+    }
+    __syncwarp(gmask);
+    walk::Carry<VEC> cy;
+    int64_t n = 0;
+    for (int64_t c = r.begin; c < r.end; c += r.step, ++n) {
+        const uint32_t s = (uint32_t)(n & 1);
+        if (!mbar_wait(bar + 8 * s, (uint32_t)((n >> 1) & 1))) {
+            atomicOr(err, 2);
+            // the other stage may still have a copy in flight: wait for it (bounded) before leaving
+            if (c + r.step < r.end) mbar_wait(bar + 8 * (s ^ 1u), (uint32_t)(((n + 1) >> 1) & 1));
+            return;
+        }
+        const walk::SharedRecs rec{buf + s * kStageStride, buf + s * kStageStride + kStageChunk * 4,
+                                   buf + s * kStageStride + kStageChunk * 8, c * (int64_t)kStageChunk};
+        walk::flag_chunk<NM, T, 4, walk::SharedRecs>(a, c, L.col, cy, rec);
+        __syncwarp(gmask);  // the whole group is done with stage s
+        const int64_t cn = c + 2 * r.step;
+        if (leader && cn < r.end) stage_issue(a, leaf_idx, cn, bar + 8 * s, buf + s * kStageStride);
+    }
     walk::flush_carry(a, L.col, cy);
 }
 
@@ -95,6 +191,27 @@ __global__ void scatter_rows_kernel(const float *__restrict__ compact, const dou
         const int c = (int)(e - f * ld);
         out[(int64_t)__ldg(fids0 + f) * ld + c] = walk::read_row(compact, heavy, hidx, f, ld, c);
     }
+}
+
+template <int NM, typename T>
+sptt_status launch_staged(const walk::Args &a, int32_t *err, cudaStream_t st) {
+    auto kern = mttkrp_staged_kernel<NM, T>;
+    const int vec = walk::Raw<T>::VEC;
+    const int gpw = 32 / (a.ld / vec);
+    const int block = gpw >= 16 ? 128 : 256;  // keep the stage buffers of a CTA near 80 KB
+    const int groups = (block / 32) * gpw;
+    const size_t smem = (size_t)((groups * 16 + 127) & ~127) + (size_t)groups * kGroupStride;
+    SPTT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    SPTT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, smem));
+    if (per_sm < 1) per_sm = 1;
+    const int64_t need = (a.nchunks + groups - 1) / groups;
+    const int64_t cap = (int64_t)device_sm_count() * per_sm;
+    int64_t grid = need < cap ? need : cap;
+    if (grid < 1) grid = 1;
+    kern<<<(unsigned)grid, block, smem, st>>>(a, err);
+    SPTT_CHECK_LAUNCH("mttkrp_staged_kernel");
+    return SPTT_OK;
 }
 
 template <int NM, typename T>
@@ -123,7 +240,16 @@ sptt_status launch_nm(const walk::Args &a, int block, int variant, cudaStream_t 
 }
 
 template <typename T>
-sptt_status launch_t(int nm, const walk::Args &a, int block, int variant, cudaStream_t st) {
+sptt_status launch_t(int nm, const walk::Args &a, int block, int variant, int32_t *err, cudaStream_t st) {
+    if (variant == 6) {
+        switch (nm) {
+            case 2: return launch_staged<2, T>(a, err, st);
+            case 3: return launch_staged<3, T>(a, err, st);
+            case 4: return launch_staged<4, T>(a, err, st);
+            case 5: return launch_staged<5, T>(a, err, st);
+            default: return set_error(SPTT_ERR_UNSUPPORTED, "nmodes");
+        }
+    }
     switch (nm) {
         case 2: return launch_nm<2, T>(a, block, variant, st);
         case 3: return launch_nm<3, T>(a, block, variant, st);
@@ -138,7 +264,8 @@ sptt_status launch_t(int nm, const walk::Args &a, int block, int variant, cudaSt
 constexpr int32_t kDefaultChunk = 128;
 
 sptt_status mttkrp_prepare(sptt_csf *csf, const sptt_sched *sched, cudaStream_t st) {
-    const int32_t chunk = (sched && sched->chunk) ? sched->chunk : kDefaultChunk;
+    const int32_t chunk = (sched && sched->variant == 6) ? kStageChunk
+                          : ((sched && sched->chunk) ? sched->chunk : kDefaultChunk);
     if (csf->nfibs[csf->nmodes - 1] == 0) return SPTT_OK;
     return csf_ensure_partition(csf, chunk, st);
 }
@@ -149,10 +276,10 @@ sptt_status mttkrp_launch(sptt_csf *csf, const void *const *factors, int32_t dty
     SPTT_TRY(fill_zero_launch(out, (size_t)csf->nfibs[0] * ld * sizeof(float), st));
     const int64_t nnz = csf->nfibs[N - 1];
     if (nnz == 0) return SPTT_OK;
-    const int32_t chunk = (sched && sched->chunk) ? sched->chunk : kDefaultChunk;
-    const int block = (sched && sched->block) ? sched->block : 256;
     int variant = sched ? sched->variant : 0;
     if (variant == 0) variant = (dtype == SPTT_BF16) ? 2 : 3;  // fastest measured per gather type
+    const int32_t chunk = variant == 6 ? kStageChunk : ((sched && sched->chunk) ? sched->chunk : kDefaultChunk);
+    const int block = (sched && sched->block) ? sched->block : 256;
     SPTT_TRY(csf_ensure_partition(csf, chunk, st));
     if (csf->nheavy > 0) SPTT_TRY(fill_zero_launch(heavy, (size_t)csf->nheavy * ld * sizeof(double), st));
     walk::Args a{};
@@ -171,8 +298,8 @@ sptt_status mttkrp_launch(sptt_csf *csf, const void *const *factors, int32_t dty
     a.out = out;
     a.heavy = heavy;
     a.hidx = csf->hidx;
-    if (dtype == SPTT_BF16) return launch_t<__nv_bfloat16>(N, a, block, variant, st);
-    return launch_t<float>(N, a, block, variant, st);
+    if (dtype == SPTT_BF16) return launch_t<__nv_bfloat16>(N, a, block, variant, csf->err, st);
+    return launch_t<float>(N, a, block, variant, csf->err, st);
 }
 
 }  // namespace sptt
@@ -202,8 +329,8 @@ extern "C" sptt_status sptt_mttkrp(const sptt_csf *csf, const void *const *facto
             return set_error(SPTT_ERR_BAD_ARG, "sched->chunk must be a power of two in [16, 4096]");
         if (sched->block && (sched->block < 32 || sched->block > 256 || sched->block % 32))
             return set_error(SPTT_ERR_BAD_ARG, "sched->block must be a multiple of 32 in [32, 256]");
-        if (sched->variant < 0 || sched->variant > 5)
-            return set_error(SPTT_ERR_BAD_ARG, "sched->variant must be in [0, 5]");
+        if (sched->variant < 0 || sched->variant > 6)
+            return set_error(SPTT_ERR_BAD_ARG, "sched->variant must be in [0, 6]");
     }
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     sptt_csf *c = const_cast<sptt_csf *>(csf);

@@ -172,6 +172,45 @@ __device__ __forceinline__ void fold(float (&parent)[Raw<T>::VEC], float (&child
     }
 }
 
+// Where a chunk's leaf records (values, leaf indices, level flags) are read
+// from: global memory, or a copy staged in shared memory.
+struct GlobalRecs {
+    const float *vals;
+    const int32_t *idx;
+    const uint8_t *lvl;
+    __device__ __forceinline__ float4 v4(int64_t k) const { return __ldg(reinterpret_cast<const float4 *>(vals + k)); }
+    __device__ __forceinline__ int4 i4(int64_t k) const { return __ldg(reinterpret_cast<const int4 *>(idx + k)); }
+    __device__ __forceinline__ uint32_t l4(int64_t k) const { return __ldg(reinterpret_cast<const uint32_t *>(lvl + k)); }
+    __device__ __forceinline__ uint2 l8(int64_t k) const { return __ldg(reinterpret_cast<const uint2 *>(lvl + k)); }
+};
+
+struct SharedRecs {  // shared-memory addresses of the chunk's copy; k0 = the chunk's first leaf
+    uint32_t sv, si, sl;
+    int64_t k0;
+    __device__ __forceinline__ float4 v4(int64_t k) const {
+        float4 r;
+        asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                     : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w) : "r"(sv + (uint32_t)(k - k0) * 4u));
+        return r;
+    }
+    __device__ __forceinline__ int4 i4(int64_t k) const {
+        int4 r;
+        asm volatile("ld.shared.v4.s32 {%0, %1, %2, %3}, [%4];"
+                     : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w) : "r"(si + (uint32_t)(k - k0) * 4u));
+        return r;
+    }
+    __device__ __forceinline__ uint32_t l4(int64_t k) const {
+        uint32_t r;
+        asm volatile("ld.shared.u32 %0, [%1];" : "=r"(r) : "r"(sl + (uint32_t)(k - k0)));
+        return r;
+    }
+    __device__ __forceinline__ uint2 l8(int64_t k) const {
+        uint2 r;
+        asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(r.x), "=r"(r.y) : "r"(sl + (uint32_t)(k - k0)));
+        return r;
+    }
+};
+
 // The batched walk driven by the per-leaf level flags. A lane group takes
 // its chunk in batches of B leaves: the batch's values, leaf indices and
 // level flags arrive in vector loads; then every factor row the batch needs
@@ -179,8 +218,9 @@ __device__ __forceinline__ void fold(float (&parent)[Raw<T>::VEC], float (&child
 // the batch, whose ids are consecutive) is requested before any is used.
 // Rows of fibers at higher levels are requested when the fiber opens and
 // used when it closes.
-template <int NM, typename T, int B>
-__device__ __forceinline__ void flag_chunk(const Args &a, int64_t c, int col, Carry<Raw<T>::VEC> &cy) {
+template <int NM, typename T, int B, typename Recs = GlobalRecs>
+__device__ __forceinline__ void flag_chunk(const Args &a, int64_t c, int col, Carry<Raw<T>::VEC> &cy,
+                                           const Recs &rec) {
     using Rw = Raw<T>;
     constexpr int VEC = Rw::VEC;
     constexpr int NL = NM - 1;  // accumulator levels 0..NM-2
@@ -208,20 +248,20 @@ __device__ __forceinline__ void flag_chunk(const Args &a, int64_t c, int col, Ca
         int32_t li[B];
         uint32_t lw[2] = {0u, 0u};
         {
-            const float4 va = __ldg(reinterpret_cast<const float4 *>(a.vals + kb));
-            const int4 ia = __ldg(reinterpret_cast<const int4 *>(a.fids[NM - 1] + kb));
+            const float4 va = rec.v4(kb);
+            const int4 ia = rec.i4(kb);
             v[0] = va.x; v[1] = va.y; v[2] = va.z; v[3] = va.w;
             li[0] = ia.x; li[1] = ia.y; li[2] = ia.z; li[3] = ia.w;
             if (B == 8) {
-                const float4 vb = __ldg(reinterpret_cast<const float4 *>(a.vals + kb + 4));
-                const int4 ib = __ldg(reinterpret_cast<const int4 *>(a.fids[NM - 1] + kb + 4));
+                const float4 vb = rec.v4(kb + 4);
+                const int4 ib = rec.i4(kb + 4);
                 v[4 % B] = vb.x; v[5 % B] = vb.y; v[6 % B] = vb.z; v[7 % B] = vb.w;
                 li[4 % B] = ib.x; li[5 % B] = ib.y; li[6 % B] = ib.z; li[7 % B] = ib.w;
-                const uint2 l2 = __ldg(reinterpret_cast<const uint2 *>(a.lvl + kb));
+                const uint2 l2 = rec.l8(kb);
                 lw[0] = l2.x;
                 lw[1] = l2.y;
             } else {
-                lw[0] = __ldg(reinterpret_cast<const uint32_t *>(a.lvl + kb));
+                lw[0] = rec.l4(kb);
             }
         }
         const int nvalid = (k1 - kb < B) ? (int)(k1 - kb) : B;

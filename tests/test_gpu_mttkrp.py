@@ -65,7 +65,7 @@ def test_mttkrp_padded_rank(R, ld, cuda_device):
 
 @pytest.mark.parametrize("chunk", [16, 32, 128, 512, 4096])
 @pytest.mark.parametrize("block", [64, 256])
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6])
 def test_mttkrp_schedules_agree(chunk, block, variant, cuda_device):
     dims = (400, 300, 200, 20)
     t = make(dims, 50003, seed=5, dist="zipf", s=1.3)
@@ -75,7 +75,7 @@ def test_mttkrp_schedules_agree(chunk, block, variant, cuda_device):
         _check(M, t, F, root, 16, 1e-5)
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6])
 @pytest.mark.parametrize("nm", [2, 3, 4, 5])
 def test_mttkrp_variants_every_order(variant, nm, cuda_device):
     dims = (290, 170, 50, 30, 10)[:nm]
@@ -136,7 +136,8 @@ def test_mttkrp_rejects_bad_arguments(cuda_device):
     c = sptt.Csf(dims, di, dv, 0)
     F = [torch.rand(d, 8, device=cuda_device) for d in dims]
     out = torch.empty(10, 8, device=cuda_device)
-    for bad in (dict(sched=(24, 256, 0)), dict(sched=(64, 512, 0)), dict(factor_dtype=7)):
+    for bad in (dict(sched=(24, 256, 0)), dict(sched=(64, 512, 0)), dict(sched=(64, 256, 7)),
+                dict(factor_dtype=7)):
         with pytest.raises(sptt.SpttError):
             c.mttkrp(F, out=out, **bad)
     with pytest.raises(sptt.SpttError):  # ld 6 is not a multiple of 4
@@ -145,3 +146,16 @@ def test_mttkrp_rejects_bad_arguments(cuda_device):
     with pytest.raises(sptt.SpttError):  # BF16 needs ld % 8 == 0
         c.mttkrp([torch.rand(d, 4, device=cuda_device).bfloat16() for d in dims],
                  out=torch.empty(10, 4, device=cuda_device), factor_dtype=sptt.SPTT_BF16)
+
+
+def test_staged_variant_reports_no_timeout_and_matches_default(cuda_device):
+    dims = (3000, 900, 200)
+    t = make(dims, 300000, seed=6, dist="zipf", s=1.3)
+    di, dv = to_dev(t, cuda_device)
+    c = sptt.Csf(dims, di, dv, 0)
+    F = [torch.rand(d, 16, device=cuda_device) for d in dims]
+    ref = c.mttkrp(F).clone()
+    for _ in range(3):
+        got = c.mttkrp(F, sched=(64, 256, 6, 0))
+        assert sptt.lib().sptt_csf_check(c.handle, torch.cuda.current_stream().cuda_stream) == 0
+        assert torch.allclose(got, ref, rtol=1e-5, atol=1e-5)
