@@ -49,6 +49,13 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-extras", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--extra-batched", action="store_true",
+                   help="also time the 512-tensor batched workload (one persistent launch per run)")
+    p.add_argument("--extra-sched", action="store_true",
+                   help="also train the learned scheduler and report its held-out regret")
+    p.add_argument("--batch-count", type=int, default=512)
+    p.add_argument("--sched-train", type=int, default=120)
+    p.add_argument("--sched-heldout", type=int, default=40)
     p.add_argument("--variant", type=int, default=0, help="MTTKRP kernel variant for every mode (0 = default)")
     p.add_argument("--chunk", type=int, default=0, help="MTTKRP chunk size (0 = default)")
     return p.parse_args()
@@ -221,6 +228,108 @@ def flop_model(csf, R):
     return 2 * R * (nnz + sum(csf.nfibs[1:-1]))
 
 
+def batched_extra(args, dev):
+    """The batched workload: 512 tensors (3/4 modes, log-uniform sizes), R = 16,
+    15 iterations, one persistent launch per run, replayed from a CUDA graph;
+    against the same tensors decomposed one after another."""
+    import torch
+
+    import paper_1812_05961_gb300 as sptt
+    import tensorgen
+    R, iters = 16, 15
+    specs = tensorgen.batch_tensor_specs(args.batch_count, seed=4)
+    t0 = time.time()
+    tensors = []
+    for i, (dims, nnz) in enumerate(specs):
+        x = tensorgen.batch_member(dims, nnz, seed=1000 + i, device=dev)
+        tensors.append((x.dims, x.inds, x.vals))
+    gen_s = time.time() - t0
+    work = sum(len(d) * int(v.numel()) * R for d, _, v in tensors) * iters
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        t0 = time.time()
+        b = sptt.Batch(tensors, R, seed=1, use_graph=1)
+        create_s = time.time() - t0
+        b.init()
+        b.run(iters)  # direct launch
+        b.run(iters)  # captured
+        grid, chunks, tiles = b.info()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 3
+        ev0.record(side)
+        for _ in range(reps):
+            b.run(iters)
+        ev1.record(side)
+        torch.cuda.synchronize()
+        batched_s = ev0.elapsed_time(ev1) / 1e3 / reps
+    # one tensor at a time through the single-tensor path (creation not timed)
+    cpds = [sptt.Cpd(d, i, v, R, seed=1 + k).init() for k, (d, i, v) in enumerate(tensors)]
+    for c in cpds:
+        c.iterate(1)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for c in cpds:
+        c.iterate(iters)
+    ev1.record()
+    torch.cuda.synchronize()
+    seq_s = ev0.elapsed_time(ev1) / 1e3
+    del cpds
+    return {"tensors": len(tensors), "total_nnz": int(sum(int(v.numel()) for _, _, v in tensors)),
+            "rank": R, "iters": iters, "grid": grid, "chunks_per_mode": chunks[:4], "gen_s": round(gen_s, 1),
+            "create_s": round(create_s, 1), "batched_s_per_run": batched_s,
+            "batched_GnnzR_per_s": work / batched_s / 1e9, "sequential_s": seq_s,
+            "sequential_GnnzR_per_s": work / seq_s / 1e9, "speedup": seq_s / batched_s}
+
+
+def sched_extra(args, dev):
+    """The learned scheduler: trained on autotuner sweeps of generated tensors,
+    evaluated on held-out ones and on a 5-mode probe tensor."""
+    import math as _m
+
+    import numpy as np
+    import torch
+
+    import paper_1812_05961_gb300 as sptt
+    from paper_1812_05961_gb300 import schedtrain
+    import tensorgen
+
+    def specs(n, seed):
+        g = np.random.default_rng(seed)
+        out = []
+        for i in range(n):
+            nm = int(g.integers(3, 6))
+            dims = [int(_m.exp(g.uniform(_m.log(100), _m.log(1e7)))) for _ in range(nm)]
+            space = float(np.prod(dims, dtype=np.float64))
+            nnz = int(min(_m.exp(g.uniform(_m.log(1e5), _m.log(2e7))), space / 4))
+            out.append((dims, max(nnz, 1000), float(g.uniform(0.8, 1.5)), int(g.choice([8, 16, 32, 64])),
+                        seed * 10000 + i))
+        return out
+
+    def dataset(sp):
+        ds = schedtrain.Dataset()
+        for dims, nnz, s_, R, sd in sp:
+            t = tensorgen.sample_unique(dims, nnz, sd, dev, "zipf", s=s_, values="uniform")
+            ds.samples += schedtrain.sweep_tensor(t.dims, t.inds, t.vals, R, reps=3)
+            del t
+            torch.cuda.empty_cache()
+        return ds
+
+    t0 = time.time()
+    train = dataset(specs(args.sched_train, 21))
+    held = dataset(specs(args.sched_heldout, 77))
+    probe = dataset([([1_000_000, 1_000_000, 100_000, 10_000, 500], 20_000_000, 1.1, 32, 5)])
+    sweep_s = time.time() - t0
+    model, hist = schedtrain.train(train, steps=3000, lr=3e-3)
+    res = {"train_samples": len(train.samples), "heldout_samples": len(held.samples), "sweep_s": round(sweep_s, 1),
+           "loss_first_last": [float(hist[0]), float(hist[-1])]}
+    d = schedtrain.default_index()
+    for name, ds in (("heldout", held), ("probe_5mode_2e7", probe)):
+        res[name] = {"learned": schedtrain.summarize(schedtrain.regret(ds, model)),
+                     "default": schedtrain.summarize(schedtrain.regret(ds, fixed=d))}
+    return res
+
+
 def ours(args, rank, world, local):
     import torch
 
@@ -355,6 +464,14 @@ def ours(args, rank, world, local):
             b16["delta_fit_vs_fp32"] = b16["fit_after_20"] - f32["fit_after_20"]
             b16["speedup_vs_fp32"] = f32["s_per_iter"] / b16["s_per_iter"]
         extras["precision_and_rank"] = res
+
+    if args.extra_batched:
+        del cpd
+        torch.cuda.empty_cache()
+        extras["batched"] = batched_extra(args, dev)
+    if args.extra_sched:
+        torch.cuda.empty_cache()
+        extras["scheduler"] = sched_extra(args, dev)
 
     cpu_base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

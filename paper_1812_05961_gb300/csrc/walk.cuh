@@ -269,15 +269,19 @@ __device__ __forceinline__ void flag_chunk(const Args &a, int64_t c, int col, Ca
 #pragma unroll
         for (int j = 0; j < B; ++j)
             if (j < nvalid) x[j] = Rw::load(a.fac[NM - 1], li[j], ld, col);
-        // leaves that open a new level-LF fiber (never the chunk's first leaf)
+        // leaves that open a new level-LF fiber (never the chunk's first
+        // leaf): a per-byte compare of the packed flags, whose 0/1 bytes a
+        // multiply gathers into bits 24..27 (bit 24 + j = byte j)
         uint32_t sm = 0;
 #pragma unroll
-        for (int j = 0; j < B; ++j) {
-            const uint32_t d = (lw[j >> 2] >> (8 * (j & 3))) & 0xffu;
-            if (j < nvalid && d <= (uint32_t)LF && (kb + j) != k0) sm |= 1u << j;
+        for (int w = 0; w < B / 4; ++w) {
+            const uint32_t le = __vcmpleu4(lw[w], (uint32_t)LF * 0x01010101u) & 0x01010101u;
+            sm |= (((le * 0x01020408u) >> 24) & 0xfu) << (4 * w);
         }
+        sm &= (nvalid >= 32) ? 0xffffffffu : ((1u << nvalid) - 1u);
+        if (kb == k0) sm &= ~1u;
         uint4 nr[B];
-        if (LF >= 1) {
+        if constexpr (LF >= 1) {
 #pragma unroll
             for (int j = 0; j < B; ++j)
                 if ((sm >> j) & 1u) {
@@ -288,13 +292,26 @@ __device__ __forceinline__ void flag_chunk(const Args &a, int64_t c, int col, Ca
 #pragma unroll
         for (int j = 0; j < B; ++j) {
             if (j >= nvalid) break;
-            if ((sm >> j) & 1u) {
-                const int d = (int)((lw[j >> 2] >> (8 * (j & 3))) & 0xffu);
-                if (LF >= 1) {
-                    fold<T>(acc[LF - 1], acc[LF], rowc[LF]);
-                    ++f[LF];
-                    rowc[LF] = nr[j];
+            const bool opens = (sm >> j) & 1u;
+            if constexpr (LF >= 1) {
+                // the leaf-parent fiber closes: branch-free, as some lane
+                // group of the warp almost always takes this step
+                float r[VEC];
+                Rw::widen(rowc[LF], r);
+#pragma unroll
+                for (int i = 0; i < VEC; ++i) {
+                    const float folded = fmaf(r[i], acc[LF][i], acc[LF - 1][i]);
+                    acc[LF - 1][i] = opens ? folded : acc[LF - 1][i];
+                    acc[LF][i] = opens ? 0.f : acc[LF][i];
                 }
+                f[LF] += opens ? 1 : 0;
+                rowc[LF].x = opens ? nr[j].x : rowc[LF].x;
+                rowc[LF].y = opens ? nr[j].y : rowc[LF].y;
+                rowc[LF].z = opens ? nr[j].z : rowc[LF].z;
+                rowc[LF].w = opens ? nr[j].w : rowc[LF].w;
+            }
+            if (opens) {
+                const int d = (int)((lw[j >> 2] >> (8 * (j & 3))) & 0xffu);
 #pragma unroll
                 for (int l = LF - 1; l >= 1; --l) {
                     if (d <= l) {
