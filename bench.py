@@ -262,6 +262,7 @@ def batched_extra(args, dev):
         ev1.record(side)
         torch.cuda.synchronize()
         batched_s = ev0.elapsed_time(ev1) / 1e3 / reps
+        phase_ms = sptt.sptt_batch_phase_ms(b.handle)
     # one tensor at a time through the single-tensor path (creation not timed)
     cpds = [sptt.Cpd(d, i, v, R, seed=1 + k).init() for k, (d, i, v) in enumerate(tensors)]
     for c in cpds:
@@ -278,6 +279,7 @@ def batched_extra(args, dev):
     return {"tensors": len(tensors), "total_nnz": int(sum(int(v.numel()) for _, _, v in tensors)),
             "rank": R, "iters": iters, "grid": grid, "chunks_per_mode": chunks[:4], "gen_s": round(gen_s, 1),
             "create_s": round(create_s, 1), "batched_s_per_run": batched_s,
+            "phase_ms_all_runs": phase_ms,
             "batched_GnnzR_per_s": work / batched_s / 1e9, "sequential_s": seq_s,
             "sequential_GnnzR_per_s": work / seq_s / 1e9, "speedup": seq_s / batched_s}
 

@@ -436,6 +436,11 @@ sptt_status sptt_batch_lambda(sptt_batch *batch, int32_t t, double *lambda);
  * output may be NULL). */
 sptt_status sptt_batch_info(sptt_batch *batch, int32_t *grid, int64_t *chunks, int64_t *tiles);
 
+/* Wall time (ms, summed over all runs since create) that CTA 0 of the
+ * batched kernel spent in each phase: MTTKRP, normal equations, row solve,
+ * finalise/fit, normalise (5 doubles, host). Synchronises. */
+sptt_status sptt_batch_phase_ms(sptt_batch *batch, double *ms);
+
 /*
  * Test hook for the bounded barrier: on the next runs, CTA `skip_block` leaves
  * the kernel before its first barrier (so the others' waits run out), and

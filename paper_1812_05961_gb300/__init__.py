@@ -132,6 +132,7 @@ def lib() -> ctypes.CDLL:
             "sptt_batch_lambda": (_ST, [_P, _I32, _P]),
             "sptt_batch_info": (_ST, [_P, _P, _P, _P]),
             "sptt_debug_batch_stall": (_ST, [_P, _I32, _I64]),
+            "sptt_batch_phase_ms": (_ST, [_P, _P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -447,6 +448,12 @@ def sptt_batch_info(b: int):
     tiles = (ctypes.c_int64 * SPTT_MAX_MODES)()
     _check(lib().sptt_batch_info(b, ctypes.byref(grid), chunks, tiles), "sptt_batch_info")
     return grid.value, list(chunks), list(tiles)
+
+
+def sptt_batch_phase_ms(b: int):
+    ms = (ctypes.c_double * 5)()
+    _check(lib().sptt_batch_phase_ms(b, ms), "sptt_batch_phase_ms")
+    return dict(zip(("mttkrp", "normal_eq", "row_solve", "finalize_fit", "normalize"), list(ms)))
 
 
 def sptt_debug_batch_stall(b: int, skip_block: int, timeout_ns: int):

@@ -67,6 +67,7 @@ struct BatchArgs {
     int64_t *it_base;    // iterations run before this launch (indexes the fit ring)
     uint64_t timeout_ns;
     int32_t skip_block;  // test hook: this CTA leaves before the first barrier (-1: none)
+    unsigned long long *phase_ns;  // [5] wall time CTA 0 spends in each phase (M, P, S, F, N)
     int32_t zero_first;  // clear A_n before its first update (rows without a slice end at 0)
 };
 
@@ -284,6 +285,14 @@ __global__ void __launch_bounds__(kBThreads, 2) batched_cpals_kernel(const Batch
     const int64_t nwarps = (int64_t)(gridDim.x * blockDim.x) >> 5;
     const int rank = a.rank;
 
+    uint64_t tp = globaltimer();
+    auto phase_done = [&](int ph) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            const uint64_t now = globaltimer();
+            a.phase_ns[ph] += now - tp;
+            tp = now;
+        }
+    };
     for (int it = 0; it < a.iters; ++it) {
         for (int n = 0; n < a.max_modes; ++n) {
             // M: MTTKRP of mode n over the global chunk list
@@ -304,6 +313,7 @@ __global__ void __launch_bounds__(kBThreads, 2) batched_cpals_kernel(const Batch
                 }
             }
             if (!grid_barrier(a)) return;
+            phase_done(0);
             // P: normal equations per tensor
             for (int tt = blockIdx.x; tt < a.count; tt += gridDim.x) {
                 const BTensor &T = a.T[tt];
@@ -319,9 +329,11 @@ __global__ void __launch_bounds__(kBThreads, 2) batched_cpals_kernel(const Batch
                 __syncthreads();
             }
             if (!grid_barrier(a)) return;
+            phase_done(1);
             // S: row solve + Gram + dots
             solve_phase<RP>(a, n, solve_sm);
             if (!grid_barrier(a)) return;
+            phase_done(2);
             // F: lambda, G_n, fit
             for (int tt = blockIdx.x; tt < a.count; tt += gridDim.x) {
                 const BTensor &T = a.T[tt];
@@ -349,9 +361,11 @@ __global__ void __launch_bounds__(kBThreads, 2) batched_cpals_kernel(const Batch
                 __syncthreads();
             }
             if (!grid_barrier(a)) return;
+            phase_done(3);
             // N: normalise the updated factor
             normalize_phase(a, n);
             if (!grid_barrier(a)) return;
+            phase_done(4);
         }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) *a.it_base = it0 + a.iters;
@@ -386,6 +400,7 @@ struct sptt_batch {
     int64_t total_tiles[kMaxModes] = {0};
     unsigned *d_bar = nullptr;
     int32_t *d_err = nullptr;
+    unsigned long long *d_phase = nullptr;
     int64_t *d_it_base = nullptr;
     double *partials = nullptr;         // Gram workspace for init
     int32_t gram_blocks = 0;
@@ -438,6 +453,7 @@ sptt_status launch_batch(sptt_batch *b, int32_t iters) {
     a.it_base = b->d_it_base;
     a.timeout_ns = b->timeout_ns;
     a.skip_block = b->skip_block;
+    a.phase_ns = b->d_phase;
     a.zero_first = b->zero_first ? 1 : 0;
     SPTT_TRY(fill_zero_launch(b->d_bar, 2 * sizeof(unsigned), b->st));
     SPTT_TRY(fill_zero_launch(b->d_err, sizeof(int32_t), b->st));
@@ -578,6 +594,7 @@ extern "C" sptt_status sptt_batch_create(const sptt_coo *coos, int32_t count, in
     SPTT_TRY(batch_alloc(b, &b->d_bar, 2, true));
     SPTT_TRY(batch_alloc(b, &b->d_err, 1, true));
     SPTT_TRY(batch_alloc(b, &b->d_it_base, 1, true));
+    SPTT_TRY(batch_alloc(b, &b->d_phase, 5, true));
     b->gram_blocks = device_sm_count() * 2;
     SPTT_TRY(batch_alloc(b, &b->partials, (size_t)b->gram_blocks * (rank * rank + rank), false));
     // a grid that is fully resident (cooperative launch)
@@ -713,6 +730,16 @@ extern "C" sptt_status sptt_batch_info(sptt_batch *b, int32_t *grid, int64_t *ch
         if (chunks) chunks[n] = n < b->max_modes ? b->total_chunks[n] : 0;
         if (tiles) tiles[n] = n < b->max_modes ? b->total_tiles[n] : 0;
     }
+    return SPTT_OK;
+}
+
+extern "C" sptt_status sptt_batch_phase_ms(sptt_batch *b, double *ms) {
+    clear_error();
+    if (!b || !ms) return set_error(SPTT_ERR_BAD_ARG, "batch and ms must be non-NULL");
+    unsigned long long ns[5];
+    SPTT_CUDA(cudaMemcpyAsync(ns, b->d_phase, sizeof(ns), cudaMemcpyDeviceToHost, b->st));
+    SPTT_CUDA(cudaStreamSynchronize(b->st));
+    for (int i = 0; i < 5; ++i) ms[i] = ns[i] * 1e-6;
     return SPTT_OK;
 }
 

@@ -75,14 +75,24 @@ __global__ void __launch_bounds__(kThreads) gram_kernel(const float *__restrict_
         }
 }
 
-// out[e] = sum_b partials[b][e] in block order (deterministic).
+// out[e] = sum_b partials[b][e]: 8 lanes per element each sum every 8th
+// block, then the 8 lane sums are added in lane order (deterministic).
+constexpr int kRedLanes = 8;
 __global__ void reduce_partials_kernel(const double *__restrict__ partials, int nblocks, int pstride, int nelem,
                                        double *__restrict__ out) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= nelem) return;
-    double s = 0.0;
-    for (int b = 0; b < nblocks; ++b) s += partials[(int64_t)b * pstride + e];
-    out[e] = s;
+    __shared__ double s[kRedLanes][33];
+    const int e = blockIdx.x * 32 + threadIdx.x;
+    double v = 0.0;
+    if (e < nelem)
+        for (int b = threadIdx.y; b < nblocks; b += kRedLanes) v += partials[(int64_t)b * pstride + e];
+    s[threadIdx.y][threadIdx.x] = v;
+    __syncthreads();
+    if (threadIdx.y == 0 && e < nelem) {
+        double t = 0.0;
+#pragma unroll
+        for (int y = 0; y < kRedLanes; ++y) t += s[y][threadIdx.x];
+        out[e] = t;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -380,7 +390,7 @@ sptt_status to_bf16_launch(const float *A, __nv_bfloat16 *B, int64_t n, cudaStre
 sptt_status dense_work_alloc(DenseWork *w, int32_t rank, int32_t ld, int64_t /*max_rows*/, cudaStream_t st) {
     w->rank = rank;
     w->ld = ld;
-    w->nblocks = device_sm_count() * 2;
+    w->nblocks = device_sm_count() * 4;
     const int64_t pstride = (int64_t)rank * rank + rank;
     SPTT_TRY(dev_alloc_n(&w->partials, (size_t)w->nblocks * pstride, st));
     SPTT_TRY(dev_alloc_n(&w->gram_un, (size_t)pstride, st));
@@ -422,7 +432,7 @@ sptt_status gram_launch(const float *A, int64_t rows, int32_t rank, int32_t ld, 
     }
     SPTT_CHECK_LAUNCH("gram_kernel");
     const int ne = rank * rank;
-    reduce_partials_kernel<<<(ne + kThreads - 1) / kThreads, kThreads, 0, st>>>(partials, nblocks, pstride, ne, G);
+    reduce_partials_kernel<<<(ne + 31) / 32, dim3(32, kRedLanes), 0, st>>>(partials, nblocks, pstride, ne, G);
     SPTT_CHECK_LAUNCH("reduce_partials_kernel");
     return SPTT_OK;
 }
@@ -453,8 +463,8 @@ sptt_status postsolve_launch(const float *M, const double *heavy, const int32_t 
         default: postsolve_dispatch<64>(M, heavy, hidx, fids0, A, rows, w, pstride, st); break;
     }
     SPTT_CHECK_LAUNCH("postsolve_kernel");
-    reduce_partials_kernel<<<(pstride + kThreads - 1) / kThreads, kThreads, 0, st>>>(w->partials, w->nblocks,
-                                                                                     pstride, pstride, w->gram_un);
+    reduce_partials_kernel<<<(pstride + 31) / 32, dim3(32, kRedLanes), 0, st>>>(w->partials, w->nblocks, pstride,
+                                                                               pstride, w->gram_un);
     SPTT_CHECK_LAUNCH("reduce_partials_kernel");
     return SPTT_OK;
 }

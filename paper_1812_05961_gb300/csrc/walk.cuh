@@ -292,26 +292,13 @@ __device__ __forceinline__ void flag_chunk(const Args &a, int64_t c, int col, Ca
 #pragma unroll
         for (int j = 0; j < B; ++j) {
             if (j >= nvalid) break;
-            const bool opens = (sm >> j) & 1u;
-            if constexpr (LF >= 1) {
-                // the leaf-parent fiber closes: branch-free, as some lane
-                // group of the warp almost always takes this step
-                float r[VEC];
-                Rw::widen(rowc[LF], r);
-#pragma unroll
-                for (int i = 0; i < VEC; ++i) {
-                    const float folded = fmaf(r[i], acc[LF][i], acc[LF - 1][i]);
-                    acc[LF - 1][i] = opens ? folded : acc[LF - 1][i];
-                    acc[LF][i] = opens ? 0.f : acc[LF][i];
-                }
-                f[LF] += opens ? 1 : 0;
-                rowc[LF].x = opens ? nr[j].x : rowc[LF].x;
-                rowc[LF].y = opens ? nr[j].y : rowc[LF].y;
-                rowc[LF].z = opens ? nr[j].z : rowc[LF].z;
-                rowc[LF].w = opens ? nr[j].w : rowc[LF].w;
-            }
-            if (opens) {
+            if ((sm >> j) & 1u) {
                 const int d = (int)((lw[j >> 2] >> (8 * (j & 3))) & 0xffu);
+                if constexpr (LF >= 1) {
+                    fold<T>(acc[LF - 1], acc[LF], rowc[LF]);
+                    ++f[LF];
+                    rowc[LF] = nr[j];
+                }
 #pragma unroll
                 for (int l = LF - 1; l >= 1; --l) {
                     if (d <= l) {
