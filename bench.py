@@ -53,6 +53,8 @@ def parse():
                    help="also time the 512-tensor batched workload (one persistent launch per run)")
     p.add_argument("--extra-sched", action="store_true",
                    help="also train the learned scheduler and report its held-out regret")
+    p.add_argument("--extra-mixed4", action="store_true",
+                   help="also time the 4-mode R=64 workload: BF16 gathers + FP32 refinement vs FP32")
     p.add_argument("--batch-count", type=int, default=512)
     p.add_argument("--sched-train", type=int, default=120)
     p.add_argument("--sched-heldout", type=int, default=40)
@@ -153,10 +155,15 @@ def cpu_oracle_rate(t_cpu_inds, t_cpu_vals, dims, R, seconds):
         oracle.cpd_als(inds, vals, dims, R, 1, seed=1, coalesce_first=False)
         return time.perf_counter() - t0
 
-    s0 = min(nnz, 500_000)
-    t0 = run(s0)
-    s = int(min(nnz, max(s0, s0 * seconds / max(t0, 1e-3))))
-    t = run(s) if s != s0 else t0
+    # the iteration has a fixed part (Grams over all rows, the dense solve),
+    # so the sample is rescaled until its time reaches the target
+    s, t = min(nnz, 500_000), None
+    t = run(s)
+    for _ in range(3):
+        if t >= 0.6 * seconds or s >= nnz:
+            break
+        s = int(min(nnz, s * seconds / max(t, 1e-3)))
+        t = run(s)
     rate = len(dims) * s * R / t / 1e9
     return rate, t, s
 
@@ -282,6 +289,53 @@ def batched_extra(args, dev):
             "phase_ms_all_runs": phase_ms,
             "batched_GnnzR_per_s": work / batched_s / 1e9, "sequential_s": seq_s,
             "sequential_GnnzR_per_s": work / seq_s / 1e9, "speedup": seq_s / batched_s}
+
+
+def mixed4_extra(args, dev):
+    """The 4-mode mixed-precision workload: BF16 gathers for 25 iterations plus
+    one FP32 refinement sweep against 26 FP32 iterations from the same start,
+    R = 64: s/iter of each and the fit difference."""
+    import torch
+
+    import paper_1812_05961_gb300 as sptt
+    import tensorgen
+
+    t0 = time.time()
+    t = tensorgen.powerlaw4(seed=3, device=dev)
+    torch.cuda.synchronize()
+    gen_s = time.time() - t0
+    torch.cuda.empty_cache()
+    R = 64
+    stream = torch.cuda.current_stream()
+    out = {"workload": "power-law 4-mode %s, %d nnz, Zipf(1.2), values U(0,1), R=64" %
+                       ("x".join(map(str, t.dims)), t.nnz), "gen_s": round(gen_s, 1)}
+    for name, prec in (("fp32", sptt.SPTT_F32), ("bf16", sptt.SPTT_BF16)):
+        t1 = time.time()
+        c = sptt.Cpd(t.dims, t.inds, t.vals, R, seed=3, precision=prec).init()
+        torch.cuda.synchronize()
+        create_s = time.time() - t1
+        a, b, e = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        a.record(stream)
+        c.iterate(25)
+        b.record(stream)
+        if prec == sptt.SPTT_BF16:
+            c.refine(1)
+        else:
+            c.iterate(1)
+        e.record(stream)
+        torch.cuda.synchronize()
+        s_iter = a.elapsed_time(b) / 25 / 1e3
+        out[name] = {"s_per_iter": s_iter, "last_sweep_s": b.elapsed_time(e) / 1e3,
+                     "total_s": a.elapsed_time(e) / 1e3, "fit": c.fit()[0], "create_s": round(create_s, 2),
+                     "GnnzR_per_s": 4 * t.nnz * R / s_iter / 1e9}
+        del c
+        torch.cuda.empty_cache()
+    out["delta_fit_bf16_vs_fp32"] = out["bf16"]["fit"] - out["fp32"]["fit"]
+    out["speedup_per_iter_bf16_vs_fp32"] = out["fp32"]["s_per_iter"] / out["bf16"]["s_per_iter"]
+    out["speedup_total_bf16_plus_refine_vs_fp32"] = out["fp32"]["total_s"] / out["bf16"]["total_s"]
+    del t
+    torch.cuda.empty_cache()
+    return out
 
 
 def sched_extra(args, dev):
@@ -474,6 +528,9 @@ def ours(args, rank, world, local):
     if args.extra_sched:
         torch.cuda.empty_cache()
         extras["scheduler"] = sched_extra(args, dev)
+    if args.extra_mixed4:
+        torch.cuda.empty_cache()
+        extras["mixed_precision_4mode"] = mixed4_extra(args, dev)
 
     cpu_base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

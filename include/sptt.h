@@ -142,7 +142,11 @@ sptt_status sptt_csf_copy_level(const sptt_csf *csf, int32_t level, int32_t *fpt
  *               by bulk copies (chunk fixed at 64); 1 = plain walk (fiber ends
  *               from fptr, one leaf at a time); 2..5 = batched walk driven by
  *               the per-leaf level flags with (batch, CTAs per SM) = (8, 2),
- *               (4, 3), (4, 4), (8, 1)
+ *               (4, 3), (4, 4), (8, 1); 7 = flag walk and 8 = staged walk
+ *               with 32-byte row segments (one 256-bit gather per lane, half
+ *               the lanes per row) and batches of 2 leaves; they need
+ *               ld * element size and every non-root factor 32-byte aligned,
+ *               and otherwise run as variant 3 / 6
  */
 typedef struct {
     int32_t chunk;

@@ -235,8 +235,9 @@ extern "C" sptt_status sptt_cpd_create(const sptt_coo *coo, int32_t rank, const 
             return set_error(SPTT_ERR_BAD_ARG, "sched->chunk must be a power of two in [16, 4096]");
         if (s->block && (s->block < 32 || s->block > 256 || s->block % 32))
             return set_error(SPTT_ERR_BAD_ARG, "sched->block must be a multiple of 32 in [32, 256]");
-        if (s->variant < 0 || s->variant > 6 || s->order < 0 || s->order > 1)
-            return set_error(SPTT_ERR_BAD_ARG, "sched->variant must be in [0, 6] and order in [0, 1]");
+        if (s->variant < 0 || s->variant > kMaxVariant || s->order < 0 || s->order > 1)
+            return set_error(SPTT_ERR_BAD_ARG, "sched->variant must be in [0, " + std::to_string(kMaxVariant) +
+                                                   "] and order in [0, 1]");
     }
     if (o.plan < 0 || o.plan > 2) return set_error(SPTT_ERR_BAD_ARG, "opts.plan must be 0, 1 or 2");
     if (o.plan == 2 && !o.mlp) return set_error(SPTT_ERR_BAD_ARG, "opts.plan = 2 needs opts.mlp");

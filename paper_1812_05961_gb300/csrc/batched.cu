@@ -10,7 +10,7 @@
 //      large and small tensors are balanced together (walk.cuh);
 //   P  per tensor (one CTA each): V = Hadamard of the other Grams, W = V^+
 //      (FP64 Cholesky / pseudo-inverse, dense_dev.cuh);
-//   S  row solve A_un = M W over one global list of 32-row tiles, with the
+//   S  row solve A_un = M W over one global list of 4096/R-row tiles, with the
 //      Gram of A_un and the fit's dots accumulated in FP64 (each CTA takes a
 //      contiguous run of tiles and flushes once per tensor it touches);
 //      M is cleared as it is read, ready for the next mode;
@@ -30,7 +30,6 @@ namespace sptt {
 namespace {
 
 constexpr int kBThreads = 256;
-constexpr int kTileRows = 32;
 constexpr int kFitRing = 4096;
 
 struct BTensor {
@@ -123,142 +122,112 @@ __device__ __forceinline__ int find_owner(const int64_t *prefix, int count, int6
     return lo;
 }
 
-template <int RP>
-struct SolveSmem {
-    float W[RP][RP + 1];
-    float Mt[kTileRows][RP + 1];
-    float At[kTileRows][RP + 1];
+// Rows per tile of the S and N phases: 4096 / RP (256 at RP = 16, 128 at
+// RP = 32), so one tile is 16 KB of M whatever the rank.
+__host__ __device__ constexpr int tile_rows(int rp) { return 4096 / rp; }
+
+// The contiguous run [g0, g1) of a global work list that this CTA takes.
+struct Span {
+    int64_t g0, g1;
 };
 
-template <int RP>
-__device__ void solve_phase(const BatchArgs &a, int n, SolveSmem<RP> &sm) {
-    constexpr int E = RP / 16;
-    constexpr int CE = RP / 16;
-    constexpr int RE = kTileRows / 16;
-    const int t = threadIdx.x, tr = t / 16, tc = t % 16;
-    const int rank = a.rank, ld = a.ld;
-    const int64_t total = a.total_tiles[n];
+__device__ __forceinline__ Span cta_span(int64_t total) {
     const int64_t per = (total + gridDim.x - 1) / gridDim.x;
-    const int64_t g0 = (int64_t)blockIdx.x * per;
-    const int64_t g1 = (g0 + per < total) ? g0 + per : total;
-    int cur = -1;
-    double accG[E][E];
-    double accD = 0.0;
-#pragma unroll
-    for (int x = 0; x < E; ++x)
-#pragma unroll
-        for (int y = 0; y < E; ++y) accG[x][y] = 0.0;
-    auto flush = [&](int tt) {
-        double *gun = a.T[tt].gun;
-#pragma unroll
-        for (int x = 0; x < E; ++x)
-#pragma unroll
-            for (int y = 0; y < E; ++y) {
-                const int r = tr * E + x, c = tc * E + y;
-                if (r < rank && c < rank) atomicAdd(gun + r * rank + c, accG[x][y]);
-                accG[x][y] = 0.0;
-            }
-        if (t < rank) atomicAdd(gun + rank * rank + t, accD);
-        accD = 0.0;
-    };
-    for (int64_t gt = g0; gt < g1; ++gt) {
-        const int tt = find_owner(a.tile_prefix[n], a.count, gt);
-        const BTensor &T = a.T[tt];
-        if (tt != cur) {
-            if (cur >= 0) flush(cur);
-            cur = tt;
-            __syncthreads();
-            for (int e = t; e < RP * RP; e += blockDim.x) {
-                const int r = e / RP, c = e % RP;
-                sm.W[r][c] = (r < rank && c < rank) ? T.W[r * rank + c] : 0.f;
-            }
-        }
-        const int64_t i0 = (gt - __ldg(a.tile_prefix[n] + tt)) * kTileRows;
-        const int64_t rows = T.nslices[n];
-        float *M = T.M;
-        const int32_t *hidx = T.hidx[n];
-        for (int e = t; e < kTileRows * RP; e += blockDim.x) {
-            const int r = e / RP, c = e % RP;
-            const int64_t i = i0 + r;
-            float v = 0.f;
-            if (i < rows && c < ld) {  // read the row, then leave M zero for the next mode
-                const int32_t h = __ldg(hidx + i);
-                if (h >= 0) {
-                    if (c < rank) v = (float)T.Mh[(int64_t)h * ld + c];
-                    T.Mh[(int64_t)h * ld + c] = 0.0;
-                } else {
-                    if (c < rank) v = M[i * ld + c];
-                }
-                M[i * ld + c] = 0.f;
-            }
-            sm.Mt[r][c] = v;
-        }
-        __syncthreads();
-        float o[RE][CE];
-#pragma unroll
-        for (int y = 0; y < RE; ++y)
-#pragma unroll
-            for (int x = 0; x < CE; ++x) o[y][x] = 0.f;
-        for (int k = 0; k < RP; ++k) {
-#pragma unroll
-            for (int y = 0; y < RE; ++y) {
-                const float mk = sm.Mt[tr * RE + y][k];
-#pragma unroll
-                for (int x = 0; x < CE; ++x) o[y][x] = fmaf(mk, sm.W[k][tc * CE + x], o[y][x]);
-            }
-        }
-        const int32_t *fids0 = T.fids0[n];
-        float *A = T.A[n];
-#pragma unroll
-        for (int y = 0; y < RE; ++y) {
-            const int r = tr * RE + y;
-            const int64_t i = i0 + r;
-            const int64_t dst = (i < rows) ? (int64_t)__ldg(fids0 + i) * ld : 0;
-#pragma unroll
-            for (int x = 0; x < CE; ++x) {
-                const int c = tc * CE + x;
-                sm.At[r][c] = o[y][x];
-                if (i < rows && c < ld) A[dst + c] = o[y][x];
-            }
-        }
-        __syncthreads();
-        float s[E][E];
-#pragma unroll
-        for (int x = 0; x < E; ++x)
-#pragma unroll
-            for (int y = 0; y < E; ++y) s[x][y] = 0.f;
-        for (int r = 0; r < kTileRows; ++r)
-#pragma unroll
-            for (int x = 0; x < E; ++x)
-#pragma unroll
-                for (int y = 0; y < E; ++y) s[x][y] = fmaf(sm.At[r][tr * E + x], sm.At[r][tc * E + y], s[x][y]);
-#pragma unroll
-        for (int x = 0; x < E; ++x)
-#pragma unroll
-            for (int y = 0; y < E; ++y) accG[x][y] += (double)s[x][y];
-        if (t < RP) {
-            float d = 0.f;
-            for (int r = 0; r < kTileRows; ++r) d = fmaf(sm.Mt[r][t], sm.At[r][t], d);
-            accD += (double)d;
-        }
-        __syncthreads();
-    }
-    if (cur >= 0) flush(cur);
+    Span s;
+    s.g0 = (int64_t)blockIdx.x * per;
+    s.g1 = (s.g0 + per < total) ? s.g0 + per : total;
+    return s;
 }
 
-__device__ void normalize_phase(const BatchArgs &a, int n) {
-    const int ld = a.ld, rank = a.rank, qpr = ld / 4;
-    const int64_t total = a.total_tiles[n];
-    for (int64_t gt = blockIdx.x; gt < total; gt += gridDim.x) {
-        const int tt = find_owner(a.tile_prefix[n], a.count, gt);
+// Owner of item g, advanced from a previous owner at or before g.
+__device__ __forceinline__ int advance_owner(const int64_t *prefix, int tt, int64_t g) {
+    while (g >= __ldg(prefix + tt + 1)) ++tt;
+    return tt;
+}
+
+// M: MTTKRP of mode n over the global chunk list. The lane groups of the
+// whole grid interleave over it, so every tensor's chunks (whose costs differ
+// from tensor to tensor) are spread over all CTAs; a group's chunks are far
+// apart, so its heavy-slice partial is flushed after each chunk.
+template <int NM>
+__device__ __noinline__ void walk_chunk(const walk::Args &w, int64_t c, int col) {
+    const walk::GlobalRecs rec{w.vals, w.fids[NM - 1], w.lvl};
+    walk::Carry<4> cy;
+    walk::flag_chunk<NM, float, 4>(w, c, col, cy, rec);
+    walk::flush_carry(w, col, cy);
+}
+
+__device__ __noinline__ void mttkrp_phase(const BatchArgs &a, int n, int gi, int gpw, int col) {
+    const int64_t gwarp = (int64_t)(blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = (int64_t)(gridDim.x * blockDim.x) >> 5;
+    const int64_t *prefix = a.chunk_prefix[n];
+    for (int64_t gc = gwarp * gpw + gi; gc < a.total_chunks[n]; gc += nwarps * gpw) {
+        const int tt = find_owner(prefix, a.count, gc);
         const BTensor &T = a.T[tt];
-        const int64_t i0 = (gt - __ldg(a.tile_prefix[n] + tt)) * kTileRows;
+        const int64_t c = gc - __ldg(prefix + tt);
+        switch (T.nmodes) {
+            case 2: walk_chunk<2>(T.w[n], c, col); break;
+            case 3: walk_chunk<3>(T.w[n], c, col); break;
+            default: walk_chunk<4>(T.w[n], c, col); break;
+        }
+    }
+}
+
+// S: A_un = M W over the tile list (dense_dev.cuh's tile body, which clears
+// M as it reads it); each CTA takes a contiguous run of tiles and adds its
+// Gram and dot totals to a tensor's accumulators when it moves on.
+template <int RP>
+__device__ __noinline__ void solve_phase(const BatchArgs &a, int n, dense::SolveTile<RP> &sm) {
+    static_assert(dense::SolveTile<RP>::TR == tile_rows(RP), "tile lists and tile body agree");
+    const Span sp = cta_span(a.total_tiles[n]);
+    if (sp.g0 >= sp.g1) return;
+    const int64_t *prefix = a.tile_prefix[n];
+    const int rank = a.rank;
+    int tt = find_owner(prefix, a.count, sp.g0);
+    int cur = -1;
+    dense::SolveRun acc;
+    dense::solve_begin(sm, acc);
+    for (int64_t gt = sp.g0; gt < sp.g1; ++gt) {
+        tt = advance_owner(prefix, tt, gt);
+        const BTensor &T = a.T[tt];
+        if (tt != cur) {
+            if (cur >= 0) {
+                double *gun = a.T[cur].gun;
+                dense::solve_reduce(sm, acc, rank, [&](int e, double v) { atomicAdd(gun + e, v); });
+            }
+            cur = tt;
+            dense::solve_load_w(sm, T.W, rank);  // the last tile (or reduction) ended with a barrier
+        }
+        const int64_t i0 = (gt - __ldg(prefix + tt)) * tile_rows(RP);
+        dense::solve_tile<RP, true>(sm, acc, T.M, T.Mh, T.hidx[n], T.fids0[n], T.A[n], i0, T.nslices[n], rank,
+                                    a.ld);
+    }
+    double *gun = a.T[cur].gun;
+    dense::solve_reduce(sm, acc, rank, [&](int e, double v) { atomicAdd(gun + e, v); });
+}
+
+// N: A_n *= 1 / lambda over the tile list (the slices' rows only; rows of
+// empty slices are zero already).
+template <int RP>
+__device__ __noinline__ void normalize_phase(const BatchArgs &a, int n) {
+    constexpr int TR = tile_rows(RP);
+    const int ld = a.ld, rank = a.rank, qpr = ld / 4;
+    const Span sp = cta_span(a.total_tiles[n]);
+    if (sp.g0 >= sp.g1) return;
+    const int64_t *prefix = a.tile_prefix[n];
+    int tt = find_owner(prefix, a.count, sp.g0);
+    for (int64_t gt = sp.g0; gt < sp.g1; ++gt) {
+        tt = advance_owner(prefix, tt, gt);
+        const BTensor &T = a.T[tt];
+        const int64_t i0 = (gt - __ldg(prefix + tt)) * TR;
         const int64_t rows = T.nslices[n];
-        for (int e = threadIdx.x; e < kTileRows * qpr; e += blockDim.x) {
+        const int32_t *fids0 = T.fids0[n];
+        float *A = T.A[n];
+        for (int e = threadIdx.x; e < TR * qpr; e += kBThreads) {
             const int64_t i = i0 + e / qpr;
-            if (i >= rows) continue;
+            if (i >= rows) break;  // e grows with i
             const int c0 = (e % qpr) * 4;
-            float4 *p = reinterpret_cast<float4 *>(T.A[n] + (int64_t)__ldg(T.fids0[n] + i) * ld + c0);
+            float4 *p = reinterpret_cast<float4 *>(A + (int64_t)__ldg(fids0 + i) * ld + c0);
             float4 v = *p;
             v.x = (c0 + 0 < rank) ? v.x * T.inv_lambda[c0 + 0] : 0.f;
             v.y = (c0 + 1 < rank) ? v.y * T.inv_lambda[c0 + 1] : 0.f;
@@ -273,7 +242,7 @@ template <int RP>
 __global__ void __launch_bounds__(kBThreads, 2) batched_cpals_kernel(const BatchArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     double *prep_sm = reinterpret_cast<double *>(smem);
-    SolveSmem<RP> &solve_sm = *reinterpret_cast<SolveSmem<RP> *>(smem);
+    dense::SolveTile<RP> &solve_sm = *reinterpret_cast<dense::SolveTile<RP> *>(smem);
     if ((int)blockIdx.x == a.skip_block) return;  // test hook: a CTA that never arrives
     const int64_t it0 = *a.it_base;
     const int lane = threadIdx.x & 31;
@@ -281,8 +250,6 @@ __global__ void __launch_bounds__(kBThreads, 2) batched_cpals_kernel(const Batch
     const int gpw = 32 / G;
     const int gi = lane / G;
     const int col = (lane - gi * G) * 4;
-    const int64_t gwarp = (int64_t)(blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = (int64_t)(gridDim.x * blockDim.x) >> 5;
     const int rank = a.rank;
 
     uint64_t tp = globaltimer();
@@ -296,22 +263,7 @@ __global__ void __launch_bounds__(kBThreads, 2) batched_cpals_kernel(const Batch
     for (int it = 0; it < a.iters; ++it) {
         for (int n = 0; n < a.max_modes; ++n) {
             // M: MTTKRP of mode n over the global chunk list
-            if (gi < gpw) {
-                for (int64_t gc = gwarp * gpw + gi; gc < a.total_chunks[n]; gc += nwarps * gpw) {
-                    const int tt = find_owner(a.chunk_prefix[n], a.count, gc);
-                    const BTensor &T = a.T[tt];
-                    const int64_t c = gc - __ldg(a.chunk_prefix[n] + tt);
-                    walk::Carry<4> cy;  // chunks of one group are far apart here: flushed per chunk
-                    const walk::Args &w = T.w[n];
-                    const walk::GlobalRecs rec{w.vals, w.fids[T.nmodes - 1], w.lvl};
-                    switch (T.nmodes) {
-                        case 2: walk::flag_chunk<2, float, 4>(w, c, col, cy, rec); break;
-                        case 3: walk::flag_chunk<3, float, 4>(w, c, col, cy, rec); break;
-                        default: walk::flag_chunk<4, float, 4>(w, c, col, cy, rec); break;
-                    }
-                    walk::flush_carry(T.w[n], col, cy);
-                }
-            }
+            if (gi < gpw) mttkrp_phase(a, n, gi, gpw, col);
             if (!grid_barrier(a)) return;
             phase_done(0);
             // P: normal equations per tensor
@@ -363,7 +315,7 @@ __global__ void __launch_bounds__(kBThreads, 2) batched_cpals_kernel(const Batch
             if (!grid_barrier(a)) return;
             phase_done(3);
             // N: normalise the updated factor
-            normalize_phase(a, n);
+            normalize_phase<RP>(a, n);
             if (!grid_barrier(a)) return;
             phase_done(4);
         }
@@ -374,7 +326,7 @@ __global__ void __launch_bounds__(kBThreads, 2) batched_cpals_kernel(const Batch
 size_t batched_smem_bytes(int rank, int rp) {
     const int half = (rank + 2) / 2;
     const size_t prep = (3 * (size_t)rank * rank + 16 + 2 * half) * sizeof(double) + 2 * half * sizeof(int) + 64;
-    const size_t solve = rp == 16 ? sizeof(SolveSmem<16>) : sizeof(SolveSmem<32>);
+    const size_t solve = rp == 16 ? sizeof(dense::SolveTile<16>) : sizeof(dense::SolveTile<32>);
     return prep > solve ? prep : solve;
 }
 
@@ -581,7 +533,8 @@ extern "C" sptt_status sptt_batch_create(const sptt_coo *coos, int32_t count, in
             const BTensor &T = b->host[t];
             const bool has = T.nmodes > n;
             cp[t + 1] = cp[t] + (has ? T.w[n].nchunks : 0);
-            tp[t + 1] = tp[t] + (has ? (T.nslices[n] + kTileRows - 1) / kTileRows : 0);
+            const int tr = tile_rows(rank <= 16 ? 16 : 32);
+            tp[t + 1] = tp[t] + (has ? (T.nslices[n] + tr - 1) / tr : 0);
         }
         b->total_chunks[n] = cp[count];
         b->total_tiles[n] = tp[count];

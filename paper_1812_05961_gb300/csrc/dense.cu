@@ -18,7 +18,6 @@ using dense::block_sum_d;
 
 constexpr int kThreads = 256;
 constexpr int kGramRows = 64;   // rows per tile of the Gram kernel
-constexpr int kSolveRows = 32;  // rows per tile of the fused post-solve kernel
 
 // ---------------------------------------------------------------------------
 // Gram: partials[block][a*rank+b] = sum over the block's rows of A[i,a] A[i,b]
@@ -110,97 +109,17 @@ __global__ void __launch_bounds__(kThreads) postsolve_kernel(const float *__rest
                                                              int64_t rows, int rank, int ld,
                                                              const float *__restrict__ Wg,
                                                              double *__restrict__ partials, int pstride) {
-    constexpr int E = RP / 16;         // Gram tile per thread side
-    constexpr int CE = RP / 16;        // solve: columns per thread
-    constexpr int RE = kSolveRows / 16;  // solve: rows per thread
-    __shared__ float W[RP][RP + 1];
-    __shared__ float Mt[kSolveRows][RP + 1];
-    __shared__ float At[kSolveRows][RP + 1];
-    const int t = threadIdx.x, tr = t / 16, tc = t % 16;
-    for (int e = t; e < RP * RP; e += kThreads) {
-        const int a = e / RP, b = e % RP;
-        W[a][b] = (a < rank && b < rank) ? Wg[a * rank + b] : 0.f;
-    }
-    double accG[E][E];
-#pragma unroll
-    for (int x = 0; x < E; ++x)
-#pragma unroll
-        for (int y = 0; y < E; ++y) accG[x][y] = 0.0;
-    double accD = 0.0;
-    for (int64_t i0 = (int64_t)blockIdx.x * kSolveRows; i0 < rows; i0 += (int64_t)gridDim.x * kSolveRows) {
-        for (int e = t; e < kSolveRows * RP; e += kThreads) {
-            const int r = e / RP, c = e % RP;
-            const int64_t i = i0 + r;
-            Mt[r][c] = (i < rows && c < rank) ? walk::read_row(M, heavy, hidx, i, ld, c) : 0.f;
-        }
-        __syncthreads();
-        float o[RE][CE];
-#pragma unroll
-        for (int y = 0; y < RE; ++y)
-#pragma unroll
-            for (int x = 0; x < CE; ++x) o[y][x] = 0.f;
-#pragma unroll 4
-        for (int k = 0; k < RP; ++k) {
-            float mk[RE], wk[CE];
-#pragma unroll
-            for (int y = 0; y < RE; ++y) mk[y] = Mt[tr * RE + y][k];
-#pragma unroll
-            for (int x = 0; x < CE; ++x) wk[x] = W[k][tc * CE + x];
-#pragma unroll
-            for (int y = 0; y < RE; ++y)
-#pragma unroll
-                for (int x = 0; x < CE; ++x) o[y][x] = fmaf(mk[y], wk[x], o[y][x]);
-        }
-#pragma unroll
-        for (int y = 0; y < RE; ++y) {
-            const int r = tr * RE + y;
-            const int64_t i = i0 + r;
-            const int64_t dst = (i < rows) ? (int64_t)__ldg(fids0 + i) * ld : 0;
-#pragma unroll
-            for (int x = 0; x < CE; ++x) {
-                const int c = tc * CE + x;
-                At[r][c] = o[y][x];
-                if (i < rows && c < ld) A[dst + c] = o[y][x];
-            }
-        }
-        __syncthreads();
-        float s[E][E];
-#pragma unroll
-        for (int x = 0; x < E; ++x)
-#pragma unroll
-            for (int y = 0; y < E; ++y) s[x][y] = 0.f;
-        for (int r = 0; r < kSolveRows; ++r) {
-            float xa[E], xb[E];
-#pragma unroll
-            for (int x = 0; x < E; ++x) {
-                xa[x] = At[r][tr * E + x];
-                xb[x] = At[r][tc * E + x];
-            }
-#pragma unroll
-            for (int x = 0; x < E; ++x)
-#pragma unroll
-                for (int y = 0; y < E; ++y) s[x][y] = fmaf(xa[x], xb[y], s[x][y]);
-        }
-#pragma unroll
-        for (int x = 0; x < E; ++x)
-#pragma unroll
-            for (int y = 0; y < E; ++y) accG[x][y] += (double)s[x][y];
-        if (t < RP) {
-            float d = 0.f;
-            for (int r = 0; r < kSolveRows; ++r) d = fmaf(Mt[r][t], At[r][t], d);
-            accD += (double)d;
-        }
-        __syncthreads();
-    }
+    using ST = dense::SolveTile<RP>;
+    extern __shared__ __align__(16) unsigned char solve_smem[];
+    ST &sm = *reinterpret_cast<ST *>(solve_smem);
+    dense::solve_load_w(sm, Wg, rank);
+    dense::SolveRun acc;
+    dense::solve_begin(sm, acc);
+    for (int64_t i0 = (int64_t)blockIdx.x * ST::TR; i0 < rows; i0 += (int64_t)gridDim.x * ST::TR)
+        dense::solve_tile<RP, false>(sm, acc, const_cast<float *>(M), const_cast<double *>(heavy), hidx, fids0, A,
+                                     i0, rows, rank, ld);
     double *P = partials + (int64_t)blockIdx.x * pstride;
-#pragma unroll
-    for (int x = 0; x < E; ++x)
-#pragma unroll
-        for (int y = 0; y < E; ++y) {
-            const int a = tr * E + x, b = tc * E + y;
-            if (a < rank && b < rank) P[a * rank + b] = accG[x][y];
-        }
-    if (t < rank) P[rank * rank + t] = accD;
+    dense::solve_reduce(sm, acc, rank, [&](int e, double v) { P[e] = v; });
 }
 
 // ---------------------------------------------------------------------------
@@ -406,6 +325,12 @@ sptt_status dense_work_alloc(DenseWork *w, int32_t rank, int32_t ld, int64_t /*m
     SPTT_TRY(fill_zero_launch(w->inner, sizeof(double), st));
     SPTT_CUDA(cudaFuncSetAttribute(normal_prep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)prep_smem_bytes(SPTT_MAX_RANK_ALS)));
+    SPTT_CUDA(cudaFuncSetAttribute(postsolve_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)sizeof(dense::SolveTile<16>)));
+    SPTT_CUDA(cudaFuncSetAttribute(postsolve_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)sizeof(dense::SolveTile<32>)));
+    SPTT_CUDA(cudaFuncSetAttribute(postsolve_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)sizeof(dense::SolveTile<64>)));
     return SPTT_OK;
 }
 
@@ -449,8 +374,8 @@ sptt_status normal_prep_launch(double *const *grams, int32_t nmodes, int32_t n, 
 template <int RP>
 static void postsolve_dispatch(const float *M, const double *heavy, const int32_t *hidx, const int32_t *fids0,
                                float *A, int64_t rows, DenseWork *w, int pstride, cudaStream_t st) {
-    postsolve_kernel<RP><<<w->nblocks, kThreads, 0, st>>>(M, heavy, hidx, fids0, A, rows, w->rank, w->ld, w->W,
-                                                          w->partials, pstride);
+    postsolve_kernel<RP><<<w->nblocks, kThreads, sizeof(dense::SolveTile<RP>), st>>>(
+        M, heavy, hidx, fids0, A, rows, w->rank, w->ld, w->W, w->partials, pstride);
 }
 
 sptt_status postsolve_launch(const float *M, const double *heavy, const int32_t *hidx, const int32_t *fids0,

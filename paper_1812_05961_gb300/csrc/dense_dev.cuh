@@ -25,6 +25,193 @@ __device__ __forceinline__ double block_sum_d(double v, double *red) {
     return s;
 }
 
+// ---------------------------------------------------------------------------
+// Row solve after each MTTKRP (Algorithm 1 lines 5-6, 8-9, 11-12): for one
+// tile of TR = 4096 / RP rows of the compact MTTKRP result M (heavy slices
+// from their FP64 rows), A_un = M W is written to A at the slices' mode
+// indices, and each thread adds its share of the Gram A_un^T A_un and of the
+// column dots <M, A_un> (for the fit) to FP32 sums; every 64 rows (16 for
+// the dots) those are added to the thread's FP64 totals (kept in shared
+// memory), and a block reduction finally hands the totals to the caller. Shared by the per-step kernel (per-block
+// partials) and the batched kernel (atomics per tensor). 256 threads.
+// ---------------------------------------------------------------------------
+template <int RP>
+struct SolveTile {
+    static constexpr int TR = 4096 / RP;             // rows per tile
+    static constexpr int S = RP + 4;                 // row stride: 16-byte rows, conflict-free float4 access
+    static constexpr int TPR = RP / 16;              // product: threads per row, 16 columns each
+    static constexpr int NB = (RP / 4) * (RP / 4);   // Gram: 4 x 4 blocks of entries
+    static constexpr int RG = 256 / NB;              // Gram: row groups
+    static constexpr int GROWS = TR / RG;            // Gram: rows per thread per tile
+    static constexpr int DG = 256 / RP;              // dots: row groups
+    static constexpr int CONV = GROWS >= 64 ? 1 : 64 / GROWS;  // tiles per FP32 run
+    float W[RP][RP];
+    float Mt[TR][S];
+    float At[TR][S];
+    double G[256][17];  // per thread: FP64 totals of its 4 x 4 Gram block (padded: conflict-free)
+    double D[256];      // per thread: FP64 total of its dot
+};
+
+// Per-thread FP32 run sums (registers).
+struct SolveRun {
+    float gs[16];
+    float ds;
+    int run;
+};
+
+template <int RP>
+__device__ __forceinline__ void solve_begin(SolveTile<RP> &sm, SolveRun &acc) {
+    const int t = threadIdx.x;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        acc.gs[q] = 0.f;
+        sm.G[t][q] = 0.0;
+    }
+    acc.ds = 0.f;
+    sm.D[t] = 0.0;
+    acc.run = 0;
+}
+
+template <int RP>
+__device__ __forceinline__ void solve_end_run(SolveTile<RP> &sm, SolveRun &acc) {
+    const int t = threadIdx.x;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        sm.G[t][q] += (double)acc.gs[q];
+        acc.gs[q] = 0.f;
+    }
+    sm.D[t] += (double)acc.ds;
+    acc.ds = 0.f;
+    acc.run = 0;
+}
+
+// W (rank x rank, FP32, row-major) into the tile's zero-padded RP x RP copy.
+// The caller orders it against the tile's readers (the tile starts and ends
+// with a barrier).
+template <int RP>
+__device__ __forceinline__ void solve_load_w(SolveTile<RP> &sm, const float *__restrict__ Wg, int rank) {
+    for (int e = threadIdx.x; e < RP * RP; e += blockDim.x) {
+        const int r = e / RP, c = e % RP;
+        sm.W[r][c] = (r < rank && c < rank) ? Wg[r * rank + c] : 0.f;
+    }
+}
+
+// One tile starting at compact row i0. CLEAR leaves the rows of M (and the
+// heavy rows) it read at zero, ready for the next MTTKRP.
+template <int RP, bool CLEAR>
+__device__ __forceinline__ void solve_tile(SolveTile<RP> &sm, SolveRun &acc, float *M, double *heavy,
+                                           const int32_t *__restrict__ hidx, const int32_t *__restrict__ fids0,
+                                           float *A, int64_t i0, int64_t rows, int rank, int ld) {
+    using ST = SolveTile<RP>;
+    constexpr int Q = RP / 4;
+    const int t = threadIdx.x;
+    for (int e = t; e < ST::TR * Q; e += 256) {
+        const int r = e / Q, c = (e % Q) * 4;
+        const int64_t i = i0 + r;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (i < rows && c < ld) {
+            const int32_t h = __ldg(hidx + i);
+            float4 *pm = reinterpret_cast<float4 *>(M + i * ld + c);
+            if (h >= 0) {
+                double2 *ph = reinterpret_cast<double2 *>(heavy + (int64_t)h * ld + c);
+                const double2 d0 = ph[0], d1 = ph[1];
+                v = make_float4((float)d0.x, (float)d0.y, (float)d1.x, (float)d1.y);
+                if (CLEAR) {
+                    ph[0] = make_double2(0.0, 0.0);
+                    ph[1] = make_double2(0.0, 0.0);
+                }
+            } else {
+                v = *pm;
+            }
+            if (CLEAR) *pm = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (c + 0 >= rank) v.x = 0.f;
+            if (c + 1 >= rank) v.y = 0.f;
+            if (c + 2 >= rank) v.z = 0.f;
+            if (c + 3 >= rank) v.w = 0.f;
+        }
+        *reinterpret_cast<float4 *>(&sm.Mt[r][c]) = v;
+    }
+    __syncthreads();
+    {
+        const int r = t / ST::TPR, cb = (t % ST::TPR) * 16;
+        float o[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) o[j] = 0.f;
+#pragma unroll 2
+        for (int k = 0; k < RP; k += 4) {
+            const float4 m4 = *reinterpret_cast<const float4 *>(&sm.Mt[r][k]);
+            const float mk[4] = {m4.x, m4.y, m4.z, m4.w};
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float4 w4 = *reinterpret_cast<const float4 *>(&sm.W[k + kk][cb + 4 * q]);
+                    o[4 * q + 0] = fmaf(mk[kk], w4.x, o[4 * q + 0]);
+                    o[4 * q + 1] = fmaf(mk[kk], w4.y, o[4 * q + 1]);
+                    o[4 * q + 2] = fmaf(mk[kk], w4.z, o[4 * q + 2]);
+                    o[4 * q + 3] = fmaf(mk[kk], w4.w, o[4 * q + 3]);
+                }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            *reinterpret_cast<float4 *>(&sm.At[r][cb + 4 * q]) =
+                make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
+        const int64_t i = i0 + r;
+        if (i < rows) {
+            float *dst = A + (int64_t)__ldg(fids0 + i) * ld + cb;
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (cb + 4 * q < ld)
+                    *reinterpret_cast<float4 *>(dst + 4 * q) =
+                        make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
+        }
+    }
+    __syncthreads();
+    {
+        const int blk = t % ST::NB, g = t / ST::NB;
+        const int bx = blk / (RP / 4), by = blk % (RP / 4);
+        const int live = (rows - i0 < ST::TR) ? (int)(rows - i0) : ST::TR;  // rows past the end are zero
+        for (int r = g; r < live; r += ST::RG) {
+            const float4 a4 = *reinterpret_cast<const float4 *>(&sm.At[r][bx * 4]);
+            const float4 b4 = *reinterpret_cast<const float4 *>(&sm.At[r][by * 4]);
+            const float xa[4] = {a4.x, a4.y, a4.z, a4.w}, xb[4] = {b4.x, b4.y, b4.z, b4.w};
+#pragma unroll
+            for (int x = 0; x < 4; ++x)
+#pragma unroll
+                for (int y = 0; y < 4; ++y) acc.gs[x * 4 + y] = fmaf(xa[x], xb[y], acc.gs[x * 4 + y]);
+        }
+        const int c = t % RP;
+        for (int r = t / RP; r < live; r += ST::DG) acc.ds = fmaf(sm.Mt[r][c], sm.At[r][c], acc.ds);
+    }
+    __syncthreads();
+    if (++acc.run == ST::CONV) solve_end_run(sm, acc);
+}
+
+// Block-wide totals of the Gram (entry r * rank + c) and of the dots (entry
+// rank * rank + c), handed to emit(entry, value) in a fixed order; then the
+// totals restart from zero. Every thread of the block calls it.
+template <int RP, typename Emit>
+__device__ __forceinline__ void solve_reduce(SolveTile<RP> &sm, SolveRun &acc, int rank, Emit emit) {
+    using ST = SolveTile<RP>;
+    solve_end_run(sm, acc);
+    const int t = threadIdx.x;
+    __syncthreads();
+    for (int e = t; e < ST::NB * 16; e += 256) {
+        const int b = e / 16, q = e % 16;
+        double v = 0.0;
+        for (int gg = 0; gg < ST::RG; ++gg) v += sm.G[gg * ST::NB + b][q];
+        const int r = (b / (RP / 4)) * 4 + q / 4, c = (b % (RP / 4)) * 4 + q % 4;
+        if (r < rank && c < rank) emit(r * rank + c, v);
+    }
+    if (t < RP) {
+        double v = 0.0;
+        for (int gg = 0; gg < ST::DG; ++gg) v += sm.D[gg * RP + t];
+        if (t < rank) emit(rank * rank + t, v);
+    }
+    __syncthreads();
+    solve_begin(sm, acc);
+}
+
 // V = Hadamard_{m != n} G_m; W = V^dagger (FP64: Cholesky with the
 // positive-definite test, else the pseudo-inverse by parallel cyclic
 // Jacobi). One CTA; sm holds 3 R^2 + 16 + (R + 2) doubles and R + 2 ints.

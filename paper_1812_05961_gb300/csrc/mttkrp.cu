@@ -64,14 +64,15 @@ __device__ __forceinline__ ChunkRange cta_chunks(int64_t nchunks, const Lanes &L
     return r;
 }
 
-template <int NM, typename T, int B, int MINB>
+template <int NM, typename T, int B, int MINB, int W = 16>
 __global__ void __launch_bounds__(256, MINB) mttkrp_flag_kernel(const walk::Args a) {
-    const Lanes L = lanes_for(a.ld, walk::Raw<T>::VEC);
+    const Lanes L = lanes_for(a.ld, walk::Raw<T, W>::VEC);
     if (L.idle) return;  // no warp collectives in the walk
     const ChunkRange r = cta_chunks(a.nchunks, L);
-    walk::Carry<walk::Raw<T>::VEC> cy;
+    walk::Carry<walk::Raw<T, W>::VEC> cy;
     const walk::GlobalRecs rec{a.vals, a.fids[NM - 1], a.lvl};
-    for (int64_t c = r.begin; c < r.end; c += r.step) walk::flag_chunk<NM, T, B>(a, c, L.col, cy, rec);
+    for (int64_t c = r.begin; c < r.end; c += r.step)
+        walk::flag_chunk<NM, T, B, walk::GlobalRecs, W>(a, c, L.col, cy, rec);
     walk::flush_carry(a, L.col, cy);
 }
 
@@ -134,10 +135,10 @@ __device__ __forceinline__ void stage_issue(const walk::Args &a, const int32_t *
                  ::"r"(dst + kStageChunk * 8), "l"(a.lvl + k0), "r"(kStageChunk), "r"(bar) : "memory");
 }
 
-template <int NM, typename T>
+template <int NM, typename T, int W>
 __global__ void __launch_bounds__(256, 2) mttkrp_staged_kernel(const walk::Args a, int32_t *err) {
     extern __shared__ __align__(128) unsigned char smem[];
-    constexpr int VEC = walk::Raw<T>::VEC;
+    constexpr int VEC = walk::Raw<T, W>::VEC;
     const Lanes L = lanes_for(a.ld, VEC);
     if (L.idle) return;  // no CTA-wide barrier below: every group runs on its own
     const int G = a.ld / VEC;
@@ -172,7 +173,7 @@ __global__ void __launch_bounds__(256, 2) mttkrp_staged_kernel(const walk::Args 
         }
         const walk::SharedRecs rec{buf + s * kStageStride, buf + s * kStageStride + kStageChunk * 4,
                                    buf + s * kStageStride + kStageChunk * 8, c * (int64_t)kStageChunk};
-        walk::flag_chunk<NM, T, 4, walk::SharedRecs>(a, c, L.col, cy, rec);
+        walk::flag_chunk<NM, T, (W == 32 ? 2 : 4), walk::SharedRecs, W>(a, c, L.col, cy, rec);
         __syncwarp(gmask);  // the whole group is done with stage s
         const int64_t cn = c + 2 * r.step;
         if (leader && cn < r.end) stage_issue(a, leaf_idx, cn, bar + 8 * s, buf + s * kStageStride);
@@ -193,10 +194,10 @@ __global__ void scatter_rows_kernel(const float *__restrict__ compact, const dou
     }
 }
 
-template <int NM, typename T>
+template <int NM, typename T, int W>
 sptt_status launch_staged(const walk::Args &a, int32_t *err, cudaStream_t st) {
-    auto kern = mttkrp_staged_kernel<NM, T>;
-    const int vec = walk::Raw<T>::VEC;
+    auto kern = mttkrp_staged_kernel<NM, T, W>;
+    const int vec = walk::Raw<T, W>::VEC;
     const int gpw = 32 / (a.ld / vec);
     const int block = gpw >= 16 ? 128 : 256;  // keep the stage buffers of a CTA near 80 KB
     const int groups = (block / 32) * gpw;
@@ -223,12 +224,13 @@ sptt_status launch_nm(const walk::Args &a, int block, int variant, cudaStream_t 
         case 3: kern = mttkrp_flag_kernel<NM, T, 4, 3>; break;
         case 4: kern = mttkrp_flag_kernel<NM, T, 4, 4>; break;
         case 5: kern = mttkrp_flag_kernel<NM, T, 8, 1>; break;
+        case 7: kern = mttkrp_flag_kernel<NM, T, 2, 2, 32>; break;
         default: kern = mttkrp_flag_kernel<NM, T, 4, 3>; break;
     }
     int per_sm = 0;
     SPTT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, 0));
     if (per_sm < 1) per_sm = 1;
-    const int vec = walk::Raw<T>::VEC;
+    const int vec = variant == 7 ? walk::Raw<T, 32>::VEC : walk::Raw<T>::VEC;
     const int64_t groups_per_block = (int64_t)(block / 32) * (32 / (a.ld / vec));
     const int64_t need = (a.nchunks + groups_per_block - 1) / groups_per_block;
     const int64_t cap = (int64_t)device_sm_count() * per_sm;
@@ -241,12 +243,13 @@ sptt_status launch_nm(const walk::Args &a, int block, int variant, cudaStream_t 
 
 template <typename T>
 sptt_status launch_t(int nm, const walk::Args &a, int block, int variant, int32_t *err, cudaStream_t st) {
-    if (variant == 6) {
+    if (variant == 6 || variant == 8) {
+        const bool wide = variant == 8;
         switch (nm) {
-            case 2: return launch_staged<2, T>(a, err, st);
-            case 3: return launch_staged<3, T>(a, err, st);
-            case 4: return launch_staged<4, T>(a, err, st);
-            case 5: return launch_staged<5, T>(a, err, st);
+            case 2: return wide ? launch_staged<2, T, 32>(a, err, st) : launch_staged<2, T, 16>(a, err, st);
+            case 3: return wide ? launch_staged<3, T, 32>(a, err, st) : launch_staged<3, T, 16>(a, err, st);
+            case 4: return wide ? launch_staged<4, T, 32>(a, err, st) : launch_staged<4, T, 16>(a, err, st);
+            case 5: return wide ? launch_staged<5, T, 32>(a, err, st) : launch_staged<5, T, 16>(a, err, st);
             default: return set_error(SPTT_ERR_UNSUPPORTED, "nmodes");
         }
     }
@@ -263,8 +266,10 @@ sptt_status launch_t(int nm, const walk::Args &a, int block, int variant, int32_
 
 constexpr int32_t kDefaultChunk = 128;
 
+static bool staged_variant(int v) { return v == 6 || v == 8; }
+
 sptt_status mttkrp_prepare(sptt_csf *csf, const sptt_sched *sched, cudaStream_t st) {
-    const int32_t chunk = (sched && sched->variant == 6) ? kStageChunk
+    const int32_t chunk = (sched && staged_variant(sched->variant)) ? kStageChunk
                           : ((sched && sched->chunk) ? sched->chunk : kDefaultChunk);
     if (csf->nfibs[csf->nmodes - 1] == 0) return SPTT_OK;
     return csf_ensure_partition(csf, chunk, st);
@@ -278,7 +283,17 @@ sptt_status mttkrp_launch(sptt_csf *csf, const void *const *factors, int32_t dty
     if (nnz == 0) return SPTT_OK;
     int variant = sched ? sched->variant : 0;
     if (variant == 0) variant = (dtype == SPTT_BF16) ? 2 : 3;  // fastest measured per gather type
-    const int32_t chunk = variant == 6 ? kStageChunk : ((sched && sched->chunk) ? sched->chunk : kDefaultChunk);
+    if (variant == 7 || variant == 8) {
+        // 32-byte row segments need ld * sizeof(T) and every gathered factor
+        // 32-byte aligned; otherwise the 16-byte form of the same walk runs
+        const int esz = dtype == SPTT_BF16 ? 2 : 4;
+        bool wide_ok = (ld * esz) % 32 == 0;
+        for (int l = 1; l < N; ++l)
+            wide_ok = wide_ok && reinterpret_cast<uintptr_t>(factors[csf->order[l]]) % 32 == 0;
+        if (!wide_ok) variant = variant == 7 ? 3 : 6;
+    }
+    const int32_t chunk = staged_variant(variant) ? kStageChunk
+                                                  : ((sched && sched->chunk) ? sched->chunk : kDefaultChunk);
     const int block = (sched && sched->block) ? sched->block : 256;
     SPTT_TRY(csf_ensure_partition(csf, chunk, st));
     if (csf->nheavy > 0) SPTT_TRY(fill_zero_launch(heavy, (size_t)csf->nheavy * ld * sizeof(double), st));
@@ -329,8 +344,8 @@ extern "C" sptt_status sptt_mttkrp(const sptt_csf *csf, const void *const *facto
             return set_error(SPTT_ERR_BAD_ARG, "sched->chunk must be a power of two in [16, 4096]");
         if (sched->block && (sched->block < 32 || sched->block > 256 || sched->block % 32))
             return set_error(SPTT_ERR_BAD_ARG, "sched->block must be a multiple of 32 in [32, 256]");
-        if (sched->variant < 0 || sched->variant > 6)
-            return set_error(SPTT_ERR_BAD_ARG, "sched->variant must be in [0, 6]");
+        if (sched->variant < 0 || sched->variant > kMaxVariant)
+            return set_error(SPTT_ERR_BAD_ARG, "sched->variant must be in [0, " + std::to_string(kMaxVariant) + "]");
     }
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     sptt_csf *c = const_cast<sptt_csf *>(csf);

@@ -11,8 +11,8 @@
 // Mapping (in place of the paper's thread-per-slice loops with a lock pool
 // or privatised outputs, Section IV-A and V-D-2):
 //   * a lane group of G = ld / VEC lanes owns one output row; lane g holds
-//     columns [g*VEC, g*VEC + VEC) (VEC = 4 for FP32 factors, 8 for BF16) and
-//     gathers them with one 16-byte load per factor row;
+//     columns [g*VEC, g*VEC + VEC) and gathers them with one 16- or 32-byte
+//     load per factor row (VEC = 4 or 8 FP32 values, 8 or 16 BF16 values);
 //   * the leaves are cut into equal chunks; the CSF's partition gives, per
 //     chunk, the fiber at every level holding the chunk's first leaf, and a
 //     lane group walks its chunk in order with one register accumulator per
@@ -49,37 +49,46 @@ struct Args {
     const int32_t *hidx;             // per slice: heavy row index or -1
 };
 
-// A factor row segment as loaded (16 bytes: 4 FP32 or 8 BF16), widened to
-// FP32 only where it is used.
-template <typename T>
-struct Raw;
-
-template <>
-struct Raw<float> {
-    static constexpr int VEC = 4;
-    __device__ __forceinline__ static uint4 load(const void *base, int64_t row, int ld, int col) {
-        return __ldg(reinterpret_cast<const uint4 *>(static_cast<const float *>(base) + row * ld + col));
-    }
-    __device__ __forceinline__ static void widen(const uint4 &u, float (&x)[4]) {
-        x[0] = __uint_as_float(u.x);
-        x[1] = __uint_as_float(u.y);
-        x[2] = __uint_as_float(u.z);
-        x[3] = __uint_as_float(u.w);
-    }
+// A factor row segment as loaded: W = 16 or 32 bytes per lane (4 or 8 FP32
+// values, 8 or 16 BF16 values), widened to FP32 only where it is used. The
+// 32-byte form is one 256-bit load, so a lane group of ld / VEC lanes still
+// requests a whole row with one instruction while half as many lanes (and
+// their per-leaf bookkeeping) are spent on it; it needs 32-byte aligned
+// rows (ld * sizeof(T) and the base pointer multiples of 32).
+template <int W>
+struct Seg {
+    uint32_t w[W / 4];
 };
 
-template <>
-struct Raw<__nv_bfloat16> {
-    static constexpr int VEC = 8;
-    __device__ __forceinline__ static uint4 load(const void *base, int64_t row, int ld, int col) {
-        return __ldg(reinterpret_cast<const uint4 *>(static_cast<const __nv_bfloat16 *>(base) + row * ld + col));
+template <typename T, int W = 16>
+struct Raw {
+    static_assert(W == 16 || W == 32, "16- or 32-byte row segments");
+    static constexpr int VEC = W / (int)sizeof(T);
+    using Row = Seg<W>;
+    __device__ __forceinline__ static Row load(const void *base, int64_t row, int ld, int col) {
+        const T *p = static_cast<const T *>(base) + row * ld + col;
+        Row r;
+        if constexpr (W == 16) {
+            const uint4 u = __ldg(reinterpret_cast<const uint4 *>(p));
+            r.w[0] = u.x; r.w[1] = u.y; r.w[2] = u.z; r.w[3] = u.w;
+        } else {
+            asm("ld.global.nc.v8.u32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                : "=r"(r.w[0]), "=r"(r.w[1]), "=r"(r.w[2]), "=r"(r.w[3]),
+                  "=r"(r.w[4]), "=r"(r.w[5]), "=r"(r.w[6]), "=r"(r.w[7])
+                : "l"(p));
+        }
+        return r;
     }
-    __device__ __forceinline__ static void widen(const uint4 &u, float (&x)[8]) {
-        const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+    __device__ __forceinline__ static void widen(const Row &u, float (&x)[VEC]) {
+        if constexpr (sizeof(T) == 4) {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {  // bf16 -> f32 is exact: the bits move to the top half
-            x[2 * i] = __uint_as_float(w[i] << 16);
-            x[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u);
+            for (int i = 0; i < VEC; ++i) x[i] = __uint_as_float(u.w[i]);
+        } else {
+#pragma unroll
+            for (int i = 0; i < W / 4; ++i) {  // bf16 -> f32 is exact: the bits move to the top half
+                x[2 * i] = __uint_as_float(u.w[i] << 16);
+                x[2 * i + 1] = __uint_as_float(u.w[i] & 0xffff0000u);
+            }
         }
     }
 };
@@ -160,16 +169,51 @@ __device__ __forceinline__ void end_chunk(const Args &a, int col, Carry<VEC> &cy
     }
 }
 
-// parent += row * child (element-wise); child = 0.
-template <typename T>
-__device__ __forceinline__ void fold(float (&parent)[Raw<T>::VEC], float (&child)[Raw<T>::VEC], const uint4 &row) {
-    float r[Raw<T>::VEC];
-    Raw<T>::widen(row, r);
+// acc += x * y element-wise over VEC values; with 32-byte segments as packed
+// FP32x2 FMAs (each element rounded exactly as fmaf rounds it).
+template <int VEC, bool PACKED>
+__device__ __forceinline__ void fma_vec(float (&acc)[VEC], const float (&x)[VEC], const float (&y)[VEC]) {
+    if constexpr (PACKED) {
 #pragma unroll
-    for (int i = 0; i < Raw<T>::VEC; ++i) {
-        parent[i] = fmaf(r[i], child[i], parent[i]);
-        child[i] = 0.f;
+        for (int i = 0; i < VEC; i += 2) {
+            const float2 r = __ffma2_rn(make_float2(x[i], x[i + 1]), make_float2(y[i], y[i + 1]),
+                                        make_float2(acc[i], acc[i + 1]));
+            acc[i] = r.x;
+            acc[i + 1] = r.y;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < VEC; ++i) acc[i] = fmaf(x[i], y[i], acc[i]);
     }
+}
+
+// acc += s * x element-wise (s broadcast).
+template <int VEC, bool PACKED>
+__device__ __forceinline__ void fma_scalar(float (&acc)[VEC], float s, const float (&x)[VEC]) {
+    if constexpr (PACKED) {
+#pragma unroll
+        for (int i = 0; i < VEC; i += 2) {
+            const float2 r = __ffma2_rn(make_float2(s, s), make_float2(x[i], x[i + 1]),
+                                        make_float2(acc[i], acc[i + 1]));
+            acc[i] = r.x;
+            acc[i + 1] = r.y;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < VEC; ++i) acc[i] = fmaf(s, x[i], acc[i]);
+    }
+}
+
+// parent += row * child (element-wise); child = 0.
+template <typename T, int W = 16>
+__device__ __forceinline__ void fold(float (&parent)[Raw<T, W>::VEC], float (&child)[Raw<T, W>::VEC],
+                                     const typename Raw<T, W>::Row &row) {
+    constexpr int VEC = Raw<T, W>::VEC;
+    float r[VEC];
+    Raw<T, W>::widen(row, r);
+    fma_vec<VEC, W == 32>(parent, r, child);
+#pragma unroll
+    for (int i = 0; i < VEC; ++i) child[i] = 0.f;
 }
 
 // Where a chunk's leaf records (values, leaf indices, level flags) are read
@@ -182,6 +226,11 @@ struct GlobalRecs {
     __device__ __forceinline__ int4 i4(int64_t k) const { return __ldg(reinterpret_cast<const int4 *>(idx + k)); }
     __device__ __forceinline__ uint32_t l4(int64_t k) const { return __ldg(reinterpret_cast<const uint32_t *>(lvl + k)); }
     __device__ __forceinline__ uint2 l8(int64_t k) const { return __ldg(reinterpret_cast<const uint2 *>(lvl + k)); }
+    __device__ __forceinline__ float2 v2(int64_t k) const { return __ldg(reinterpret_cast<const float2 *>(vals + k)); }
+    __device__ __forceinline__ int2 i2(int64_t k) const { return __ldg(reinterpret_cast<const int2 *>(idx + k)); }
+    __device__ __forceinline__ uint32_t l2(int64_t k) const {
+        return __ldg(reinterpret_cast<const unsigned short *>(lvl + k));
+    }
 };
 
 struct SharedRecs {  // shared-memory addresses of the chunk's copy; k0 = the chunk's first leaf
@@ -209,6 +258,21 @@ struct SharedRecs {  // shared-memory addresses of the chunk's copy; k0 = the ch
         asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(r.x), "=r"(r.y) : "r"(sl + (uint32_t)(k - k0)));
         return r;
     }
+    __device__ __forceinline__ float2 v2(int64_t k) const {
+        float2 r;
+        asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(r.x), "=f"(r.y) : "r"(sv + (uint32_t)(k - k0) * 4u));
+        return r;
+    }
+    __device__ __forceinline__ int2 i2(int64_t k) const {
+        int2 r;
+        asm volatile("ld.shared.v2.s32 {%0, %1}, [%2];" : "=r"(r.x), "=r"(r.y) : "r"(si + (uint32_t)(k - k0) * 4u));
+        return r;
+    }
+    __device__ __forceinline__ uint32_t l2(int64_t k) const {
+        uint32_t r;
+        asm volatile("ld.shared.u16 %0, [%1];" : "=r"(r) : "r"(sl + (uint32_t)(k - k0)));
+        return r;
+    }
 };
 
 // The batched walk driven by the per-leaf level flags. A lane group takes
@@ -218,14 +282,15 @@ struct SharedRecs {  // shared-memory addresses of the chunk's copy; k0 = the ch
 // the batch, whose ids are consecutive) is requested before any is used.
 // Rows of fibers at higher levels are requested when the fiber opens and
 // used when it closes.
-template <int NM, typename T, int B, typename Recs = GlobalRecs>
-__device__ __forceinline__ void flag_chunk(const Args &a, int64_t c, int col, Carry<Raw<T>::VEC> &cy,
+template <int NM, typename T, int B, typename Recs = GlobalRecs, int W = 16>
+__device__ __forceinline__ void flag_chunk(const Args &a, int64_t c, int col, Carry<Raw<T, W>::VEC> &cy,
                                            const Recs &rec) {
-    using Rw = Raw<T>;
+    using Rw = Raw<T, W>;
+    using Row = typename Rw::Row;
     constexpr int VEC = Rw::VEC;
     constexpr int NL = NM - 1;  // accumulator levels 0..NM-2
     constexpr int LF = NM - 2;  // level of the leaves' parent fibers
-    static_assert(B == 4 || B == 8, "batch of 4 or 8 leaves");
+    static_assert(B == 2 || B == 4 || B == 8, "batch of 2, 4 or 8 leaves");
     const int ld = a.ld;
     const int64_t k0 = c * (int64_t)a.chunk;
     const int64_t k1 = (k0 + a.chunk < a.nnz) ? k0 + a.chunk : a.nnz;
@@ -237,7 +302,7 @@ __device__ __forceinline__ void flag_chunk(const Args &a, int64_t c, int col, Ca
     for (int l = 0; l < NL; ++l)
 #pragma unroll
         for (int i = 0; i < VEC; ++i) acc[l][i] = 0.f;
-    uint4 rowc[NL];  // rows of the open fibers, levels 1..NL-1
+    Row rowc[NL];  // rows of the open fibers, levels 1..NL-1
 #pragma unroll
     for (int l = 1; l < NL; ++l) rowc[l] = Rw::load(a.fac[l], __ldg(a.fids[l] + f[l]), ld, col);
     bool first_slice = true;
@@ -247,12 +312,18 @@ __device__ __forceinline__ void flag_chunk(const Args &a, int64_t c, int col, Ca
         float v[B];
         int32_t li[B];
         uint32_t lw[2] = {0u, 0u};
-        {
+        if constexpr (B == 2) {
+            const float2 va = rec.v2(kb);
+            const int2 ia = rec.i2(kb);
+            v[0] = va.x; v[1 % B] = va.y;
+            li[0] = ia.x; li[1 % B] = ia.y;
+            lw[0] = rec.l2(kb);
+        } else {
             const float4 va = rec.v4(kb);
             const int4 ia = rec.i4(kb);
-            v[0] = va.x; v[1] = va.y; v[2] = va.z; v[3] = va.w;
-            li[0] = ia.x; li[1] = ia.y; li[2] = ia.z; li[3] = ia.w;
-            if (B == 8) {
+            v[0] = va.x; v[1 % B] = va.y; v[2 % B] = va.z; v[3 % B] = va.w;
+            li[0] = ia.x; li[1 % B] = ia.y; li[2 % B] = ia.z; li[3 % B] = ia.w;
+            if constexpr (B == 8) {
                 const float4 vb = rec.v4(kb + 4);
                 const int4 ib = rec.i4(kb + 4);
                 v[4 % B] = vb.x; v[5 % B] = vb.y; v[6 % B] = vb.z; v[7 % B] = vb.w;
@@ -264,8 +335,19 @@ __device__ __forceinline__ void flag_chunk(const Args &a, int64_t c, int col, Ca
                 lw[0] = rec.l4(kb);
             }
         }
+        // ids of the next B level-LF fibers, requested with the records: the
+        // fibers that open in this batch are among them (consecutive ids), so
+        // their rows need not wait for the flags and then for the ids. The
+        // level arrays carry 64 elements of slack past their end; an id is
+        // used only for a fiber that really opens.
+        int32_t nf[B];
+        if constexpr (LF >= 1) {
+            const int32_t *fp = a.fids[LF] + f[LF] + 1;
+#pragma unroll
+            for (int q = 0; q < B; ++q) nf[q] = __ldg(fp + q);
+        }
         const int nvalid = (k1 - kb < B) ? (int)(k1 - kb) : B;
-        uint4 x[B];
+        Row x[B];
 #pragma unroll
         for (int j = 0; j < B; ++j)
             if (j < nvalid) x[j] = Rw::load(a.fac[NM - 1], li[j], ld, col);
@@ -274,19 +356,22 @@ __device__ __forceinline__ void flag_chunk(const Args &a, int64_t c, int col, Ca
         // multiply gathers into bits 24..27 (bit 24 + j = byte j)
         uint32_t sm = 0;
 #pragma unroll
-        for (int w = 0; w < B / 4; ++w) {
+        for (int w = 0; w < (B + 3) / 4; ++w) {
             const uint32_t le = __vcmpleu4(lw[w], (uint32_t)LF * 0x01010101u) & 0x01010101u;
             sm |= (((le * 0x01020408u) >> 24) & 0xfu) << (4 * w);
         }
         sm &= (nvalid >= 32) ? 0xffffffffu : ((1u << nvalid) - 1u);
         if (kb == k0) sm &= ~1u;
-        uint4 nr[B];
+        Row nr[B];
         if constexpr (LF >= 1) {
 #pragma unroll
             for (int j = 0; j < B; ++j)
                 if ((sm >> j) & 1u) {
-                    const int pos = __popc(sm & ((1u << j) - 1u)) + 1;
-                    nr[j] = Rw::load(a.fac[LF], __ldg(a.fids[LF] + f[LF] + pos), ld, col);
+                    const int pos = __popc(sm & ((1u << j) - 1u));  // openings before leaf j
+                    int32_t id = nf[0];
+#pragma unroll
+                    for (int q = 1; q <= j; ++q) id = (pos == q) ? nf[q] : id;
+                    nr[j] = Rw::load(a.fac[LF], id, ld, col);
                 }
         }
 #pragma unroll
@@ -295,14 +380,14 @@ __device__ __forceinline__ void flag_chunk(const Args &a, int64_t c, int col, Ca
             if ((sm >> j) & 1u) {
                 const int d = (int)((lw[j >> 2] >> (8 * (j & 3))) & 0xffu);
                 if constexpr (LF >= 1) {
-                    fold<T>(acc[LF - 1], acc[LF], rowc[LF]);
+                    fold<T, W>(acc[LF - 1], acc[LF], rowc[LF]);
                     ++f[LF];
                     rowc[LF] = nr[j];
                 }
 #pragma unroll
                 for (int l = LF - 1; l >= 1; --l) {
                     if (d <= l) {
-                        fold<T>(acc[l - 1], acc[l], rowc[l]);
+                        fold<T, W>(acc[l - 1], acc[l], rowc[l]);
                         ++f[l];
                         rowc[l] = Rw::load(a.fac[l], __ldg(a.fids[l] + f[l]), ld, col);
                     }
@@ -318,14 +403,13 @@ __device__ __forceinline__ void flag_chunk(const Args &a, int64_t c, int col, Ca
             }
             float xr[VEC];
             Rw::widen(x[j], xr);
-#pragma unroll
-            for (int i = 0; i < VEC; ++i) acc[LF][i] = fmaf(v[j], xr[i], acc[LF][i]);
+            fma_scalar<VEC, W == 32>(acc[LF], v[j], xr);
         }
     }
     // chunk end: fold the open fibers; the open slice's partial is added
     // (or held back when the slice is heavy)
 #pragma unroll
-    for (int l = LF; l >= 1; --l) fold<T>(acc[l - 1], acc[l], rowc[l]);
+    for (int l = LF; l >= 1; --l) fold<T, W>(acc[l - 1], acc[l], rowc[l]);
     end_chunk<VEC>(a, col, cy, f[0], acc[0]);
 }
 

@@ -55,6 +55,27 @@ def test_batched_matches_single_tensor_path_and_continues(cuda_device):
         np.testing.assert_allclose(b.lam(t).numpy(), c.lam().numpy(), rtol=1e-4)
 
 
+@pytest.mark.parametrize("R", [16, 24])
+def test_batched_large_skewed_tensors_match_single_path(R, cuda_device):
+    # tensors of many solve tiles and many chunks, with power-law slices
+    # that span CTAs, next to tiny ones; R = 24 takes the 32-wide kernel
+    specs = [((6000, 900, 300), 250000, 1.3), ((40, 30, 20), 500, 1.0), ((12000, 500, 80, 30), 180000, 1.2),
+             ((3000, 2000, 1000), 120000, 1.1), ((50, 5000, 60), 90000, 1.4)]
+    items = []
+    for k, (dims, nnz, s_) in enumerate(specs):
+        x = tensorgen.sample_unique(list(dims), nnz, 40 + k, "cpu", dist="zipf", s=s_, values="uniform")
+        items.append((list(dims), [i.to(cuda_device) for i in x.inds], x.vals.to(cuda_device)))
+    b = sptt.Batch(items, R, seed=11).init()
+    b.run(4)
+    for t, (dims, inds, vals) in enumerate(items):
+        c = sptt.Cpd(dims, inds, vals, R, seed=11 + t).init()
+        c.iterate(4)
+        np.testing.assert_allclose(b.fit_history(t), c.fit_history(), atol=1e-5, err_msg="tensor %d" % t)
+        for m in range(len(dims)):
+            Fb, Fc = b.factor(t, m), c.factor(m)
+            assert torch.linalg.norm(Fb - Fc) <= 1e-3 * max(1.0, float(torch.linalg.norm(Fc)))
+
+
 def test_batched_graph_replay(cuda_device):
     items = _batch(12, seed=9)
     R = 8

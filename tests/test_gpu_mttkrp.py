@@ -65,7 +65,7 @@ def test_mttkrp_padded_rank(R, ld, cuda_device):
 
 @pytest.mark.parametrize("chunk", [16, 32, 128, 512, 4096])
 @pytest.mark.parametrize("block", [64, 256])
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6, 7, 8])
 def test_mttkrp_schedules_agree(chunk, block, variant, cuda_device):
     dims = (400, 300, 200, 20)
     t = make(dims, 50003, seed=5, dist="zipf", s=1.3)
@@ -75,7 +75,7 @@ def test_mttkrp_schedules_agree(chunk, block, variant, cuda_device):
         _check(M, t, F, root, 16, 1e-5)
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6, 7, 8])
 @pytest.mark.parametrize("nm", [2, 3, 4, 5])
 def test_mttkrp_variants_every_order(variant, nm, cuda_device):
     dims = (290, 170, 50, 30, 10)[:nm]
@@ -120,6 +120,40 @@ def test_mttkrp_heavy_single_slice(cuda_device):
         _check(M, t, F, root, 16, 1e-5)
 
 
+@pytest.mark.parametrize("variant", [7, 8])
+@pytest.mark.parametrize("dtype,ld", [(sptt.SPTT_F32, 4), (sptt.SPTT_F32, 12), (sptt.SPTT_F32, 24),
+                                      (sptt.SPTT_F32, 64), (sptt.SPTT_F32, 128), (sptt.SPTT_BF16, 8),
+                                      (sptt.SPTT_BF16, 24), (sptt.SPTT_BF16, 32), (sptt.SPTT_BF16, 256)])
+def test_wide_segments_any_ld(variant, dtype, ld, cuda_device):
+    # 32-byte segments where ld allows them (F32 ld % 8, BF16 ld % 16), the
+    # 16-byte walk otherwise; the result is the same either way
+    dims = (700, 300, 90)
+    t = make(dims, 40000, seed=ld, dist="zipf", s=1.2)
+    F = rand_factors(dims, ld, seed=ld + 1)
+    if dtype == sptt.SPTT_BF16:
+        F = [f.to(torch.bfloat16).float() for f in F]
+    for root in range(3):
+        M = _run(t, root, F, cuda_device, dtype=dtype, sched=(64, 256, variant))
+        _check(M, t, F, root, ld, 1e-5)
+
+
+@pytest.mark.parametrize("variant", [7, 8])
+def test_wide_segments_misaligned_factor(variant, cuda_device):
+    # a factor that is 16- but not 32-byte aligned runs the 16-byte walk
+    dims = (500, 400, 60)
+    t = make(dims, 30000, seed=2, dist="zipf", s=1.1)
+    F = rand_factors(dims, 16, seed=4)
+    di, dv = to_dev(t, cuda_device)
+    c = sptt.Csf(dims, di, dv, 0)
+    base = torch.zeros(dims[1] * 16 + 4, device=cuda_device)
+    shifted = base[4:].view(dims[1], 16)
+    shifted.copy_(F[1].to(cuda_device))
+    assert shifted.data_ptr() % 32 == 16
+    fd = [F[0].to(cuda_device), shifted, F[2].to(cuda_device)]
+    M = c.mttkrp(fd, sched=(64, 256, variant)).cpu().double().numpy()
+    _check(M, t, F, 0, 16, 1e-5)
+
+
 def test_mttkrp_custom_level_order(cuda_device):
     dims = (100, 80, 60, 40)
     t = make(dims, 20000, seed=4)
@@ -136,7 +170,7 @@ def test_mttkrp_rejects_bad_arguments(cuda_device):
     c = sptt.Csf(dims, di, dv, 0)
     F = [torch.rand(d, 8, device=cuda_device) for d in dims]
     out = torch.empty(10, 8, device=cuda_device)
-    for bad in (dict(sched=(24, 256, 0)), dict(sched=(64, 512, 0)), dict(sched=(64, 256, 7)),
+    for bad in (dict(sched=(24, 256, 0)), dict(sched=(64, 512, 0)), dict(sched=(64, 256, 9)),
                 dict(factor_dtype=7)):
         with pytest.raises(sptt.SpttError):
             c.mttkrp(F, out=out, **bad)
@@ -155,7 +189,7 @@ def test_staged_variant_reports_no_timeout_and_matches_default(cuda_device):
     c = sptt.Csf(dims, di, dv, 0)
     F = [torch.rand(d, 16, device=cuda_device) for d in dims]
     ref = c.mttkrp(F).clone()
-    for _ in range(3):
-        got = c.mttkrp(F, sched=(64, 256, 6, 0))
+    for variant in (6, 8, 6, 8):
+        got = c.mttkrp(F, sched=(64, 256, variant, 0))
         assert sptt.lib().sptt_csf_check(c.handle, torch.cuda.current_stream().cuda_stream) == 0
         assert torch.allclose(got, ref, rtol=1e-5, atol=1e-5)
