@@ -53,6 +53,8 @@ def parse():
                    help="also time the 512-tensor batched workload (one persistent launch per run)")
     p.add_argument("--extra-sched", action="store_true",
                    help="also train the learned scheduler and report its held-out regret")
+    p.add_argument("--extra-one-csf", action="store_true",
+                   help="also time one CSF for all modes (non-root MTTKRPs with privatised hot rows)")
     p.add_argument("--extra-mixed4", action="store_true",
                    help="also time the 4-mode R=64 workload: BF16 gathers + FP32 refinement vs FP32")
     p.add_argument("--batch-count", type=int, default=512)
@@ -338,6 +340,62 @@ def mixed4_extra(args, dev):
     return out
 
 
+def one_csf_extra(args, t, R, dev):
+    """One CSF for all modes (the non-root modes by sptt_mttkrp_mode) against
+    one CSF per mode, on the bench tensor: per-mode MTTKRP times, CP-ALS
+    s/iter, CSF memory and the fit after 10 iterations."""
+    import torch
+
+    import paper_1812_05961_gb300 as sptt
+    dims = t.dims
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    F = [torch.rand(d, R, device=dev) for d in dims]
+    out = {}
+    for csf_mode in (1, 2):
+        root = min(range(3), key=lambda m: (dims[m], m)) if csf_mode == 1 else max(range(3), key=lambda m: (dims[m], -m))
+        c = sptt.Csf(dims, t.inds, t.vals, root)
+        csf_bytes = sum(n * 4 for n in c.nfibs) + sum(n * 4 for n in c.nfibs[:-1]) + c.nfibs[-1] * 5
+        ms = {}
+        for m in range(3):
+            o = torch.empty(dims[m], R, device=dev)
+            ms["mode%d" % m] = timed(lambda: c.mttkrp_mode(m, F, out=o))
+            if m != root:
+                ms["mode%d_global_only" % m] = timed(lambda: c.mttkrp_mode(m, F, out=o, sched=(128, 256, 1)))
+        del c
+        cpd = sptt.Cpd(dims, t.inds, t.vals, R, seed=1, csf_mode=csf_mode).init()
+        cpd.iterate(2)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        cpd.iterate(8)
+        b.record(stream)
+        torch.cuda.synchronize()
+        s_iter = a.elapsed_time(b) / 8 / 1e3
+        out["csf_mode%d" % csf_mode] = {"root": root, "mttkrp_ms": ms, "s_per_iter": s_iter,
+                                        "GnnzR_per_s": 3 * t.nnz * R / s_iter / 1e9, "fit_after_10": cpd.fit()[0],
+                                        "csf_bytes": csf_bytes}
+        del cpd
+        torch.cuda.empty_cache()
+    ref = sptt.Cpd(dims, t.inds, t.vals, R, seed=1).init()
+    ref.iterate(10)
+    out["per_mode_fit_after_10"] = ref.fit()[0]
+    del ref
+    torch.cuda.empty_cache()
+    return out
+
+
 def sched_extra(args, dev):
     """The learned scheduler: trained on autotuner sweeps of generated tensors,
     evaluated on held-out ones and on a 5-mode probe tensor."""
@@ -379,10 +437,9 @@ def sched_extra(args, dev):
     model, hist = schedtrain.train(train, steps=3000, lr=3e-3)
     res = {"train_samples": len(train.samples), "heldout_samples": len(held.samples), "sweep_s": round(sweep_s, 1),
            "loss_first_last": [float(hist[0]), float(hist[-1])]}
-    d = schedtrain.default_index()
     for name, ds in (("heldout", held), ("probe_5mode_2e7", probe)):
         res[name] = {"learned": schedtrain.summarize(schedtrain.regret(ds, model)),
-                     "default": schedtrain.summarize(schedtrain.regret(ds, fixed=d))}
+                     "default": schedtrain.summarize(schedtrain.regret(ds))}
     return res
 
 
@@ -528,6 +585,9 @@ def ours(args, rank, world, local):
     if args.extra_sched:
         torch.cuda.empty_cache()
         extras["scheduler"] = sched_extra(args, dev)
+    if args.extra_one_csf:
+        torch.cuda.empty_cache()
+        extras["one_csf"] = one_csf_extra(args, t, R, dev)
     if args.extra_mixed4:
         torch.cuda.empty_cache()
         extras["mixed_precision_4mode"] = mixed4_extra(args, dev)

@@ -137,16 +137,17 @@ sptt_status sptt_csf_copy_level(const sptt_csf *csf, int32_t level, int32_t *fpt
  *   chunk       non-zeros per work unit of a lane group; power of two in
  *               [16, 4096]; 0 = default
  *   block       threads per CTA (multiple of 32, <= 256); 0 = default
- *   variant     kernel variant: 0 = default (3 for F32 gathers, 2 for BF16);
- *               6 = flag walk whose leaf records are staged in shared memory
- *               by bulk copies (chunk fixed at 64); 1 = plain walk (fiber ends
- *               from fptr, one leaf at a time); 2..5 = batched walk driven by
- *               the per-leaf level flags with (batch, CTAs per SM) = (8, 2),
- *               (4, 3), (4, 4), (8, 1); 7 = flag walk and 8 = staged walk
- *               with 32-byte row segments (one 256-bit gather per lane, half
- *               the lanes per row) and batches of 2 leaves; they need
- *               ld * element size and every non-root factor 32-byte aligned,
- *               and otherwise run as variant 3 / 6
+ *   variant     kernel variant: 0 = default (the fastest measured for the
+ *               gather type and ld); 1 = plain walk (fiber ends from fptr,
+ *               one leaf at a time); 2..5 = walk driven by the per-leaf
+ *               level flags, (leaves per batch, CTAs per SM, pipelined) =
+ *               (8, 1, yes), (4, 3, no), (4, 2, yes), (2, 3, yes); 6 = the
+ *               pipelined walk with its leaf records staged in shared memory
+ *               by bulk copies (chunk fixed at 64); 7 = flag walk and 8 =
+ *               staged walk with 32-byte row segments (one 256-bit gather per
+ *               lane, half the lanes per row) and batches of 2 leaves; 7 and
+ *               8 need ld * element size and every non-root factor 32-byte
+ *               aligned, and otherwise run as variant 3 / 6
  */
 typedef struct {
     int32_t chunk;
@@ -179,6 +180,34 @@ typedef struct {
  */
 sptt_status sptt_mttkrp(const sptt_csf *csf, const void *const *factors, int32_t factor_dtype,
                         int32_t ld, float *out, const sptt_sched *sched, sptt_stream stream);
+
+/*
+ * MTTKRP for any mode n of the tensor from one CSF (Section III; Algorithm 1
+ * lines 5, 8, 11), the single-CSF form whose output conflicts the paper
+ * resolves with a lock pool or privatised copies (Section IV-A, V-D-2).
+ * mode = the CSF's root runs sptt_mttkrp. For a mode at tree level L >= 1,
+ * each level-L fiber (each leaf when L = N-1) adds the Hadamard product of
+ * its ancestors' factor rows times the sum below it to M[fids[L][f], :]:
+ * the same M as the element definition of sptt_mttkrp.
+ *   factors   as for sptt_mttkrp; factors[n] is not read and may be NULL.
+ *   ld, out   as for sptt_mttkrp (out: dims[n] x ld, overwritten).
+ *   sched     chunk as for sptt_mttkrp; variant: 0 = default (privatised hot
+ *             rows), 1 = every row through global reductions, 2 = privatised
+ *             hot rows: the rows with the most contributions (up to 64 KB
+ *             of them) are summed per CTA in shared memory and added to out
+ *             every few rounds of chunks. order is ignored.
+ * Accumulation is FP32 (global and shared-memory atomics, so the summation
+ * order varies from run to run). A privatised row is summed in FP32 runs of
+ * a few rounds of chunks per CTA; with variant 1 a row's n contributions
+ * form one FP32 sum (error about sqrt(n) 2^-24 of the row's scale, so rows
+ * with ~10^5 contributions or more miss the 1e-5 bound that the privatised
+ * default keeps). The first call for a mode and row width
+ * builds the work partition and the hot-row table (allocates and
+ * synchronises); later calls are asynchronous. Errors: BAD_ARG, OOM.
+ */
+sptt_status sptt_mttkrp_mode(const sptt_csf *csf, int32_t mode, const void *const *factors,
+                             int32_t factor_dtype, int32_t ld, float *out, const sptt_sched *sched,
+                             sptt_stream stream);
 
 /* ------------------------------------------------------------------------ */
 /* Dense R x R pieces (Algorithm 1 lines 4, 7, 10).                          */
@@ -234,6 +263,16 @@ sptt_status sptt_gram_noalloc(const float *A, int64_t rows, int32_t rank, int32_
  *                 the autotuner (sptt_autotune); 2: choose it with the learned
  *                 scheduler `mlp` (sptt_mlp_predict on sptt_csf_features)
  *   mlp           the trained scheduler for plan = 2
+ *   csf_mode      0: one CSF per mode, each rooted at its mode (root-mode
+ *                 MTTKRPs only; N times the CSF memory); 1: one CSF for all
+ *                 modes, the shortest mode at the root and the others below
+ *                 by ascending length; 2: one CSF, the longest mode at the
+ *                 root. With one CSF the non-root modes use sptt_mttkrp_mode's
+ *                 kernels, sched (not mode_sched) applies to every mode, and
+ *                 plan must be 0; with the default schedule each non-root
+ *                 mode takes the output-conflict strategy (privatised hot
+ *                 rows or global reductions) that ran faster in a timing
+ *                 at create time (which therefore synchronises).
  */
 typedef struct sptt_mlp sptt_mlp;
 typedef struct {
@@ -246,6 +285,7 @@ typedef struct {
     const sptt_sched *mode_sched;
     int32_t plan;
     const sptt_mlp *mlp;
+    int32_t csf_mode;
 } sptt_opts;
 
 typedef struct sptt_cpd sptt_cpd;

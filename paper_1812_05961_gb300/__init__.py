@@ -59,7 +59,7 @@ class sptt_opts(ctypes.Structure):
                 ("refine_iters", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("profile", ctypes.c_int32), ("sched", ctypes.POINTER(sptt_sched)),
                 ("mode_sched", ctypes.POINTER(sptt_sched)), ("plan", ctypes.c_int32),
-                ("mlp", ctypes.c_void_p)]
+                ("mlp", ctypes.c_void_p), ("csf_mode", ctypes.c_int32)]
 
 
 _lib = None
@@ -92,6 +92,7 @@ def lib() -> ctypes.CDLL:
             "sptt_csf_copy_level": (_ST, [_P, _I32, _P, _P, _P, _P]),
             "sptt_csf_check": (_ST, [_P, _P]),
             "sptt_mttkrp": (_ST, [_P, _P, _I32, _I32, _P, _P, _P]),
+            "sptt_mttkrp_mode": (_ST, [_P, _I32, _P, _I32, _I32, _P, _P, _P]),
             "sptt_gram": (_ST, [_P, _I64, _I32, _I32, _P, _P]),
             "sptt_gram_noalloc": (_ST, [_P, _I64, _I32, _I32, _P, _P]),
             "sptt_cpd_create": (_ST, [ctypes.POINTER(sptt_coo), _I32, ctypes.POINTER(sptt_opts), _P,
@@ -191,9 +192,9 @@ def _sched(s):
 
 
 def _opts(seed=0, precision=SPTT_F32, refine_iters=0, use_graph=0, profile=0, sched=None,
-          mode_sched=None, plan=0, mlp=None):
+          mode_sched=None, plan=0, mlp=None, csf_mode=0):
     o = sptt_opts(seed, precision, refine_iters, use_graph, profile, None, None, plan,
-                  None if mlp is None else (mlp.handle if hasattr(mlp, "handle") else mlp))
+                  None if mlp is None else (mlp.handle if hasattr(mlp, "handle") else mlp), csf_mode)
     keep = []
     if sched is not None:
         one = _sched(sched)
@@ -275,6 +276,22 @@ def sptt_mttkrp(csf: int, factors: Sequence[Optional[torch.Tensor]], out: torch.
         s = _sched(sched)
     _check(lib().sptt_mttkrp(csf, arr, factor_dtype, ld, out.data_ptr(),
                              None if s is None else ctypes.byref(s), _stream(stream)), "sptt_mttkrp")
+    return out
+
+
+def sptt_mttkrp_mode(csf: int, mode: int, factors: Sequence[Optional[torch.Tensor]], out: torch.Tensor,
+                     factor_dtype: int = SPTT_F32, sched=None, stream=None):
+    """out (dims[mode] x ld float32, device) = MTTKRP of any mode from one CSF."""
+    ld = out.shape[1]
+    arr = (ctypes.c_void_p * len(factors))(*[0 if f is None else f.data_ptr() for f in factors])
+    for f in factors:
+        if f is not None and (not f.is_contiguous() or f.shape[1] != ld):
+            raise ValueError("factors must be contiguous with ld = out.shape[1] columns")
+    s = None
+    if sched is not None:
+        s = _sched(sched)
+    _check(lib().sptt_mttkrp_mode(csf, mode, arr, factor_dtype, ld, out.data_ptr(),
+                                  None if s is None else ctypes.byref(s), _stream(stream)), "sptt_mttkrp_mode")
     return out
 
 
@@ -583,6 +600,14 @@ class Csf:
             dev = next(f.device for f in factors if f is not None)
             out = torch.empty((self.dims[self.root], ld), dtype=torch.float32, device=dev)
         return sptt_mttkrp(self.handle, factors, out, factor_dtype, sched, stream)
+
+    def mttkrp_mode(self, mode, factors, out=None, ld=None, factor_dtype=SPTT_F32, sched=None, stream=None):
+        if out is None:
+            if ld is None:
+                ld = next(f.shape[1] for f in factors if f is not None)
+            dev = next(f.device for f in factors if f is not None)
+            out = torch.empty((self.dims[mode], ld), dtype=torch.float32, device=dev)
+        return sptt_mttkrp_mode(self.handle, mode, factors, out, factor_dtype, sched, stream)
 
     def close(self):
         if self.handle:

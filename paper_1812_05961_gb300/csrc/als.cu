@@ -38,10 +38,14 @@ struct sptt_cpd {
     bool has_msched[SPTT_MAX_MODES] = {false};
     cudaStream_t st = nullptr;
     sptt_csf *csf[SPTT_MAX_MODES] = {nullptr};
+    // csf_mode 1/2: one CSF for every mode; one_level[n] = the tree level of mode n
+    sptt_csf *one = nullptr;
+    int32_t one_level[SPTT_MAX_MODES] = {0};
+    sptt_sched one_sched[SPTT_MAX_MODES] = {};  // schedule of each non-root mode's MTTKRP
     float *A[SPTT_MAX_MODES] = {nullptr};
     __nv_bfloat16 *Ab[SPTT_MAX_MODES] = {nullptr};
     double *G[SPTT_MAX_MODES] = {nullptr};
-    float *M = nullptr;      // MTTKRP output, compact (one row per slice)
+    float *M = nullptr;      // MTTKRP output: compact (one row per slice) for a root mode, full otherwise
     double *Mh = nullptr;    // FP64 rows of the heavy slices
     double *normx2 = nullptr;
     double *fits = nullptr;  // device ring of fit values, kFitHistory entries
@@ -112,15 +116,22 @@ sptt_status run_iteration(sptt_cpd *c, bool bf16) {
     for (int m = 0; m < N; ++m) fac[m] = bf16 ? (const void *)c->Ab[m] : (const void *)c->A[m];
     for (int n = 0; n < N; ++n) {
         const sptt_sched *sched = c->has_msched[n] ? &c->msched[n] : nullptr;
+        sptt_csf *cs = c->one ? c->one : c->csf[n];
+        const int L = c->one ? c->one_level[n] : 0;  // L > 0: a non-root mode of the one CSF
+        const int32_t dt = bf16 ? SPTT_BF16 : SPTT_F32;
         {
             Timed t(c, 0);
-            SPTT_TRY(mttkrp_launch(c->csf[n], fac, bf16 ? SPTT_BF16 : SPTT_F32, c->ld, c->M, c->Mh, sched, c->st));
+            if (L == 0) SPTT_TRY(mttkrp_launch(cs, fac, dt, c->ld, c->M, c->Mh, sched, c->st));
+            else SPTT_TRY(mttkrp_mode_launch(cs, L, fac, dt, c->ld, c->M, &c->one_sched[n], c->st));
         }
         {
             Timed t(c, 1);
             SPTT_TRY(normal_prep_launch(c->G, N, n, c->rank, &c->w, c->st));
         }
-        const sptt_csf *cs = c->csf[n];
+        // the compact result of a root mode maps slice f to row fids[0][f];
+        // a non-root mode's result is full (row i is row i)
+        const int32_t *rowmap = L == 0 ? cs->fids[0] : nullptr;
+        const int64_t nrows = L == 0 ? cs->nfibs[0] : c->dims[n];
         {
             Timed t(c, 2);
             // rows of mode n without a slice come out zero: clear A (and its
@@ -128,17 +139,75 @@ sptt_status run_iteration(sptt_cpd *c, bool bf16) {
             SPTT_TRY(fill_zero_launch(c->A[n], (size_t)c->dims[n] * c->ld * sizeof(float), c->st));
             if (c->Ab[n])
                 SPTT_TRY(fill_zero_launch(c->Ab[n], (size_t)c->dims[n] * c->ld * sizeof(__nv_bfloat16), c->st));
-            SPTT_TRY(postsolve_launch(c->M, c->Mh, cs->hidx, cs->fids[0], c->A[n], cs->nfibs[0], &c->w, c->st));
+            SPTT_TRY(postsolve_launch(c->M, L == 0 ? c->Mh : nullptr, L == 0 ? cs->hidx : nullptr, rowmap, c->A[n],
+                                      nrows, &c->w, c->st));
         }
         {
             Timed t(c, 3);
             SPTT_TRY(finalize_launch(c->G[n], &c->w, c->st));
-            SPTT_TRY(normalize_launch(c->A[n], c->Ab[n], cs->fids[0], cs->nfibs[0], &c->w, c->st));
+            SPTT_TRY(normalize_launch(c->A[n], c->Ab[n], rowmap, nrows, &c->w, c->st));
         }
     }
     {
         Timed t(c, 4);
         SPTT_TRY(fit_launch(c->G, N, c->normx2, &c->w, c->fits, kFitHistory, c->iter_dev, c->st));
+    }
+    return SPTT_OK;
+}
+
+// Work partitions (and, with one CSF, the hot-row tables of the non-root
+// levels) of every mode's MTTKRP; their first build allocates and
+// synchronises, so this runs before any capture.
+sptt_status prepare_all(sptt_cpd *c) {
+    if (c->one) {
+        const sptt_sched *s = c->has_msched[0] ? &c->msched[0] : nullptr;
+        SPTT_TRY(mttkrp_prepare(c->one, s, c->st));
+        for (int n = 0; n < c->N; ++n)
+            if (c->one_level[n] > 0)
+                SPTT_TRY(mttkrp_mode_prepare(c->one, c->one_level[n], c->ld, &c->one_sched[n], c->st));
+        return SPTT_OK;
+    }
+    for (int n = 0; n < c->N; ++n)
+        SPTT_TRY(mttkrp_prepare(c->csf[n], c->has_msched[n] ? &c->msched[n] : nullptr, c->st));
+    return SPTT_OK;
+}
+
+// With one CSF and the default schedule, each non-root mode's MTTKRP takes
+// whichever output-conflict strategy (privatised hot rows, or global
+// reductions only) ran faster in a short timing on the handle's own factors
+// and buffers (the results are discarded; the factors are re-initialised
+// by sptt_cpd_init).
+sptt_status choose_conflict_strategy(sptt_cpd *c) {
+    const void *fac[SPTT_MAX_MODES];
+    for (int m = 0; m < c->N; ++m) fac[m] = c->A[m];
+    cudaEvent_t e[3];
+    for (auto &x : e) SPTT_CUDA(cudaEventCreate(&x));
+    struct Ev {
+        cudaEvent_t *e;
+        ~Ev() { for (int i = 0; i < 3; ++i) cudaEventDestroy(e[i]); }
+    } guard{e};
+    for (int n = 0; n < c->N; ++n) {
+        const int L = c->one_level[n];
+        if (L == 0) continue;
+        float best = 0.f;
+        int best_v = 2;
+        for (int v = 2; v >= 1; --v) {
+            sptt_sched s = c->one_sched[n];
+            s.variant = v;
+            SPTT_TRY(mttkrp_mode_prepare(c->one, L, c->ld, &s, c->st));
+            SPTT_TRY(mttkrp_mode_launch(c->one, L, fac, SPTT_F32, c->ld, c->M, &s, c->st));  // warm-up
+            SPTT_CUDA(cudaEventRecord(e[0], c->st));
+            SPTT_TRY(mttkrp_mode_launch(c->one, L, fac, SPTT_F32, c->ld, c->M, &s, c->st));
+            SPTT_CUDA(cudaEventRecord(e[1], c->st));
+            SPTT_CUDA(cudaEventSynchronize(e[1]));
+            float ms = 0.f;
+            SPTT_CUDA(cudaEventElapsedTime(&ms, e[0], e[1]));
+            if (v == 2 || ms < best) {
+                best = ms;
+                best_v = v;
+            }
+        }
+        c->one_sched[n].variant = best_v;
     }
     return SPTT_OK;
 }
@@ -149,8 +218,7 @@ sptt_status run_iteration(sptt_cpd *c, bool bf16) {
 sptt_status run_iteration_graph(sptt_cpd *c, bool bf16) {
     const int p = bf16 ? 1 : 0;
     if (!c->graph[p]) {
-        for (int n = 0; n < c->N; ++n)
-            SPTT_TRY(mttkrp_prepare(c->csf[n], c->has_msched[n] ? &c->msched[n] : nullptr, c->st));
+        SPTT_TRY(prepare_all(c));
         SPTT_CUDA(cudaStreamSynchronize(c->st));
         cudaGraph_t g = nullptr;
         SPTT_CUDA(cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
@@ -183,13 +251,16 @@ sptt_status step(sptt_cpd *c, bool bf16) {
 
 sptt_status read_fit(sptt_cpd *c, int64_t it, double *out) {
     SPTT_CUDA(cudaMemcpyAsync(out, c->fits + (it % kFitHistory), sizeof(double), cudaMemcpyDeviceToHost, c->st));
-    for (int m = 0; m < c->N; ++m) SPTT_TRY(sptt_csf_check(c->csf[m], c->st));  // synchronises
+    if (c->one) SPTT_TRY(sptt_csf_check(c->one, c->st));  // synchronises
+    for (int m = 0; m < c->N; ++m)
+        if (c->csf[m]) SPTT_TRY(sptt_csf_check(c->csf[m], c->st));
     return SPTT_OK;
 }
 
 void destroy(sptt_cpd *c) {
     if (!c) return;
     cudaStreamSynchronize(c->st);
+    if (c->one) csf_destroy(c->one);
     for (int m = 0; m < SPTT_MAX_MODES; ++m) {
         if (c->csf[m]) csf_destroy(c->csf[m]);
         if (c->A[m]) dev_free(c->A[m], c->st);
@@ -240,6 +311,9 @@ extern "C" sptt_status sptt_cpd_create(const sptt_coo *coo, int32_t rank, const 
                                                    "] and order in [0, 1]");
     }
     if (o.plan < 0 || o.plan > 2) return set_error(SPTT_ERR_BAD_ARG, "opts.plan must be 0, 1 or 2");
+    if (o.csf_mode < 0 || o.csf_mode > 2) return set_error(SPTT_ERR_BAD_ARG, "opts.csf_mode must be 0, 1 or 2");
+    if (o.csf_mode != 0 && (o.plan != 0 || o.mode_sched))
+        return set_error(SPTT_ERR_BAD_ARG, "one CSF for all modes takes one schedule (opts.sched) and plan 0");
     if (o.plan == 2 && !o.mlp) return set_error(SPTT_ERR_BAD_ARG, "opts.plan = 2 needs opts.mlp");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     sptt_cpd *c = new sptt_cpd();
@@ -263,7 +337,23 @@ extern "C" sptt_status sptt_cpd_create(const sptt_coo *coo, int32_t rank, const 
             c->has_msched[m] = true;
         }
     }
-    {
+    if (o.csf_mode != 0) {
+        // one CSF: the shortest (csf_mode 1) or longest (2) mode at the root,
+        // ties to the lower mode id, the others below by ascending length
+        int root = 0;
+        for (int m = 1; m < c->N; ++m)
+            if (o.csf_mode == 1 ? c->dims[m] < c->dims[root] : c->dims[m] > c->dims[root]) root = m;
+        int32_t order[SPTT_MAX_MODES];
+        level_order(c->dims, c->N, root, 0, order);
+        DevCoo dc;
+        SPTT_TRY(coo_to_device(coo, st, &dc));
+        SPTT_TRY(csf_build_device(&dc.coo, root, order, st, &c->one));
+        for (int l = 0; l < c->N; ++l) c->one_level[order[l]] = l;
+        for (int m = 0; m < c->N; ++m) {
+            c->one_sched[m] = c->has_msched[m] ? c->msched[m] : sptt_sched{};
+            if (c->one_sched[m].variant != 1) c->one_sched[m].variant = 2;  // privatise unless told otherwise
+        }
+    } else {
         DevCoo dc;
         SPTT_TRY(coo_to_device(coo, st, &dc));
         for (int m = 0; m < c->N; ++m) {
@@ -302,12 +392,15 @@ extern "C" sptt_status sptt_cpd_create(const sptt_coo *coo, int32_t rank, const 
         }
     }
     int64_t max_rows = 0, max_slices = 0, max_heavy = 0;
+    SPTT_TRY(prepare_all(c));
     for (int m = 0; m < c->N; ++m) {
         const int64_t rows = c->dims[m];
         if (rows > max_rows) max_rows = rows;
-        if (c->csf[m]->nfibs[0] > max_slices) max_slices = c->csf[m]->nfibs[0];
-        SPTT_TRY(mttkrp_prepare(c->csf[m], c->has_msched[m] ? &c->msched[m] : nullptr, st));
-        if (c->csf[m]->nheavy > max_heavy) max_heavy = c->csf[m]->nheavy;
+        // rows of the MTTKRP result of mode m: compact for a root mode, full otherwise
+        const sptt_csf *cs = c->one ? c->one : c->csf[m];
+        const int64_t mrows = (c->one && c->one_level[m] > 0) ? rows : cs->nfibs[0];
+        if (mrows > max_slices) max_slices = mrows;
+        if (cs->nheavy > max_heavy) max_heavy = cs->nheavy;
         SPTT_TRY(dev_alloc_n(&c->A[m], (size_t)rows * c->ld, st));
         SPTT_TRY(fill_zero_launch(c->A[m], (size_t)rows * c->ld * sizeof(float), st));
         if (o.precision == SPTT_BF16) {
@@ -324,8 +417,13 @@ extern "C" sptt_status sptt_cpd_create(const sptt_coo *coo, int32_t rank, const 
     SPTT_TRY(dev_alloc_n(&c->iter_dev, 1, st));
     SPTT_TRY(fill_zero_launch(c->iter_dev, sizeof(int64_t), st));
     SPTT_TRY(dense_work_alloc(&c->w, rank, c->ld, max_rows, st));
-    const sptt_csf *c0 = c->csf[0];
+    const sptt_csf *c0 = c->one ? c->one : c->csf[0];
     SPTT_TRY(sumsq_launch(c0->vals, c0->nfibs[c0->nmodes - 1], c->normx2, st));
+    if (c->one && !(c->has_msched[0] && c->msched[0].variant != 0)) {
+        for (int m = 0; m < c->N; ++m)
+            SPTT_TRY(init_factor_launch(c->opts.seed, m, c->dims[m], c->rank, c->ld, c->A[m], st));
+        SPTT_TRY(choose_conflict_strategy(c));
+    }
     SPTT_CUDA(cudaStreamSynchronize(st));
     guard.c = nullptr;
     *out = c;

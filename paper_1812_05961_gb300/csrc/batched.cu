@@ -153,7 +153,7 @@ template <int NM>
 __device__ __noinline__ void walk_chunk(const walk::Args &w, int64_t c, int col) {
     const walk::GlobalRecs rec{w.vals, w.fids[NM - 1], w.lvl};
     walk::Carry<4> cy;
-    walk::flag_chunk<NM, float, 4>(w, c, col, cy, rec);
+    walk::flag_chunk<NM, float, 4, walk::GlobalRecs, 16, false>(w, c, col, cy, rec);
     walk::flush_carry(w, col, cy);
 }
 

@@ -267,6 +267,8 @@ void csf_destroy(sptt_csf *c) {
     for (int l = 0; l < kMaxModes; ++l) {
         if (c->fptr[l]) cudaFree(c->fptr[l]);
         if (c->fids[l]) cudaFree(c->fids[l]);
+        if (c->hslot[l]) cudaFree(c->hslot[l]);
+        if (c->hrow[l]) cudaFree(c->hrow[l]);
     }
     if (c->vals) cudaFree(c->vals);
     if (c->lvl) cudaFree(c->lvl);

@@ -149,7 +149,7 @@ __global__ void normalize_kernel(float *__restrict__ A, __nv_bfloat16 *__restric
          t += (int64_t)gridDim.x * blockDim.x) {
         const int64_t f = t / qpr;
         const int c0 = (int)(t - f * qpr) * 4;
-        const int64_t q = ((int64_t)__ldg(fids0 + f) * ld + c0) / 4;
+        const int64_t q = ((fids0 ? (int64_t)__ldg(fids0 + f) : f) * ld + c0) / 4;
         float4 v = reinterpret_cast<float4 *>(A)[q];
         float x[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll

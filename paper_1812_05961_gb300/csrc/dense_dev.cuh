@@ -97,7 +97,8 @@ __device__ __forceinline__ void solve_load_w(SolveTile<RP> &sm, const float *__r
 }
 
 // One tile starting at compact row i0. CLEAR leaves the rows of M (and the
-// heavy rows) it read at zero, ready for the next MTTKRP.
+// heavy rows) it read at zero, ready for the next MTTKRP. fids0 = NULL: row i
+// of M is row i of A (a full MTTKRP result); hidx = NULL: no heavy rows.
 template <int RP, bool CLEAR>
 __device__ __forceinline__ void solve_tile(SolveTile<RP> &sm, SolveRun &acc, float *M, double *heavy,
                                            const int32_t *__restrict__ hidx, const int32_t *__restrict__ fids0,
@@ -110,7 +111,7 @@ __device__ __forceinline__ void solve_tile(SolveTile<RP> &sm, SolveRun &acc, flo
         const int64_t i = i0 + r;
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
         if (i < rows && c < ld) {
-            const int32_t h = __ldg(hidx + i);
+            const int32_t h = hidx ? __ldg(hidx + i) : -1;
             float4 *pm = reinterpret_cast<float4 *>(M + i * ld + c);
             if (h >= 0) {
                 double2 *ph = reinterpret_cast<double2 *>(heavy + (int64_t)h * ld + c);
@@ -158,7 +159,7 @@ __device__ __forceinline__ void solve_tile(SolveTile<RP> &sm, SolveRun &acc, flo
                 make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
         const int64_t i = i0 + r;
         if (i < rows) {
-            float *dst = A + (int64_t)__ldg(fids0 + i) * ld + cb;
+            float *dst = A + (fids0 ? (int64_t)__ldg(fids0 + i) : i) * ld + cb;
 #pragma unroll
             for (int q = 0; q < 4; ++q)
                 if (cb + 4 * q < ld)

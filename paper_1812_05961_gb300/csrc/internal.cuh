@@ -127,6 +127,13 @@ struct sptt_csf {
     // Device error word of the kernels that read this CSF (bit 2: a bounded
     // wait for a staged copy ran out); read by sptt_csf_check.
     int32_t *err = nullptr;
+    // Hot rows of the MTTKRP for the mode at level l >= 1 (mttkrp_mode.cu):
+    // hslot[l][i] = shared-memory slot of row i or -1, hrow[l][s] = row of
+    // slot s; built for a row width whose slot capacity is hot_cap[l].
+    int32_t *hslot[SPTT_MAX_MODES] = {nullptr};
+    int32_t *hrow[SPTT_MAX_MODES] = {nullptr};
+    int32_t nhot[SPTT_MAX_MODES] = {0};
+    int32_t hot_cap[SPTT_MAX_MODES] = {0};
 };
 
 namespace sptt {
@@ -162,6 +169,14 @@ sptt_status mttkrp_launch(sptt_csf *csf, const void *const *factors, int32_t dty
 // Builds the work partition the launch will use (allocates on first use, so
 // call it before any stream capture).
 sptt_status mttkrp_prepare(sptt_csf *csf, const sptt_sched *sched, cudaStream_t st);
+
+// MTTKRP for the mode at level L >= 1 of the CSF (mttkrp_mode.cu): out is
+// full (dims[order[L]] x ld FP32), zeroed here, then filled. Call
+// mttkrp_mode_prepare first (partition and hot-row table; synchronises).
+sptt_status mttkrp_mode_prepare(sptt_csf *csf, int32_t L, int32_t ld, const sptt_sched *sched, cudaStream_t st);
+sptt_status mttkrp_mode_launch(sptt_csf *csf, int32_t L, const void *const *factors, int32_t dtype, int32_t ld,
+                               float *out, const sptt_sched *sched, cudaStream_t st);
+int csf_level_of(const sptt_csf *csf, int32_t mode);
 
 // ---------------------------------------------------------------------------
 // Dense kernels (dense.cu)

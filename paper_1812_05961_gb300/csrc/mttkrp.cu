@@ -28,24 +28,8 @@
 namespace sptt {
 namespace {
 
-// Lane-group layout of a warp: G = ld / VEC lanes per output row.
-struct Lanes {
-    int col;     // first column of this lane
-    int gi;      // lane group index within the warp
-    int gpw;     // lane groups per warp
-    bool idle;   // lanes past the last whole group
-};
-
-__device__ __forceinline__ Lanes lanes_for(int ld, int vec) {
-    Lanes L;
-    const int G = ld / vec;
-    const int lane = threadIdx.x & 31;
-    L.gpw = 32 / G;
-    L.gi = lane / G;
-    L.col = (lane - L.gi * G) * vec;
-    L.idle = L.gi >= L.gpw;
-    return L;
-}
+using walk::Lanes;
+using walk::lanes_for;
 
 // Each CTA takes a contiguous range of chunks; its lane groups interleave
 // within the range, so a group's consecutive chunks are close together and a
@@ -64,7 +48,7 @@ __device__ __forceinline__ ChunkRange cta_chunks(int64_t nchunks, const Lanes &L
     return r;
 }
 
-template <int NM, typename T, int B, int MINB, int W = 16>
+template <int NM, typename T, int B, int MINB, int W = 16, bool PIPE = true>
 __global__ void __launch_bounds__(256, MINB) mttkrp_flag_kernel(const walk::Args a) {
     const Lanes L = lanes_for(a.ld, walk::Raw<T, W>::VEC);
     if (L.idle) return;  // no warp collectives in the walk
@@ -72,7 +56,7 @@ __global__ void __launch_bounds__(256, MINB) mttkrp_flag_kernel(const walk::Args
     walk::Carry<walk::Raw<T, W>::VEC> cy;
     const walk::GlobalRecs rec{a.vals, a.fids[NM - 1], a.lvl};
     for (int64_t c = r.begin; c < r.end; c += r.step)
-        walk::flag_chunk<NM, T, B, walk::GlobalRecs, W>(a, c, L.col, cy, rec);
+        walk::flag_chunk<NM, T, B, walk::GlobalRecs, W, PIPE>(a, c, L.col, cy, rec);
     walk::flush_carry(a, L.col, cy);
 }
 
@@ -220,12 +204,12 @@ sptt_status launch_nm(const walk::Args &a, int block, int variant, cudaStream_t 
     void (*kern)(const walk::Args) = nullptr;
     switch (variant) {
         case 1: kern = mttkrp_root_kernel<NM, T>; break;
-        case 2: kern = mttkrp_flag_kernel<NM, T, 8, 2>; break;
-        case 3: kern = mttkrp_flag_kernel<NM, T, 4, 3>; break;
-        case 4: kern = mttkrp_flag_kernel<NM, T, 4, 4>; break;
-        case 5: kern = mttkrp_flag_kernel<NM, T, 8, 1>; break;
+        case 2: kern = mttkrp_flag_kernel<NM, T, 8, 1>; break;
+        case 3: kern = mttkrp_flag_kernel<NM, T, 4, 3, 16, false>; break;
+        case 4: kern = mttkrp_flag_kernel<NM, T, 4, 2>; break;
+        case 5: kern = mttkrp_flag_kernel<NM, T, 2, 3>; break;
         case 7: kern = mttkrp_flag_kernel<NM, T, 2, 2, 32>; break;
-        default: kern = mttkrp_flag_kernel<NM, T, 4, 3>; break;
+        default: kern = mttkrp_flag_kernel<NM, T, 4, 3, 16, false>; break;
     }
     int per_sm = 0;
     SPTT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, 0));
@@ -268,6 +252,15 @@ constexpr int32_t kDefaultChunk = 128;
 
 static bool staged_variant(int v) { return v == 6 || v == 8; }
 
+// The fastest variant measured per gather type and row width on the 3-mode
+// power-law workload (R = 16 and 32): FP32 rows of up to 64 bytes take the
+// non-pipelined walk at 3 CTAs per SM, wider FP32 rows the 32-byte-segment
+// walk; BF16 rows take the pipelined walk at 2 CTAs per SM.
+int default_variant(int32_t dtype, int32_t ld) {
+    if (dtype == SPTT_BF16) return 4;
+    return ld <= 16 ? 3 : 7;
+}
+
 sptt_status mttkrp_prepare(sptt_csf *csf, const sptt_sched *sched, cudaStream_t st) {
     const int32_t chunk = (sched && staged_variant(sched->variant)) ? kStageChunk
                           : ((sched && sched->chunk) ? sched->chunk : kDefaultChunk);
@@ -282,7 +275,7 @@ sptt_status mttkrp_launch(sptt_csf *csf, const void *const *factors, int32_t dty
     const int64_t nnz = csf->nfibs[N - 1];
     if (nnz == 0) return SPTT_OK;
     int variant = sched ? sched->variant : 0;
-    if (variant == 0) variant = (dtype == SPTT_BF16) ? 2 : 3;  // fastest measured per gather type
+    if (variant == 0) variant = default_variant(dtype, ld);
     if (variant == 7 || variant == 8) {
         // 32-byte row segments need ld * sizeof(T) and every gathered factor
         // 32-byte aligned; otherwise the 16-byte form of the same walk runs

@@ -20,17 +20,18 @@ constexpr int kThreads = 256;
 
 // ---------------------------------------------------------------------------
 // Candidate schedules: order (ascending / descending length below the root)
-// x walk variant (3: batch 4, 3 CTAs/SM; 2: batch 8, 2 CTAs/SM) x chunk.
+// x walk variant (3: batch 4, 3 CTAs/SM; 4: batch 4, 2 CTAs/SM, pipelined;
+// 5: batch 2, 3 CTAs/SM, pipelined; 7: 32-byte row segments) x chunk.
 // ---------------------------------------------------------------------------
 constexpr int kNumCands = 16;
-const int kCandChunks[4] = {64, 128, 256, 512};
-const int kCandVariants[2] = {3, 2};
+const int kCandChunks[2] = {64, 128};
+const int kCandVariants[4] = {3, 4, 5, 7};
 
 sptt_sched candidate(int i) {
     sptt_sched s{};
     s.order = i / 8;
-    s.variant = kCandVariants[(i / 4) % 2];
-    s.chunk = kCandChunks[i % 4];
+    s.variant = kCandVariants[(i / 2) % 4];
+    s.chunk = kCandChunks[i % 2];
     s.block = 256;
     return s;
 }

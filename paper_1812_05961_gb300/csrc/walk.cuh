@@ -33,6 +33,25 @@
 namespace sptt {
 namespace walk {
 
+// Lane-group layout of a warp: G = ld / VEC lanes per output row.
+struct Lanes {
+    int col;     // first column of this lane
+    int gi;      // lane group index within the warp
+    int gpw;     // lane groups per warp
+    bool idle;   // lanes past the last whole group
+};
+
+__device__ __forceinline__ Lanes lanes_for(int ld, int vec) {
+    Lanes L;
+    const int G = ld / vec;
+    const int lane = threadIdx.x & 31;
+    L.gpw = 32 / G;
+    L.gi = lane / G;
+    L.col = (lane - L.gi * G) * vec;
+    L.idle = L.gi >= L.gpw;
+    return L;
+}
+
 struct Args {
     const int32_t *fptr[kMaxModes];  // levels 0..N-2 (used by the plain walk only)
     const int32_t *fids[kMaxModes];  // levels 0..N-1
@@ -275,6 +294,36 @@ struct SharedRecs {  // shared-memory addresses of the chunk's copy; k0 = the ch
     }
 };
 
+// The records of the B leaves from kb on: values, leaf indices and the
+// packed level flags (byte j of lw[j / 4] = leaf kb + j).
+template <int B, typename Recs>
+__device__ __forceinline__ void fetch_batch(const Recs &rec, int64_t kb, float (&v)[B], int32_t (&li)[B],
+                                            uint32_t (&lw)[2]) {
+    if constexpr (B == 2) {
+        const float2 va = rec.v2(kb);
+        const int2 ia = rec.i2(kb);
+        v[0] = va.x; v[1 % B] = va.y;
+        li[0] = ia.x; li[1 % B] = ia.y;
+        lw[0] = rec.l2(kb);
+    } else {
+        const float4 va = rec.v4(kb);
+        const int4 ia = rec.i4(kb);
+        v[0] = va.x; v[1 % B] = va.y; v[2 % B] = va.z; v[3 % B] = va.w;
+        li[0] = ia.x; li[1 % B] = ia.y; li[2 % B] = ia.z; li[3 % B] = ia.w;
+        if constexpr (B == 8) {
+            const float4 vb = rec.v4(kb + 4);
+            const int4 ib = rec.i4(kb + 4);
+            v[4 % B] = vb.x; v[5 % B] = vb.y; v[6 % B] = vb.z; v[7 % B] = vb.w;
+            li[4 % B] = ib.x; li[5 % B] = ib.y; li[6 % B] = ib.z; li[7 % B] = ib.w;
+            const uint2 l2 = rec.l8(kb);
+            lw[0] = l2.x;
+            lw[1] = l2.y;
+        } else {
+            lw[0] = rec.l4(kb);
+        }
+    }
+}
+
 // The batched walk driven by the per-leaf level flags. A lane group takes
 // its chunk in batches of B leaves: the batch's values, leaf indices and
 // level flags arrive in vector loads; then every factor row the batch needs
@@ -282,7 +331,7 @@ struct SharedRecs {  // shared-memory addresses of the chunk's copy; k0 = the ch
 // the batch, whose ids are consecutive) is requested before any is used.
 // Rows of fibers at higher levels are requested when the fiber opens and
 // used when it closes.
-template <int NM, typename T, int B, typename Recs = GlobalRecs, int W = 16>
+template <int NM, typename T, int B, typename Recs = GlobalRecs, int W = 16, bool PIPE = true>
 __device__ __forceinline__ void flag_chunk(const Args &a, int64_t c, int col, Carry<Raw<T, W>::VEC> &cy,
                                            const Recs &rec) {
     using Rw = Raw<T, W>;
@@ -308,43 +357,36 @@ __device__ __forceinline__ void flag_chunk(const Args &a, int64_t c, int col, Ca
     bool first_slice = true;
     take_carry<VEC>(a, col, cy, f[0], acc[0]);
 
-    for (int64_t kb = k0; kb < k1; kb += B) {
-        float v[B];
-        int32_t li[B];
-        uint32_t lw[2] = {0u, 0u};
-        if constexpr (B == 2) {
-            const float2 va = rec.v2(kb);
-            const int2 ia = rec.i2(kb);
-            v[0] = va.x; v[1 % B] = va.y;
-            li[0] = ia.x; li[1 % B] = ia.y;
-            lw[0] = rec.l2(kb);
-        } else {
-            const float4 va = rec.v4(kb);
-            const int4 ia = rec.i4(kb);
-            v[0] = va.x; v[1 % B] = va.y; v[2 % B] = va.z; v[3 % B] = va.w;
-            li[0] = ia.x; li[1 % B] = ia.y; li[2 % B] = ia.z; li[3 % B] = ia.w;
-            if constexpr (B == 8) {
-                const float4 vb = rec.v4(kb + 4);
-                const int4 ib = rec.i4(kb + 4);
-                v[4 % B] = vb.x; v[5 % B] = vb.y; v[6 % B] = vb.z; v[7 % B] = vb.w;
-                li[4 % B] = ib.x; li[5 % B] = ib.y; li[6 % B] = ib.z; li[7 % B] = ib.w;
-                const uint2 l2 = rec.l8(kb);
-                lw[0] = l2.x;
-                lw[1] = l2.y;
-            } else {
-                lw[0] = rec.l4(kb);
-            }
-        }
-        // ids of the next B level-LF fibers, requested with the records: the
-        // fibers that open in this batch are among them (consecutive ids), so
-        // their rows need not wait for the flags and then for the ids. The
-        // level arrays carry 64 elements of slack past their end; an id is
-        // used only for a fiber that really opens.
-        int32_t nf[B];
+    // Each batch requests, with its records, the ids of the next B level-LF
+    // fibers: the fibers a batch opens have consecutive ids, so their rows
+    // need not wait for the flags and then for the ids. With PIPE the walk
+    // is also software-pipelined: while a batch's factor rows are in flight,
+    // the next batch's records and next fiber ids (after the ones this batch
+    // opens, which its flags count) are requested, so a batch's row requests
+    // wait for no load of their own batch; it costs about 3B + 2 registers.
+    // The level arrays carry 64 elements of slack past their end and the
+    // leaf arrays more; a prefetched id is used only for a fiber that really
+    // opens.
+    float v[B];
+    int32_t li[B];
+    uint32_t lw[2] = {0u, 0u};
+    int32_t nf[B];
+    if constexpr (PIPE) {
+        fetch_batch<B>(rec, k0, v, li, lw);
         if constexpr (LF >= 1) {
             const int32_t *fp = a.fids[LF] + f[LF] + 1;
 #pragma unroll
             for (int q = 0; q < B; ++q) nf[q] = __ldg(fp + q);
+        }
+    }
+    for (int64_t kb = k0; kb < k1; kb += B) {
+        if constexpr (!PIPE) {
+            fetch_batch<B>(rec, kb, v, li, lw);
+            if constexpr (LF >= 1) {
+                const int32_t *fp = a.fids[LF] + f[LF] + 1;
+#pragma unroll
+                for (int q = 0; q < B; ++q) nf[q] = __ldg(fp + q);
+            }
         }
         const int nvalid = (k1 - kb < B) ? (int)(k1 - kb) : B;
         Row x[B];
@@ -373,6 +415,19 @@ __device__ __forceinline__ void flag_chunk(const Args &a, int64_t c, int col, Ca
                     for (int q = 1; q <= j; ++q) id = (pos == q) ? nf[q] : id;
                     nr[j] = Rw::load(a.fac[LF], id, ld, col);
                 }
+        }
+        const bool more = PIPE && kb + B < k1;
+        float vn[B];
+        int32_t lin[B];
+        uint32_t lwn[2] = {0u, 0u};
+        int32_t nfn[B];
+        if (more) {
+            fetch_batch<B>(rec, kb + B, vn, lin, lwn);
+            if constexpr (LF >= 1) {
+                const int32_t *fp = a.fids[LF] + f[LF] + __popc(sm) + 1;
+#pragma unroll
+                for (int q = 0; q < B; ++q) nfn[q] = __ldg(fp + q);
+            }
         }
 #pragma unroll
         for (int j = 0; j < B; ++j) {
@@ -404,6 +459,16 @@ __device__ __forceinline__ void flag_chunk(const Args &a, int64_t c, int col, Ca
             float xr[VEC];
             Rw::widen(x[j], xr);
             fma_scalar<VEC, W == 32>(acc[LF], v[j], xr);
+        }
+        if (more) {
+#pragma unroll
+            for (int q = 0; q < B; ++q) {
+                v[q] = vn[q];
+                li[q] = lin[q];
+                if constexpr (LF >= 1) nf[q] = nfn[q];
+            }
+            lw[0] = lwn[0];
+            lw[1] = lwn[1];
         }
     }
     // chunk end: fold the open fibers; the open slice's partial is added

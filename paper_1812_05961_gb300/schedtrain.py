@@ -25,6 +25,7 @@ class Sample:
     features: List[float]
     times_ms: List[float]
     label: str = ""
+    rank: int = 16
 
 
 @dataclass
@@ -47,7 +48,7 @@ def sweep_tensor(dims, inds, vals, rank: int, dtype: int = SPTT_F32, reps: int =
         feats = sptt_csf_features(csf.handle, rank)
         csf.close()
         ms = sptt_autotune(dims, inds, vals, root, rank, dtype, reps)
-        out.append(Sample(feats, ms, "%s root %d R %d" % (label, root, rank)))
+        out.append(Sample(feats, ms, "%s root %d R %d" % (label, root, rank), rank))
     return out
 
 
@@ -59,22 +60,28 @@ def train(ds: Dataset, steps: int = 2000, lr: float = 3e-3, seed: int = 0, devic
     return m, hist
 
 
-def default_index() -> int:
+def default_index(rank: int = 16, dtype: int = SPTT_F32) -> int:
     """Index of the library's default schedule among the candidates
-    (ascending order, variant 3, chunk 128)."""
+    (ascending order, chunk 128, the default variant for the gather type
+    and rank)."""
+    ld = (rank + 7) // 8 * 8
+    variant = 4 if dtype != SPTT_F32 else (3 if ld <= 16 else 7)
     for i, c in enumerate(sptt_sched_candidates()):
-        if c[0] == 128 and c[2] == 3 and c[3] == 0:
+        if c[0] == 128 and c[2] == variant and c[3] == 0:
             return i
     return 0
 
 
 def regret(ds: Dataset, model=None, fixed: int = None):
     """Per-sample time of the chosen schedule over the best one, minus 1:
-    choices from the model, or the fixed candidate index."""
+    choices from the model, or the fixed candidate index (None: the
+    library's default for each sample's rank)."""
     if model is not None:
         choice, _ = sptt_mlp_predict(model.handle, [s.features for s in ds.samples])
-    else:
+    elif fixed is not None:
         choice = [fixed] * len(ds.samples)
+    else:
+        choice = [default_index(s.rank) for s in ds.samples]
     return [s.times_ms[k] / min(s.times_ms) - 1.0 for s, k in zip(ds.samples, choice)]
 
 

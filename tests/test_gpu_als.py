@@ -203,3 +203,47 @@ def test_graph_replay_matches_stream_launches(cuda_device):
     np.testing.assert_allclose(fc, fa, atol=1e-9)
     np.testing.assert_allclose(b.fit_history(), fa, atol=1e-9)
     assert l1 - l0 >= 5 * (4 * 6 + 1)  # every replayed kernel is counted
+
+
+@pytest.mark.parametrize("csf_mode", [1, 2])
+@pytest.mark.parametrize("dims,nnz,R,iters", [
+    ((200, 150, 100), 20000, 8, 6),
+    ((60, 50, 40, 30), 30000, 12, 5),
+    ((20, 18, 16, 14, 12), 20000, 8, 4),
+    ((400, 300), 20000, 10, 5),
+])
+def test_one_csf_for_all_modes_matches_oracle(csf_mode, dims, nnz, R, iters, cuda_device):
+    # the non-root modes' MTTKRPs from the one CSF (sptt_mttkrp_mode's kernels)
+    t = make(dims, nnz, seed=nnz % 97 + R, dist="zipf", s=1.2)
+    inds_np, vals_np = t.numpy()
+    di, dv = to_dev(t, cuda_device)
+    one = sptt.Cpd(dims, di, dv, R, seed=5, csf_mode=csf_mode).init()
+    one.iterate(iters)
+    per_mode = sptt.Cpd(dims, di, dv, R, seed=5).init()
+    per_mode.iterate(iters)
+    ref = oracle.cpd_als(inds_np, vals_np, dims, R, iters, seed=5)
+    np.testing.assert_allclose(one.fit_history(), ref["fits"], atol=1e-4, rtol=0)
+    np.testing.assert_allclose(one.fit_history(), per_mode.fit_history(), atol=1e-5, rtol=0)
+
+
+def test_one_csf_graph_and_bf16(cuda_device):
+    dims = (150, 120, 90, 40)
+    t = make(dims, 30000, seed=21, dist="zipf", s=1.3)
+    di, dv = to_dev(t, cuda_device)
+    a = sptt.Cpd(dims, di, dv, 16, seed=3, csf_mode=1).init()
+    a.iterate(4)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        g = sptt.Cpd(dims, di, dv, 16, seed=3, csf_mode=1, use_graph=1).init()
+        g.iterate(4)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(g.fit_history(), a.fit_history(), atol=1e-6)
+    b = sptt.Cpd(dims, di, dv, 16, seed=3, csf_mode=1, precision=sptt.SPTT_BF16).init()
+    b.iterate(4)
+    b.refine(1)
+    c = sptt.Cpd(dims, di, dv, 16, seed=3, precision=sptt.SPTT_BF16).init()
+    c.iterate(4)
+    c.refine(1)
+    assert abs(b.fit()[0] - c.fit()[0]) <= 1e-4
+    with pytest.raises(sptt.SpttError):
+        sptt.Cpd(dims, di, dv, 16, seed=3, csf_mode=1, plan=1)

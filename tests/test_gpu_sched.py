@@ -113,6 +113,6 @@ def test_learned_scheduler_beats_fixed_default_on_held_out(cuda_device):
     model, hist = schedtrain.train(train, steps=1500, lr=3e-3)
     assert float(hist[-1]) < float(hist[0])
     r_model = schedtrain.summarize(schedtrain.regret(held, model))
-    r_default = schedtrain.summarize(schedtrain.regret(held, fixed=schedtrain.default_index()))
+    r_default = schedtrain.summarize(schedtrain.regret(held))  # the library default per rank
     print("held-out regret: learned %s, default %s" % (r_model, r_default))
     assert r_model["mean"] <= r_default["mean"] + 0.02
