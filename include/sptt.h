@@ -147,7 +147,10 @@ sptt_status sptt_csf_copy_level(const sptt_csf *csf, int32_t level, int32_t *fpt
  *               staged walk with 32-byte row segments (one 256-bit gather per
  *               lane, half the lanes per row) and batches of 2 leaves; 7 and
  *               8 need ld * element size and every non-root factor 32-byte
- *               aligned, and otherwise run as variant 3 / 6
+ *               aligned, and otherwise run as variant 3 / 6. Variant 7 (and
+ *               the default, for F32 gathers) reads packed 16-byte leaf
+ *               records that the first call builds (16 bytes per non-zero
+ *               on the device, kept with the CSF)
  */
 typedef struct {
     int32_t chunk;
@@ -352,6 +355,27 @@ sptt_status sptt_cpd_factor(sptt_cpd *cpd, int32_t mode, float *dst);
 /* Copy the FP64 Gram of factor `mode` (rank x rank) into dst (host or
  * device). Synchronises. */
 sptt_status sptt_cpd_gram(sptt_cpd *cpd, int32_t mode, double *dst);
+
+/*
+ * Checkpoint / resume of a CP-ALS run (no counterpart in the paper; a
+ * long run can be stopped and continued). The state is what the next
+ * iteration reads: the normalised factors, their FP64 Grams, lambda, the
+ * iteration count and the last (up to 4096) fits. sptt_cpd_save writes it
+ * into buf (host, caller-owned): with buf = NULL or cap too small it only
+ * sets *needed (bytes) and returns SPTT_ERR_BAD_ARG for a non-NULL buf that
+ * is too small, SPTT_OK for buf = NULL. The format: a header (magic
+ * "SPTTCKP1", version, shape, rank, iteration count, number of fits, FNV-1a
+ * 64 checksum of the payload) followed by the factors (dims[m] x rank
+ * float, row-major), the Grams (rank x rank double), lambda (rank double)
+ * and the fits (double), host byte order. sptt_cpd_load restores a buffer
+ * into a handle created for a tensor of the same shape and the same rank
+ * (precision, schedules and CSF layout may differ): it checks the magic,
+ * version, shape, rank, length and checksum (SPTT_ERR_BAD_ARG if any
+ * differs); the BF16 copies are regenerated. Both synchronise. The CSFs,
+ * which depend only on the tensor, are not part of the state.
+ */
+sptt_status sptt_cpd_save(sptt_cpd *cpd, void *buf, size_t cap, size_t *needed);
+sptt_status sptt_cpd_load(sptt_cpd *cpd, const void *buf, size_t len);
 
 /*
  * Solve branches taken since sptt_cpd_init: *n_pinv = mode updates that used

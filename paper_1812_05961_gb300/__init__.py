@@ -93,6 +93,8 @@ def lib() -> ctypes.CDLL:
             "sptt_csf_check": (_ST, [_P, _P]),
             "sptt_mttkrp": (_ST, [_P, _P, _I32, _I32, _P, _P, _P]),
             "sptt_mttkrp_mode": (_ST, [_P, _I32, _P, _I32, _I32, _P, _P, _P]),
+            "sptt_cpd_save": (_ST, [_P, _P, ctypes.c_size_t, _P]),
+            "sptt_cpd_load": (_ST, [_P, _P, ctypes.c_size_t]),
             "sptt_gram": (_ST, [_P, _I64, _I32, _I32, _P, _P]),
             "sptt_gram_noalloc": (_ST, [_P, _I64, _I32, _I32, _P, _P]),
             "sptt_cpd_create": (_ST, [ctypes.POINTER(sptt_coo), _I32, ctypes.POINTER(sptt_opts), _P,
@@ -408,6 +410,20 @@ def sptt_cpd_als(dims, inds, vals, rank: int, max_iters: int, tol: float = 0.0,
     return fit.value, it.value
 
 
+def sptt_cpd_save(cpd: int) -> bytes:
+    """The run's state as a checkpoint (see include/sptt.h)."""
+    need = ctypes.c_size_t()
+    _check(lib().sptt_cpd_save(cpd, None, 0, ctypes.byref(need)), "sptt_cpd_save")
+    buf = ctypes.create_string_buffer(need.value)
+    _check(lib().sptt_cpd_save(cpd, buf, need.value, ctypes.byref(need)), "sptt_cpd_save")
+    return buf.raw
+
+
+def sptt_cpd_load(cpd: int, data: bytes):
+    buf = ctypes.create_string_buffer(bytes(data), len(data))
+    _check(lib().sptt_cpd_load(cpd, buf, len(data)), "sptt_cpd_load")
+
+
 def sptt_debug_fail_alloc_after(countdown: int):
     lib().sptt_debug_fail_alloc_after(countdown)
 
@@ -686,6 +702,13 @@ class Cpd:
 
     def lam(self):
         return sptt_cpd_lambda(self.handle, self.rank)
+
+    def save(self) -> bytes:
+        return sptt_cpd_save(self.handle)
+
+    def load(self, data: bytes):
+        sptt_cpd_load(self.handle, data)
+        return self
 
     def factor(self, mode: int, device="cpu"):
         return sptt_cpd_factor(self.handle, mode, self.dims[mode], self.rank, device)

@@ -592,3 +592,135 @@ extern "C" sptt_status sptt_cpd_als(const sptt_coo *coo, int32_t rank, int32_t m
     if (iters_out) *iters_out = it;
     return SPTT_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Checkpoint / resume
+// ---------------------------------------------------------------------------
+namespace {
+
+struct CkpHeader {
+    char magic[8];
+    uint32_t version;
+    int32_t nmodes;
+    int32_t rank;
+    int32_t pad_;
+    int64_t dims[SPTT_MAX_MODES];
+    int64_t iters;
+    int64_t nfits;
+    uint64_t checksum;  // FNV-1a 64 of the payload
+};
+
+constexpr char kCkpMagic[8] = {'S', 'P', 'T', 'T', 'C', 'K', 'P', '1'};
+constexpr uint32_t kCkpVersion = 1;
+
+uint64_t fnv1a(const unsigned char *p, size_t n) {
+    uint64_t h = 1469598103934665603ull;
+    for (size_t i = 0; i < n; ++i) {
+        h ^= p[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+size_t ckp_payload(const sptt_cpd *c, int64_t nfits) {
+    size_t b = 0;
+    for (int m = 0; m < c->N; ++m) b += (size_t)c->dims[m] * c->rank * sizeof(float);
+    b += (size_t)c->N * c->rank * c->rank * sizeof(double);
+    b += (size_t)c->rank * sizeof(double);
+    b += (size_t)nfits * sizeof(double);
+    return b;
+}
+
+}  // namespace
+
+extern "C" sptt_status sptt_cpd_save(sptt_cpd *c, void *buf, size_t cap, size_t *needed) {
+    clear_error();
+    if (!c) return set_error(SPTT_ERR_BAD_ARG, "cpd is NULL");
+    const int64_t nfits = c->iters < kFitHistory ? c->iters : kFitHistory;
+    const size_t total = sizeof(CkpHeader) + ckp_payload(c, nfits);
+    if (needed) *needed = total;
+    if (!buf) return SPTT_OK;
+    if (cap < total) return set_error(SPTT_ERR_BAD_ARG, "checkpoint buffer too small");
+    unsigned char *out = static_cast<unsigned char *>(buf);
+    unsigned char *p = out + sizeof(CkpHeader);
+    for (int m = 0; m < c->N; ++m) {
+        SPTT_CUDA(cudaMemcpy2DAsync(p, c->rank * sizeof(float), c->A[m], c->ld * sizeof(float),
+                                    c->rank * sizeof(float), c->dims[m], cudaMemcpyDeviceToHost, c->st));
+        p += (size_t)c->dims[m] * c->rank * sizeof(float);
+    }
+    for (int m = 0; m < c->N; ++m) {
+        SPTT_CUDA(cudaMemcpyAsync(p, c->G[m], (size_t)c->rank * c->rank * sizeof(double), cudaMemcpyDeviceToHost,
+                                  c->st));
+        p += (size_t)c->rank * c->rank * sizeof(double);
+    }
+    SPTT_CUDA(cudaMemcpyAsync(p, c->w.lambda, c->rank * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    p += (size_t)c->rank * sizeof(double);
+    std::vector<double> ring(kFitHistory);
+    SPTT_CUDA(cudaMemcpyAsync(ring.data(), c->fits, kFitHistory * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    SPTT_CUDA(cudaStreamSynchronize(c->st));
+    for (int64_t j = 0; j < nfits; ++j) {
+        const double f = ring[(c->iters - nfits + j) % kFitHistory];
+        memcpy(p, &f, sizeof(double));
+        p += sizeof(double);
+    }
+    CkpHeader h{};
+    memcpy(h.magic, kCkpMagic, 8);
+    h.version = kCkpVersion;
+    h.nmodes = c->N;
+    h.rank = c->rank;
+    for (int m = 0; m < c->N; ++m) h.dims[m] = c->dims[m];
+    h.iters = c->iters;
+    h.nfits = nfits;
+    h.checksum = fnv1a(out + sizeof(CkpHeader), total - sizeof(CkpHeader));
+    memcpy(out, &h, sizeof(h));
+    return SPTT_OK;
+}
+
+extern "C" sptt_status sptt_cpd_load(sptt_cpd *c, const void *buf, size_t len) {
+    clear_error();
+    if (!c || !buf) return set_error(SPTT_ERR_BAD_ARG, "cpd and buf must be non-NULL");
+    if (len < sizeof(CkpHeader)) return set_error(SPTT_ERR_BAD_ARG, "checkpoint shorter than its header");
+    CkpHeader h;
+    memcpy(&h, buf, sizeof(h));
+    if (memcmp(h.magic, kCkpMagic, 8) != 0) return set_error(SPTT_ERR_BAD_ARG, "not a checkpoint (magic)");
+    if (h.version != kCkpVersion) return set_error(SPTT_ERR_BAD_ARG, "unsupported checkpoint version");
+    if (h.nmodes != c->N || h.rank != c->rank) return set_error(SPTT_ERR_BAD_ARG, "checkpoint of another shape or rank");
+    for (int m = 0; m < c->N; ++m)
+        if (h.dims[m] != c->dims[m]) return set_error(SPTT_ERR_BAD_ARG, "checkpoint of another shape");
+    if (h.iters < 0 || h.nfits < 0 || h.nfits > kFitHistory || h.nfits > h.iters)
+        return set_error(SPTT_ERR_BAD_ARG, "corrupt checkpoint header");
+    const size_t total = sizeof(CkpHeader) + ckp_payload(c, h.nfits);
+    if (len != total) return set_error(SPTT_ERR_BAD_ARG, "checkpoint length does not match its header");
+    const unsigned char *in = static_cast<const unsigned char *>(buf);
+    if (fnv1a(in + sizeof(CkpHeader), total - sizeof(CkpHeader)) != h.checksum)
+        return set_error(SPTT_ERR_BAD_ARG, "checkpoint checksum mismatch");
+    // drop any captured iteration: the state it was captured against is replaced
+    for (int p = 0; p < 2; ++p)
+        if (c->graph[p]) {
+            cudaGraphExecDestroy(c->graph[p]);
+            c->graph[p] = nullptr;
+        }
+    const unsigned char *p = in + sizeof(CkpHeader);
+    for (int m = 0; m < c->N; ++m) {
+        SPTT_TRY(fill_zero_launch(c->A[m], (size_t)c->dims[m] * c->ld * sizeof(float), c->st));
+        SPTT_CUDA(cudaMemcpy2DAsync(c->A[m], c->ld * sizeof(float), p, c->rank * sizeof(float),
+                                    c->rank * sizeof(float), c->dims[m], cudaMemcpyHostToDevice, c->st));
+        if (c->Ab[m]) SPTT_TRY(to_bf16_launch(c->A[m], c->Ab[m], c->dims[m] * c->ld, c->st));
+        p += (size_t)c->dims[m] * c->rank * sizeof(float);
+    }
+    for (int m = 0; m < c->N; ++m) {
+        SPTT_CUDA(cudaMemcpyAsync(c->G[m], p, (size_t)c->rank * c->rank * sizeof(double), cudaMemcpyHostToDevice,
+                                  c->st));
+        p += (size_t)c->rank * c->rank * sizeof(double);
+    }
+    SPTT_CUDA(cudaMemcpyAsync(c->w.lambda, p, c->rank * sizeof(double), cudaMemcpyHostToDevice, c->st));
+    p += (size_t)c->rank * sizeof(double);
+    std::vector<double> ring(kFitHistory, 0.0);
+    for (int64_t j = 0; j < h.nfits; ++j) memcpy(&ring[(h.iters - h.nfits + j) % kFitHistory], p + j * 8, 8);
+    SPTT_CUDA(cudaMemcpyAsync(c->fits, ring.data(), kFitHistory * sizeof(double), cudaMemcpyHostToDevice, c->st));
+    const int64_t it = h.iters;
+    SPTT_CUDA(cudaMemcpyAsync(c->iter_dev, &it, sizeof(int64_t), cudaMemcpyHostToDevice, c->st));
+    SPTT_CUDA(cudaStreamSynchronize(c->st));
+    c->iters = h.iters;
+    return SPTT_OK;
+}

@@ -474,7 +474,8 @@ extern "C" sptt_status sptt_batch_create(const sptt_coo *coos, int32_t count, in
                 sptt_csf *cs = nullptr;
                 SPTT_TRY(csf_build_device(&dc.coo, m, nullptr, b->st, &cs));
                 b->csfs[(size_t)t * b->max_modes + m] = cs;
-                SPTT_TRY(mttkrp_prepare(cs, sched, b->st));
+                // the batched walk reads the separate leaf arrays: partition only
+                SPTT_TRY(csf_ensure_partition(cs, (sched && sched->chunk) ? sched->chunk : 128, b->st));
             }
         }
         int64_t max_slices = 0, max_heavy = 0;

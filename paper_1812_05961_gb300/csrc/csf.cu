@@ -274,6 +274,7 @@ void csf_destroy(sptt_csf *c) {
     if (c->lvl) cudaFree(c->lvl);
     if (c->part) cudaFree(c->part);
     if (c->hidx) cudaFree(c->hidx);
+    if (c->leafrec) cudaFree(c->leafrec);
     if (c->err) cudaFree(c->err);
     delete c;
 }
@@ -314,6 +315,43 @@ sptt_status csf_ensure_partition(sptt_csf *c, int32_t chunk, cudaStream_t st) {
     SPTT_CUDA(cudaMemcpyAsync(&nh, scan.as<int32_t>() + ns, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     SPTT_CUDA(cudaStreamSynchronize(st));
     c->nheavy = nh;
+    return SPTT_OK;
+}
+
+namespace {
+
+__global__ void leafrec_kernel(const int32_t *__restrict__ idx, const float *__restrict__ vals,
+                               const uint8_t *__restrict__ lvl, int64_t nnz, uint4 *__restrict__ rec) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nnz; k += (int64_t)gridDim.x * blockDim.x)
+        rec[k] = make_uint4((uint32_t)idx[k], __float_as_uint(vals[k]), 0u, (uint32_t)lvl[k]);
+}
+
+// The leaf that starts level-LF fiber f carries that fiber's index.
+__global__ void leafrec_fiber_kernel(const int32_t *__restrict__ fptr, const int32_t *__restrict__ fids, int64_t nf,
+                                     uint4 *__restrict__ rec) {
+    for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < nf; f += (int64_t)gridDim.x * blockDim.x)
+        rec[fptr[f]].z = (uint32_t)fids[f];
+}
+
+}  // namespace
+
+sptt_status csf_ensure_leafrec(sptt_csf *c, cudaStream_t st) {
+    if (c->leafrec) return SPTT_OK;
+    const int N = c->nmodes;
+    const int64_t nnz = c->nfibs[N - 1];
+    SPTT_CUDA(cudaMalloc(&c->leafrec, (size_t)(nnz + kLeafSlack) * sizeof(uint4)));
+    SPTT_TRY(fill_zero_launch(c->leafrec + nnz, (size_t)kLeafSlack * sizeof(uint4), st));
+    if (nnz > 0) {
+        leafrec_kernel<<<grid_for(nnz), kThreads, 0, st>>>(c->fids[N - 1], c->vals, c->lvl, nnz, c->leafrec);
+        SPTT_CHECK_LAUNCH("leafrec_kernel");
+        if (N >= 3) {
+            // level N-2 fibers: fptr[N-2][f] is the first leaf of fiber f
+            const int LF = N - 2;
+            leafrec_fiber_kernel<<<grid_for(c->nfibs[LF]), kThreads, 0, st>>>(c->fptr[LF], c->fids[LF], c->nfibs[LF],
+                                                                              c->leafrec);
+            SPTT_CHECK_LAUNCH("leafrec_fiber_kernel");
+        }
+    }
     return SPTT_OK;
 }
 

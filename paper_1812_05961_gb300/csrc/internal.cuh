@@ -130,6 +130,11 @@ struct sptt_csf {
     // Hot rows of the MTTKRP for the mode at level l >= 1 (mttkrp_mode.cu):
     // hslot[l][i] = shared-memory slot of row i or -1, hrow[l][s] = row of
     // slot s; built for a row width whose slot capacity is hot_cap[l].
+    // Packed leaf records of the flag walk (walk.cuh PackedRecs): per leaf
+    // {leaf index, value bits, index of the level-(N-2) fiber it opens or 0,
+    // level flag}, with kLeafSlack zero records after the last; built on
+    // first use.
+    uint4 *leafrec = nullptr;
     int32_t *hslot[SPTT_MAX_MODES] = {nullptr};
     int32_t *hrow[SPTT_MAX_MODES] = {nullptr};
     int32_t nhot[SPTT_MAX_MODES] = {0};
@@ -144,6 +149,7 @@ sptt_status csf_build_device(const sptt_coo *coo_dev, int32_t root, const int32_
 // ascending (kind 0) or descending (kind 1) length, ties to the lower mode id.
 void level_order(const int64_t *dims, int nmodes, int root, int kind, int32_t *order);
 sptt_status csf_ensure_partition(sptt_csf *csf, int32_t chunk, cudaStream_t st);
+sptt_status csf_ensure_leafrec(sptt_csf *csf, cudaStream_t st);
 void csf_destroy(sptt_csf *c);
 
 // Copy a host COO to the device (arrays owned by the returned holder).

@@ -48,15 +48,21 @@ __device__ __forceinline__ ChunkRange cta_chunks(int64_t nchunks, const Lanes &L
     return r;
 }
 
-template <int NM, typename T, int B, int MINB, int W = 16, bool PIPE = true>
+template <int NM, typename T, int B, int MINB, int W = 16, bool PIPE = true, bool PACKED = false>
 __global__ void __launch_bounds__(256, MINB) mttkrp_flag_kernel(const walk::Args a) {
     const Lanes L = lanes_for(a.ld, walk::Raw<T, W>::VEC);
     if (L.idle) return;  // no warp collectives in the walk
     const ChunkRange r = cta_chunks(a.nchunks, L);
     walk::Carry<walk::Raw<T, W>::VEC> cy;
-    const walk::GlobalRecs rec{a.vals, a.fids[NM - 1], a.lvl};
-    for (int64_t c = r.begin; c < r.end; c += r.step)
-        walk::flag_chunk<NM, T, B, walk::GlobalRecs, W, PIPE>(a, c, L.col, cy, rec);
+    if constexpr (PACKED) {
+        const walk::PackedRecs rec{a.leafrec};
+        for (int64_t c = r.begin; c < r.end; c += r.step)
+            walk::flag_chunk<NM, T, B, walk::PackedRecs, W, PIPE>(a, c, L.col, cy, rec);
+    } else {
+        const walk::GlobalRecs rec{a.vals, a.fids[NM - 1], a.lvl};
+        for (int64_t c = r.begin; c < r.end; c += r.step)
+            walk::flag_chunk<NM, T, B, walk::GlobalRecs, W, PIPE>(a, c, L.col, cy, rec);
+    }
     walk::flush_carry(a, L.col, cy);
 }
 
@@ -208,7 +214,7 @@ sptt_status launch_nm(const walk::Args &a, int block, int variant, cudaStream_t 
         case 3: kern = mttkrp_flag_kernel<NM, T, 4, 3, 16, false>; break;
         case 4: kern = mttkrp_flag_kernel<NM, T, 4, 2>; break;
         case 5: kern = mttkrp_flag_kernel<NM, T, 2, 3>; break;
-        case 7: kern = mttkrp_flag_kernel<NM, T, 2, 2, 32>; break;
+        case 7: kern = mttkrp_flag_kernel<NM, T, 2, 2, 32, true, true>; break;
         default: kern = mttkrp_flag_kernel<NM, T, 4, 3, 16, false>; break;
     }
     int per_sm = 0;
@@ -253,18 +259,24 @@ constexpr int32_t kDefaultChunk = 128;
 static bool staged_variant(int v) { return v == 6 || v == 8; }
 
 // The fastest variant measured per gather type and row width on the 3-mode
-// power-law workload (R = 16 and 32): FP32 rows of up to 64 bytes take the
-// non-pipelined walk at 3 CTAs per SM, wider FP32 rows the 32-byte-segment
-// walk; BF16 rows take the pipelined walk at 2 CTAs per SM.
+// power-law workload (R = 16 and 32): FP32 rows take the 32-byte-segment
+// walk on packed leaf records (the 16-byte walk at 3 CTAs per SM when ld is
+// not a multiple of 8); BF16 rows of up to 32 bytes the pipelined 16-byte
+// walk at 2 CTAs per SM, wider ones the 32-byte-segment walk.
 int default_variant(int32_t dtype, int32_t ld) {
-    if (dtype == SPTT_BF16) return 4;
-    return ld <= 16 ? 3 : 7;
+    if (dtype == SPTT_BF16) return ld <= 16 ? 4 : 7;
+    return ld % 8 == 0 ? 7 : 3;
 }
+
+// Variants that read the packed leaf records (sptt_csf::leafrec).
+static bool packed_variant(int v) { return v == 7; }
 
 sptt_status mttkrp_prepare(sptt_csf *csf, const sptt_sched *sched, cudaStream_t st) {
     const int32_t chunk = (sched && staged_variant(sched->variant)) ? kStageChunk
                           : ((sched && sched->chunk) ? sched->chunk : kDefaultChunk);
     if (csf->nfibs[csf->nmodes - 1] == 0) return SPTT_OK;
+    const int v = sched ? sched->variant : 0;
+    if (v == 0 || packed_variant(v)) SPTT_TRY(csf_ensure_leafrec(csf, st));
     return csf_ensure_partition(csf, chunk, st);
 }
 
@@ -289,6 +301,7 @@ sptt_status mttkrp_launch(sptt_csf *csf, const void *const *factors, int32_t dty
                                                   : ((sched && sched->chunk) ? sched->chunk : kDefaultChunk);
     const int block = (sched && sched->block) ? sched->block : 256;
     SPTT_TRY(csf_ensure_partition(csf, chunk, st));
+    if (packed_variant(variant)) SPTT_TRY(csf_ensure_leafrec(csf, st));
     if (csf->nheavy > 0) SPTT_TRY(fill_zero_launch(heavy, (size_t)csf->nheavy * ld * sizeof(double), st));
     walk::Args a{};
     for (int l = 0; l < N; ++l) {
@@ -306,6 +319,7 @@ sptt_status mttkrp_launch(sptt_csf *csf, const void *const *factors, int32_t dty
     a.out = out;
     a.heavy = heavy;
     a.hidx = csf->hidx;
+    a.leafrec = csf->leafrec;
     if (dtype == SPTT_BF16) return launch_t<__nv_bfloat16>(N, a, block, variant, csf->err, st);
     return launch_t<float>(N, a, block, variant, csf->err, st);
 }

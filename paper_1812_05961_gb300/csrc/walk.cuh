@@ -66,6 +66,7 @@ struct Args {
     float *out;                      // compact: nfibs[0] x ld, zeroed
     double *heavy;                   // nheavy x ld, zeroed
     const int32_t *hidx;             // per slice: heavy row index or -1
+    const uint4 *leafrec;            // packed leaf records (flag kernels of mttkrp.cu)
 };
 
 // A factor row segment as loaded: W = 16 or 32 bytes per lane (4 or 8 FP32
@@ -238,6 +239,7 @@ __device__ __forceinline__ void fold(float (&parent)[Raw<T, W>::VEC], float (&ch
 // Where a chunk's leaf records (values, leaf indices, level flags) are read
 // from: global memory, or a copy staged in shared memory.
 struct GlobalRecs {
+    static constexpr bool kPacked = false;
     const float *vals;
     const int32_t *idx;
     const uint8_t *lvl;
@@ -253,6 +255,7 @@ struct GlobalRecs {
 };
 
 struct SharedRecs {  // shared-memory addresses of the chunk's copy; k0 = the chunk's first leaf
+    static constexpr bool kPacked = false;
     uint32_t sv, si, sl;
     int64_t k0;
     __device__ __forceinline__ float4 v4(int64_t k) const {
@@ -324,6 +327,50 @@ __device__ __forceinline__ void fetch_batch(const Recs &rec, int64_t kb, float (
     }
 }
 
+// One 16-byte record per leaf (sptt_csf::leafrec): x = leaf index, y = the
+// value's bits, z = the index of the level-(N-2) fiber the leaf opens (0 if
+// it opens none), w = the leaf's level flag. A batch of leaves arrives in
+// 32-byte loads, and the factor row of a fiber that opens needs no other
+// load first.
+struct PackedRecs {
+    static constexpr bool kPacked = true;
+    const uint4 *rec;
+};
+
+// Records of the B leaves from kb on, and nf: for packed records the index
+// of the fiber each leaf opens; otherwise the indices of the B level-LF
+// fibers after fiber fb (the fibers a batch can open, in order).
+template <int B, int LF, typename Recs>
+__device__ __forceinline__ void fetch_all(const Recs &rec, const int32_t *fids_lf, int64_t fb, int64_t kb,
+                                          float (&v)[B], int32_t (&li)[B], uint32_t (&lw)[2], int32_t (&nf)[B]) {
+    if constexpr (Recs::kPacked) {
+        lw[0] = 0u;
+        lw[1] = 0u;
+#pragma unroll
+        for (int h = 0; h < B; h += 2) {
+            uint32_t r[8];
+            asm("ld.global.nc.v8.u32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                : "l"(rec.rec + kb + h));
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int j = h + q;
+                li[j] = (int32_t)r[4 * q];
+                v[j] = __uint_as_float(r[4 * q + 1]);
+                nf[j] = (int32_t)r[4 * q + 2];
+                lw[j >> 2] |= (r[4 * q + 3] & 0xffu) << (8 * (j & 3));
+            }
+        }
+    } else {
+        fetch_batch<B>(rec, kb, v, li, lw);
+        if constexpr (LF >= 1) {
+            const int32_t *fp = fids_lf + fb + 1;
+#pragma unroll
+            for (int q = 0; q < B; ++q) nf[q] = __ldg(fp + q);
+        }
+    }
+}
+
 // The batched walk driven by the per-leaf level flags. A lane group takes
 // its chunk in batches of B leaves: the batch's values, leaf indices and
 // level flags arrive in vector loads; then every factor row the batch needs
@@ -371,23 +418,10 @@ __device__ __forceinline__ void flag_chunk(const Args &a, int64_t c, int col, Ca
     int32_t li[B];
     uint32_t lw[2] = {0u, 0u};
     int32_t nf[B];
-    if constexpr (PIPE) {
-        fetch_batch<B>(rec, k0, v, li, lw);
-        if constexpr (LF >= 1) {
-            const int32_t *fp = a.fids[LF] + f[LF] + 1;
-#pragma unroll
-            for (int q = 0; q < B; ++q) nf[q] = __ldg(fp + q);
-        }
-    }
+    const int32_t *fids_lf = a.fids[LF > 0 ? LF : 0];
+    if constexpr (PIPE) fetch_all<B, LF>(rec, fids_lf, f[LF], k0, v, li, lw, nf);
     for (int64_t kb = k0; kb < k1; kb += B) {
-        if constexpr (!PIPE) {
-            fetch_batch<B>(rec, kb, v, li, lw);
-            if constexpr (LF >= 1) {
-                const int32_t *fp = a.fids[LF] + f[LF] + 1;
-#pragma unroll
-                for (int q = 0; q < B; ++q) nf[q] = __ldg(fp + q);
-            }
-        }
+        if constexpr (!PIPE) fetch_all<B, LF>(rec, fids_lf, f[LF], kb, v, li, lw, nf);
         const int nvalid = (k1 - kb < B) ? (int)(k1 - kb) : B;
         Row x[B];
 #pragma unroll
@@ -409,10 +443,15 @@ __device__ __forceinline__ void flag_chunk(const Args &a, int64_t c, int col, Ca
 #pragma unroll
             for (int j = 0; j < B; ++j)
                 if ((sm >> j) & 1u) {
-                    const int pos = __popc(sm & ((1u << j) - 1u));  // openings before leaf j
-                    int32_t id = nf[0];
+                    int32_t id;
+                    if constexpr (Recs::kPacked) {
+                        id = nf[j];
+                    } else {
+                        const int pos = __popc(sm & ((1u << j) - 1u));  // openings before leaf j
+                        id = nf[0];
 #pragma unroll
-                    for (int q = 1; q <= j; ++q) id = (pos == q) ? nf[q] : id;
+                        for (int q = 1; q <= j; ++q) id = (pos == q) ? nf[q] : id;
+                    }
                     nr[j] = Rw::load(a.fac[LF], id, ld, col);
                 }
         }
@@ -421,14 +460,7 @@ __device__ __forceinline__ void flag_chunk(const Args &a, int64_t c, int col, Ca
         int32_t lin[B];
         uint32_t lwn[2] = {0u, 0u};
         int32_t nfn[B];
-        if (more) {
-            fetch_batch<B>(rec, kb + B, vn, lin, lwn);
-            if constexpr (LF >= 1) {
-                const int32_t *fp = a.fids[LF] + f[LF] + __popc(sm) + 1;
-#pragma unroll
-                for (int q = 0; q < B; ++q) nfn[q] = __ldg(fp + q);
-            }
-        }
+        if (more) fetch_all<B, LF>(rec, fids_lf, f[LF] + __popc(sm), kb + B, vn, lin, lwn, nfn);
 #pragma unroll
         for (int j = 0; j < B; ++j) {
             if (j >= nvalid) break;

@@ -65,7 +65,7 @@ def default_index(rank: int = 16, dtype: int = SPTT_F32) -> int:
     (ascending order, chunk 128, the default variant for the gather type
     and rank)."""
     ld = (rank + 7) // 8 * 8
-    variant = 4 if dtype != SPTT_F32 else (3 if ld <= 16 else 7)
+    variant = (4 if ld <= 16 else 7) if dtype != SPTT_F32 else 7
     for i, c in enumerate(sptt_sched_candidates()):
         if c[0] == 128 and c[2] == variant and c[3] == 0:
             return i
