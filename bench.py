@@ -237,6 +237,22 @@ def flop_model(csf, R):
     return 2 * R * (nnz + sum(csf.nfibs[1:-1]))
 
 
+def every_gather_model(csf, R, s_f=4):
+    """Upper byte model: every factor-row gather from memory (no reuse)."""
+    return sum(csf.nfibs[1:]) * R * s_f
+
+
+# DRAM bytes (read + write) per launch of the default FP32 MTTKRP kernel,
+# from one ncu capture of the 2e7-non-zero case of this workload (roots
+# 0, 1, 2); the traffic is dominated by the leaf-record stream, so it is
+# scaled to other sizes by the number of non-zeros.
+NCU_TRAFFIC = {"kernel": "mttkrp_flag_kernel<3, float, 2, 2, 32, 1, 1>", "variant": 7, "nnz": 20_000_000,
+               "bytes": [368.268032e6, 405.6576e6, 405.596928e6]}
+# FP32 FMA peak from the unit counts and the clock: 152 SMs x 128 FP32
+# lanes x 2 flops x 2.07 GHz.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
 def batched_extra(args, dev):
     """The batched workload: 512 tensors (3/4 modes, log-uniform sizes), R = 16,
     15 iterations, one persistent launch per run, replayed from a CUDA graph;
@@ -469,6 +485,7 @@ def ours(args, rank, world, local):
     csfs = [sptt.Csf(dims, t.inds, t.vals, r) for r in range(3)]
     bytes_per = [byte_model(c, dims, R, distinct) for c in csfs]
     flops_per = [flop_model(c, R) for c in csfs]
+    gather_per = [every_gather_model(c, R) for c in csfs]
     nfibs = [c.nfibs for c in csfs]
     del csfs
 
@@ -516,8 +533,19 @@ def ours(args, rank, world, local):
     # so the algorithmic bytes are summed over the modes and divided by the total time
     alg_bytes = sum(bytes_per) * args.steps
     achieved = alg_bytes / (mttkrp_ms * 1e-3) / 1e9
+    # measured traffic applies while the timed kernel is the captured one
+    traffic = None
+    if sched is None and R in (16,) and len(dims) == 3:
+        traffic = sum(NCU_TRAFFIC["bytes"]) / 3 * nnz / NCU_TRAFFIC["nnz"]
+    flops_s = sum(flops_per) * args.steps / (mttkrp_ms * 1e-3) / 1e12
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": traffic,
+                "traffic_source": None if traffic is None else
+                "ncu dram__bytes_read.sum + dram__bytes_write.sum of %s at %d nnz, scaled by nnz (mean of the 3 roots)"
+                % (NCU_TRAFFIC["kernel"], NCU_TRAFFIC["nnz"]),
+                "every_gather_bytes_per_launch": [int(b) for b in gather_per],
+                "fp32_fma": {"achieved_tflops": flops_s, "peak_tflops": FP32_PEAK_TFLOPS,
+                             "frac": flops_s / FP32_PEAK_TFLOPS, "peak_kind": "derived from unit counts and clock"},
                 "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                 else "fallback 6.8 TB/s",
                 "bytes_per_launch": [int(b) for b in bytes_per],

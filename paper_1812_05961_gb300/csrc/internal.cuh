@@ -175,6 +175,8 @@ sptt_status mttkrp_launch(sptt_csf *csf, const void *const *factors, int32_t dty
 // Builds the work partition the launch will use (allocates on first use, so
 // call it before any stream capture).
 sptt_status mttkrp_prepare(sptt_csf *csf, const sptt_sched *sched, cudaStream_t st);
+// Leaves per chunk when the schedule does not say (depends on nnz and the SM count).
+int32_t default_chunk(int64_t nnz);
 
 // MTTKRP for the mode at level L >= 1 of the CSF (mttkrp_mode.cu): out is
 // full (dims[order[L]] x ld FP32), zeroed here, then filled. Call

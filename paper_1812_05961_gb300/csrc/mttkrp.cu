@@ -254,7 +254,14 @@ sptt_status launch_t(int nm, const walk::Args &a, int block, int variant, int32_
 
 }  // namespace
 
-constexpr int32_t kDefaultChunk = 128;
+// Default leaves per chunk: 128, halved (down to 16) while the tensor would
+// give fewer than 256 chunks per SM, so that small tensors still fill the GPU.
+int32_t default_chunk(int64_t nnz) {
+    const int64_t target = (int64_t)device_sm_count() * 256;
+    int32_t c = 128;
+    while (c > 16 && nnz / c < target) c >>= 1;
+    return c;
+}
 
 static bool staged_variant(int v) { return v == 6 || v == 8; }
 
@@ -273,7 +280,7 @@ static bool packed_variant(int v) { return v == 7; }
 
 sptt_status mttkrp_prepare(sptt_csf *csf, const sptt_sched *sched, cudaStream_t st) {
     const int32_t chunk = (sched && staged_variant(sched->variant)) ? kStageChunk
-                          : ((sched && sched->chunk) ? sched->chunk : kDefaultChunk);
+                          : ((sched && sched->chunk) ? sched->chunk : default_chunk(csf->nfibs[csf->nmodes - 1]));
     if (csf->nfibs[csf->nmodes - 1] == 0) return SPTT_OK;
     const int v = sched ? sched->variant : 0;
     if (v == 0 || packed_variant(v)) SPTT_TRY(csf_ensure_leafrec(csf, st));
@@ -298,7 +305,7 @@ sptt_status mttkrp_launch(sptt_csf *csf, const void *const *factors, int32_t dty
         if (!wide_ok) variant = variant == 7 ? 3 : 6;
     }
     const int32_t chunk = staged_variant(variant) ? kStageChunk
-                                                  : ((sched && sched->chunk) ? sched->chunk : kDefaultChunk);
+                                                  : ((sched && sched->chunk) ? sched->chunk : default_chunk(csf->nfibs[csf->nmodes - 1]));
     const int block = (sched && sched->block) ? sched->block : 256;
     SPTT_TRY(csf_ensure_partition(csf, chunk, st));
     if (packed_variant(variant)) SPTT_TRY(csf_ensure_leafrec(csf, st));

@@ -357,7 +357,7 @@ int csf_level_of(const sptt_csf *c, int32_t mode) {
 }
 
 sptt_status mttkrp_mode_prepare(sptt_csf *c, int32_t L, int32_t ld, const sptt_sched *sched, cudaStream_t st) {
-    const int32_t chunk = (sched && sched->chunk) ? sched->chunk : 128;
+    const int32_t chunk = (sched && sched->chunk) ? sched->chunk : default_chunk(c->nfibs[c->nmodes - 1]);
     SPTT_TRY(csf_ensure_partition(c, chunk, st));
     const bool priv = !(sched && sched->variant == 1);
     if (priv) SPTT_TRY(ensure_hot(c, L, ld, st));
@@ -370,7 +370,7 @@ sptt_status mttkrp_mode_launch(sptt_csf *c, int32_t L, const void *const *factor
     SPTT_TRY(fill_zero_launch(out, (size_t)c->dims[c->order[L]] * ld * sizeof(float), st));
     const int64_t nnz = c->nfibs[N - 1];
     if (nnz == 0) return SPTT_OK;
-    const int32_t chunk = (sched && sched->chunk) ? sched->chunk : 128;
+    const int32_t chunk = (sched && sched->chunk) ? sched->chunk : default_chunk(nnz);
     SPTT_TRY(csf_ensure_partition(c, chunk, st));
     const bool priv = !(sched && sched->variant == 1);
     LevelArgs a{};

@@ -60,14 +60,19 @@ def train(ds: Dataset, steps: int = 2000, lr: float = 3e-3, seed: int = 0, devic
     return m, hist
 
 
-def default_index(rank: int = 16, dtype: int = SPTT_F32) -> int:
-    """Index of the library's default schedule among the candidates
-    (ascending order, chunk 128, the default variant for the gather type
-    and rank)."""
+def default_index(rank: int = 16, dtype: int = SPTT_F32, nnz: int = 1 << 30, sms: int = 152) -> int:
+    """Index of the candidate closest to the library's default schedule:
+    ascending order, the default variant for the gather type and rank, and
+    the default chunk (128, halved while nnz / chunk < 256 per SM; the
+    candidates have 64 and 128)."""
     ld = (rank + 7) // 8 * 8
     variant = (4 if ld <= 16 else 7) if dtype != SPTT_F32 else 7
+    chunk = 128
+    while chunk > 16 and nnz // chunk < sms * 256:
+        chunk //= 2
+    chunk = 128 if chunk >= 128 else 64
     for i, c in enumerate(sptt_sched_candidates()):
-        if c[0] == 128 and c[2] == variant and c[3] == 0:
+        if c[0] == chunk and c[2] == variant and c[3] == 0:
             return i
     return 0
 
@@ -81,7 +86,7 @@ def regret(ds: Dataset, model=None, fixed: int = None):
     elif fixed is not None:
         choice = [fixed] * len(ds.samples)
     else:
-        choice = [default_index(s.rank) for s in ds.samples]
+        choice = [default_index(s.rank, nnz=int(round(2.0 ** s.features[0]))) for s in ds.samples]
     return [s.times_ms[k] / min(s.times_ms) - 1.0 for s, k in zip(ds.samples, choice)]
 
 
