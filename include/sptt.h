@@ -505,8 +505,10 @@ sptt_status sptt_batch_lambda(sptt_batch *batch, int32_t t, double *lambda);
 sptt_status sptt_batch_info(sptt_batch *batch, int32_t *grid, int64_t *chunks, int64_t *tiles);
 
 /* Wall time (ms, summed over all runs since create) that CTA 0 of the
- * batched kernel spent in each phase: MTTKRP, normal equations, row solve,
- * finalise/fit, normalise (5 doubles, host). Synchronises. */
+ * batched kernel spent in each phase: ms[0..4] = MTTKRP, normal equations,
+ * row solve, finalise/fit, normalise (each including the wait at the grid
+ * barrier that ends it), ms[5 + p] = the part of phase p spent waiting in
+ * that barrier (10 doubles, host). Synchronises. */
 sptt_status sptt_batch_phase_ms(sptt_batch *batch, double *ms);
 
 /*

@@ -484,9 +484,12 @@ def sptt_batch_info(b: int):
 
 
 def sptt_batch_phase_ms(b: int):
-    ms = (ctypes.c_double * 5)()
+    ms = (ctypes.c_double * 10)()
     _check(lib().sptt_batch_phase_ms(b, ms), "sptt_batch_phase_ms")
-    return dict(zip(("mttkrp", "normal_eq", "row_solve", "finalize_fit", "normalize"), list(ms)))
+    names = ("mttkrp", "normal_eq", "row_solve", "finalize_fit", "normalize")
+    out = dict(zip(names, list(ms)[:5]))
+    out.update({k + "_barrier_wait": v for k, v in zip(names, list(ms)[5:])})
+    return out
 
 
 def sptt_debug_batch_stall(b: int, skip_block: int, timeout_ns: int):

@@ -37,6 +37,11 @@ struct sptt_cpd {
     sptt_sched msched[SPTT_MAX_MODES] = {};  // schedule of each mode's MTTKRP
     bool has_msched[SPTT_MAX_MODES] = {false};
     cudaStream_t st = nullptr;
+    // the normal equations of mode n depend only on the other modes' Grams,
+    // so they run on a second stream while mode n's MTTKRP runs
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork[SPTT_MAX_MODES] = {nullptr};
+    cudaEvent_t ev_join[SPTT_MAX_MODES] = {nullptr};
     sptt_csf *csf[SPTT_MAX_MODES] = {nullptr};
     // csf_mode 1/2: one CSF for every mode; one_level[n] = the tree level of mode n
     sptt_csf *one = nullptr;
@@ -79,17 +84,19 @@ cudaEvent_t take_event(sptt_cpd *c) {
 struct Timed {
     sptt_cpd *c;
     int cat;
+    cudaStream_t s;
     cudaEvent_t a = nullptr;
-    Timed(sptt_cpd *c_, int cat_) : c(c_), cat(cat_) {
+    Timed(sptt_cpd *c_, int cat_, cudaStream_t s_) : c(c_), cat(cat_), s(s_) {
         if (c->opts.profile) {
             a = take_event(c);
-            cudaEventRecord(a, c->st);
+            cudaEventRecord(a, s);
         }
     }
+    Timed(sptt_cpd *c_, int cat_) : Timed(c_, cat_, c_->st) {}
     ~Timed() {
         if (a) {
             cudaEvent_t b = take_event(c);
-            cudaEventRecord(b, c->st);
+            cudaEventRecord(b, s);
             c->pending.push_back({cat, a, b});
         }
     }
@@ -119,12 +126,24 @@ sptt_status run_iteration(sptt_cpd *c, bool bf16) {
         sptt_csf *cs = c->one ? c->one : c->csf[n];
         const int L = c->one ? c->one_level[n] : 0;  // L > 0: a non-root mode of the one CSF
         const int32_t dt = bf16 ? SPTT_BF16 : SPTT_F32;
+        const bool fork = c->side != nullptr;
+        if (fork) {
+            SPTT_CUDA(cudaEventRecord(c->ev_fork[n], c->st));
+            SPTT_CUDA(cudaStreamWaitEvent(c->side, c->ev_fork[n], 0));
+            {
+                Timed t(c, 1, c->side);
+                SPTT_TRY(normal_prep_launch(c->G, N, n, c->rank, &c->w, c->side));
+            }
+            SPTT_CUDA(cudaEventRecord(c->ev_join[n], c->side));
+        }
         {
             Timed t(c, 0);
             if (L == 0) SPTT_TRY(mttkrp_launch(cs, fac, dt, c->ld, c->M, c->Mh, sched, c->st));
             else SPTT_TRY(mttkrp_mode_launch(cs, L, fac, dt, c->ld, c->M, &c->one_sched[n], c->st));
         }
-        {
+        if (fork) {
+            SPTT_CUDA(cudaStreamWaitEvent(c->st, c->ev_join[n], 0));
+        } else {
             Timed t(c, 1);
             SPTT_TRY(normal_prep_launch(c->G, N, n, c->rank, &c->w, c->st));
         }
@@ -280,6 +299,14 @@ void destroy(sptt_cpd *c) {
         cudaEventDestroy(r.b);
     }
     for (auto e : c->free_events) cudaEventDestroy(e);
+    for (int m = 0; m < SPTT_MAX_MODES; ++m) {
+        if (c->ev_fork[m]) cudaEventDestroy(c->ev_fork[m]);
+        if (c->ev_join[m]) cudaEventDestroy(c->ev_join[m]);
+    }
+    if (c->side) {
+        cudaStreamSynchronize(c->side);
+        cudaStreamDestroy(c->side);
+    }
     cudaStreamSynchronize(c->st);
     delete c;
 }
@@ -329,6 +356,11 @@ extern "C" sptt_status sptt_cpd_create(const sptt_coo *coo, int32_t rank, const 
     c->opts.mode_sched = nullptr;
     c->opts.mlp = nullptr;
     c->st = st;
+    SPTT_CUDA(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+    for (int m = 0; m < c->N; ++m) {
+        SPTT_CUDA(cudaEventCreateWithFlags(&c->ev_fork[m], cudaEventDisableTiming));
+        SPTT_CUDA(cudaEventCreateWithFlags(&c->ev_join[m], cudaEventDisableTiming));
+    }
     for (int m = 0; m < c->N; ++m) {
         c->dims[m] = coo->dims[m];
         const sptt_sched *s = o.mode_sched ? &o.mode_sched[m] : o.sched;

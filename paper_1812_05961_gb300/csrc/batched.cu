@@ -66,7 +66,8 @@ struct BatchArgs {
     int64_t *it_base;    // iterations run before this launch (indexes the fit ring)
     uint64_t timeout_ns;
     int32_t skip_block;  // test hook: this CTA leaves before the first barrier (-1: none)
-    unsigned long long *phase_ns;  // [5] wall time CTA 0 spends in each phase (M, P, S, F, N)
+    unsigned long long *phase_ns;  // [10] wall time CTA 0 spends in each phase (M, P, S, F, N; the barrier
+                                   // that ends it included) and, in [5 + phase], its wait in that barrier
     int32_t zero_first;  // clear A_n before its first update (rows without a slice end at 0)
 };
 
@@ -78,9 +79,10 @@ __device__ __forceinline__ uint64_t globaltimer() {
 
 // Grid barrier with a bounded wait. Returns false (on every thread of the
 // CTA) when the error word is set, by this CTA or another.
-__device__ bool grid_barrier(const BatchArgs &a) {
+__device__ bool grid_barrier(const BatchArgs &a, int ph) {
     __shared__ int s_ok;
     __syncthreads();
+    const uint64_t tb = (blockIdx.x == 0 && threadIdx.x == 0) ? globaltimer() : 0;
     if (threadIdx.x == 0) {
         volatile unsigned *vgen = a.bar + 1;
         volatile int32_t *verr = a.err;
@@ -106,6 +108,7 @@ __device__ bool grid_barrier(const BatchArgs &a) {
         }
         __threadfence();
         s_ok = ok && (*verr == 0);
+        if (blockIdx.x == 0) a.phase_ns[5 + ph] += globaltimer() - tb;
     }
     __syncthreads();
     return s_ok != 0;
@@ -264,7 +267,7 @@ __global__ void __launch_bounds__(kBThreads, 2) batched_cpals_kernel(const Batch
         for (int n = 0; n < a.max_modes; ++n) {
             // M: MTTKRP of mode n over the global chunk list
             if (gi < gpw) mttkrp_phase(a, n, gi, gpw, col);
-            if (!grid_barrier(a)) return;
+            if (!grid_barrier(a, 0)) return;
             phase_done(0);
             // P: normal equations per tensor
             for (int tt = blockIdx.x; tt < a.count; tt += gridDim.x) {
@@ -280,11 +283,11 @@ __global__ void __launch_bounds__(kBThreads, 2) batched_cpals_kernel(const Batch
                 dense::normal_prep_body(g, T.nmodes, n, rank, T.W, T.branch, prep_sm);
                 __syncthreads();
             }
-            if (!grid_barrier(a)) return;
+            if (!grid_barrier(a, 1)) return;
             phase_done(1);
             // S: row solve + Gram + dots
             solve_phase<RP>(a, n, solve_sm);
-            if (!grid_barrier(a)) return;
+            if (!grid_barrier(a, 2)) return;
             phase_done(2);
             // F: lambda, G_n, fit
             for (int tt = blockIdx.x; tt < a.count; tt += gridDim.x) {
@@ -312,11 +315,11 @@ __global__ void __launch_bounds__(kBThreads, 2) batched_cpals_kernel(const Batch
                 }
                 __syncthreads();
             }
-            if (!grid_barrier(a)) return;
+            if (!grid_barrier(a, 3)) return;
             phase_done(3);
             // N: normalise the updated factor
             normalize_phase<RP>(a, n);
-            if (!grid_barrier(a)) return;
+            if (!grid_barrier(a, 4)) return;
             phase_done(4);
         }
     }
@@ -548,7 +551,7 @@ extern "C" sptt_status sptt_batch_create(const sptt_coo *coos, int32_t count, in
     SPTT_TRY(batch_alloc(b, &b->d_bar, 2, true));
     SPTT_TRY(batch_alloc(b, &b->d_err, 1, true));
     SPTT_TRY(batch_alloc(b, &b->d_it_base, 1, true));
-    SPTT_TRY(batch_alloc(b, &b->d_phase, 5, true));
+    SPTT_TRY(batch_alloc(b, &b->d_phase, 10, true));
     b->gram_blocks = device_sm_count() * 2;
     SPTT_TRY(batch_alloc(b, &b->partials, (size_t)b->gram_blocks * (rank * rank + rank), false));
     // a grid that is fully resident (cooperative launch)
@@ -690,10 +693,10 @@ extern "C" sptt_status sptt_batch_info(sptt_batch *b, int32_t *grid, int64_t *ch
 extern "C" sptt_status sptt_batch_phase_ms(sptt_batch *b, double *ms) {
     clear_error();
     if (!b || !ms) return set_error(SPTT_ERR_BAD_ARG, "batch and ms must be non-NULL");
-    unsigned long long ns[5];
+    unsigned long long ns[10];
     SPTT_CUDA(cudaMemcpyAsync(ns, b->d_phase, sizeof(ns), cudaMemcpyDeviceToHost, b->st));
     SPTT_CUDA(cudaStreamSynchronize(b->st));
-    for (int i = 0; i < 5; ++i) ms[i] = ns[i] * 1e-6;
+    for (int i = 0; i < 10; ++i) ms[i] = ns[i] * 1e-6;
     return SPTT_OK;
 }
 
