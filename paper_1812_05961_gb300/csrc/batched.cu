@@ -226,17 +226,32 @@ __device__ __noinline__ void normalize_phase(const BatchArgs &a, int n) {
         const int64_t rows = T.nslices[n];
         const int32_t *fids0 = T.fids0[n];
         float *A = T.A[n];
-        for (int e = threadIdx.x; e < TR * qpr; e += kBThreads) {
+        // the thread's row indices, then its rows, then the stores: the loads
+        // of one tile are in flight together (TR * qpr <= 4 * kBThreads)
+        constexpr int IT = 4;
+        float4 *p[IT];
+        float4 v[IT];
+#pragma unroll
+        for (int it = 0; it < IT; ++it) {
+            const int e = threadIdx.x + it * kBThreads;
             const int64_t i = i0 + e / qpr;
-            if (i >= rows) break;  // e grows with i
-            const int c0 = (e % qpr) * 4;
-            float4 *p = reinterpret_cast<float4 *>(A + (int64_t)__ldg(fids0 + i) * ld + c0);
-            float4 v = *p;
-            v.x = (c0 + 0 < rank) ? v.x * T.inv_lambda[c0 + 0] : 0.f;
-            v.y = (c0 + 1 < rank) ? v.y * T.inv_lambda[c0 + 1] : 0.f;
-            v.z = (c0 + 2 < rank) ? v.z * T.inv_lambda[c0 + 2] : 0.f;
-            v.w = (c0 + 3 < rank) ? v.w * T.inv_lambda[c0 + 3] : 0.f;
-            *p = v;
+            p[it] = (e < TR * qpr && i < rows)
+                        ? reinterpret_cast<float4 *>(A + (int64_t)__ldg(fids0 + i) * ld + (e % qpr) * 4)
+                        : nullptr;
+        }
+#pragma unroll
+        for (int it = 0; it < IT; ++it)
+            if (p[it]) v[it] = *p[it];
+#pragma unroll
+        for (int it = 0; it < IT; ++it) {
+            if (!p[it]) continue;
+            const int c0 = ((threadIdx.x + it * kBThreads) % qpr) * 4;
+            float4 x = v[it];
+            x.x = (c0 + 0 < rank) ? x.x * T.inv_lambda[c0 + 0] : 0.f;
+            x.y = (c0 + 1 < rank) ? x.y * T.inv_lambda[c0 + 1] : 0.f;
+            x.z = (c0 + 2 < rank) ? x.z * T.inv_lambda[c0 + 2] : 0.f;
+            x.w = (c0 + 3 < rank) ? x.w * T.inv_lambda[c0 + 3] : 0.f;
+            *p[it] = x;
         }
     }
 }

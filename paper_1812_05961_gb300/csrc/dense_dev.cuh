@@ -105,36 +105,63 @@ __device__ __forceinline__ void solve_tile(SolveTile<RP> &sm, SolveRun &acc, flo
                                            float *A, int64_t i0, int64_t rows, int rank, int ld) {
     using ST = SolveTile<RP>;
     constexpr int Q = RP / 4;
+    constexpr int IT = ST::TR * Q / 256;  // float4 pieces per thread (4)
+    static_assert(ST::TR * Q == IT * 256, "a tile is whole float4 pieces per thread");
     const int t = threadIdx.x;
-    for (int e = t; e < ST::TR * Q; e += 256) {
+    // all of the thread's heavy-row indices, then all of its M pieces, then
+    // the clearing stores: the loads of one tile are in flight together
+    int32_t h[IT];
+    bool live[IT];
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+        const int e = t + it * 256;
         const int r = e / Q, c = (e % Q) * 4;
         const int64_t i = i0 + r;
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (i < rows && c < ld) {
-            const int32_t h = hidx ? __ldg(hidx + i) : -1;
-            float4 *pm = reinterpret_cast<float4 *>(M + i * ld + c);
-            if (h >= 0) {
-                double2 *ph = reinterpret_cast<double2 *>(heavy + (int64_t)h * ld + c);
+        live[it] = i < rows && c < ld;
+        h[it] = (live[it] && hidx) ? __ldg(hidx + i) : -1;
+    }
+    float4 v[IT];
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+        const int e = t + it * 256;
+        const int r = e / Q, c = (e % Q) * 4;
+        const int64_t i = i0 + r;
+        v[it] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (live[it]) {
+            if (h[it] >= 0) {
+                const double2 *ph = reinterpret_cast<const double2 *>(heavy + (int64_t)h[it] * ld + c);
                 const double2 d0 = ph[0], d1 = ph[1];
-                v = make_float4((float)d0.x, (float)d0.y, (float)d1.x, (float)d1.y);
-                if (CLEAR) {
-                    ph[0] = make_double2(0.0, 0.0);
-                    ph[1] = make_double2(0.0, 0.0);
-                }
+                v[it] = make_float4((float)d0.x, (float)d0.y, (float)d1.x, (float)d1.y);
             } else {
-                v = *pm;
+                v[it] = *reinterpret_cast<const float4 *>(M + i * ld + c);
             }
-            if (CLEAR) *pm = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (c + 0 >= rank) v.x = 0.f;
-            if (c + 1 >= rank) v.y = 0.f;
-            if (c + 2 >= rank) v.z = 0.f;
-            if (c + 3 >= rank) v.w = 0.f;
         }
-        *reinterpret_cast<float4 *>(&sm.Mt[r][c]) = v;
+    }
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+        const int e = t + it * 256;
+        const int r = e / Q, c = (e % Q) * 4;
+        const int64_t i = i0 + r;
+        if (CLEAR && live[it]) {
+            *reinterpret_cast<float4 *>(M + i * ld + c) = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (h[it] >= 0) {
+                double2 *ph = reinterpret_cast<double2 *>(heavy + (int64_t)h[it] * ld + c);
+                ph[0] = make_double2(0.0, 0.0);
+                ph[1] = make_double2(0.0, 0.0);
+            }
+        }
+        float4 x = v[it];
+        if (c + 0 >= rank) x.x = 0.f;
+        if (c + 1 >= rank) x.y = 0.f;
+        if (c + 2 >= rank) x.z = 0.f;
+        if (c + 3 >= rank) x.w = 0.f;
+        *reinterpret_cast<float4 *>(&sm.Mt[r][c]) = x;
     }
     __syncthreads();
     {
         const int r = t / ST::TPR, cb = (t % ST::TPR) * 16;
+        const int64_t irow = i0 + r;
+        const int64_t arow = irow < rows ? (fids0 ? (int64_t)__ldg(fids0 + irow) : irow) : 0;  // requested before the product
         float o[16];
 #pragma unroll
         for (int j = 0; j < 16; ++j) o[j] = 0.f;
@@ -157,9 +184,8 @@ __device__ __forceinline__ void solve_tile(SolveTile<RP> &sm, SolveRun &acc, flo
         for (int q = 0; q < 4; ++q)
             *reinterpret_cast<float4 *>(&sm.At[r][cb + 4 * q]) =
                 make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
-        const int64_t i = i0 + r;
-        if (i < rows) {
-            float *dst = A + (fids0 ? (int64_t)__ldg(fids0 + i) : i) * ld + cb;
+        if (irow < rows) {
+            float *dst = A + arow * ld + cb;
 #pragma unroll
             for (int q = 0; q < 4; ++q)
                 if (cb + 4 * q < ld)
