@@ -58,6 +58,7 @@ struct BatchArgs {
     const BTensor *T;
     int32_t count, rank, ld, iters, max_modes;
     const int64_t *chunk_prefix[kMaxModes];  // [count + 1] per mode position
+    const int32_t *chunk_owner[kMaxModes];   // [total_chunks] tensor of each global chunk
     const int64_t *tile_prefix[kMaxModes];   // [count + 1]
     int64_t total_chunks[kMaxModes];
     int64_t total_tiles[kMaxModes];
@@ -165,7 +166,7 @@ __device__ __noinline__ void mttkrp_phase(const BatchArgs &a, int n, int gi, int
     const int64_t nwarps = (int64_t)(gridDim.x * blockDim.x) >> 5;
     const int64_t *prefix = a.chunk_prefix[n];
     for (int64_t gc = gwarp * gpw + gi; gc < a.total_chunks[n]; gc += nwarps * gpw) {
-        const int tt = find_owner(prefix, a.count, gc);
+        const int tt = __ldg(a.chunk_owner[n] + gc);
         const BTensor &T = a.T[tt];
         const int64_t c = gc - __ldg(prefix + tt);
         switch (T.nmodes) {
@@ -366,6 +367,7 @@ struct sptt_batch {
     std::vector<void *> allocs;         // every device buffer owned by the batch
     BTensor *d_tensors = nullptr;
     int64_t *d_prefix = nullptr;        // 2 * max_modes * (count + 1)
+    int32_t *d_owner[kMaxModes] = {nullptr};  // per mode position: tensor of each global chunk
     int64_t total_chunks[kMaxModes] = {0};
     int64_t total_tiles[kMaxModes] = {0};
     unsigned *d_bar = nullptr;
@@ -414,6 +416,7 @@ sptt_status launch_batch(sptt_batch *b, int32_t iters) {
     a.max_modes = b->max_modes;
     for (int n = 0; n < b->max_modes; ++n) {
         a.chunk_prefix[n] = b->d_prefix + (2 * n) * (b->count + 1);
+        a.chunk_owner[n] = b->d_owner[n];
         a.tile_prefix[n] = b->d_prefix + (2 * n + 1) * (b->count + 1);
         a.total_chunks[n] = b->total_chunks[n];
         a.total_tiles[n] = b->total_tiles[n];
@@ -563,6 +566,21 @@ extern "C" sptt_status sptt_batch_create(const sptt_coo *coos, int32_t count, in
     SPTT_TRY(batch_alloc(b, &b->d_prefix, prefix.size(), false));
     SPTT_CUDA(cudaMemcpyAsync(b->d_prefix, prefix.data(), prefix.size() * sizeof(int64_t), cudaMemcpyHostToDevice,
                               b->st));
+    {
+        // chunk -> tensor tables (one load per chunk in the MTTKRP phase)
+        std::vector<int32_t> owner;
+        for (int n = 0; n < b->max_modes; ++n) {
+            const int64_t *cp = prefix.data() + (2 * n) * (count + 1);
+            owner.assign((size_t)cp[count], 0);
+            for (int t = 0; t < count; ++t)
+                for (int64_t g = cp[t]; g < cp[t + 1]; ++g) owner[(size_t)g] = t;
+            SPTT_TRY(batch_alloc(b, &b->d_owner[n], owner.size() + 1, false));
+            if (!owner.empty())
+                SPTT_CUDA(cudaMemcpyAsync(b->d_owner[n], owner.data(), owner.size() * sizeof(int32_t),
+                                          cudaMemcpyHostToDevice, b->st));
+            SPTT_CUDA(cudaStreamSynchronize(b->st));  // the host vector is reused
+        }
+    }
     SPTT_TRY(batch_alloc(b, &b->d_bar, 2, true));
     SPTT_TRY(batch_alloc(b, &b->d_err, 1, true));
     SPTT_TRY(batch_alloc(b, &b->d_it_base, 1, true));
