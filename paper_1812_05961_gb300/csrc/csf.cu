@@ -72,13 +72,27 @@ struct OutPtrs {
     int32_t *p[kMaxModes];
 };
 
+// Where each level's sorted index comes from: levels of the last-sorted key
+// group are bit fields of the sorted key (shift[l] >= 0, width bits[l]);
+// the others are gathered through the permutation.
+struct Decode {
+    int shift[kMaxModes];
+    int bits[kMaxModes];
+};
+
 __global__ void gather_sorted_kernel(IdxPtrs lev_inds, int nlev, const float *__restrict__ vals,
-                                     const uint32_t *__restrict__ perm, int64_t n, OutPtrs out,
-                                     float *__restrict__ out_vals) {
+                                     const uint32_t *__restrict__ perm, const uint64_t *__restrict__ keys,
+                                     Decode dec, int64_t n, OutPtrs out, float *__restrict__ out_vals) {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
          k += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t src = perm[k];
-        for (int l = 0; l < nlev; ++l) out.p[l][k] = lev_inds.p[l][src];
+        const uint64_t key = keys[k];
+        for (int l = 0; l < nlev; ++l) {
+            if (dec.shift[l] >= 0)
+                out.p[l][k] = dec.bits[l] ? (int32_t)((key >> dec.shift[l]) & ((uint64_t(1) << dec.bits[l]) - 1)) : 0;
+            else
+                out.p[l][k] = lev_inds.p[l][src];
+        }
         out_vals[k] = vals[src];
     }
 }
@@ -421,6 +435,9 @@ sptt_status csf_build_device(const sptt_coo *coo, int32_t root, const int32_t *o
     for (int l = 0; l < N; ++l) lev_src[l] = coo->inds[order[l]];
     DevBuf kA, kB, vA, vB;
     uint32_t *perm = nullptr;
+    uint64_t *sorted_keys = nullptr;
+    Decode dec{};
+    for (int j = 0; j < kMaxModes; ++j) dec.shift[j] = -1;
     if (n > 0) {
         SPTT_TRY(kA.alloc<uint64_t>(n, st));
         SPTT_TRY(kB.alloc<uint64_t>(n, st));
@@ -440,8 +457,13 @@ sptt_status csf_build_device(const sptt_coo *coo, int32_t root, const int32_t *o
                 --lo_level;
             }
             int shift = 0;
+            const bool last = lo_level < 0;  // this group holds level 0: it is sorted last
             for (int j = l; j > lo_level; --j) {  // leaf-most level in the low bits
                 const int b = bits_for(c->dims[order[j]]);
+                if (last) {
+                    dec.shift[j] = shift;
+                    dec.bits[j] = b;
+                }
                 if (b == 0) continue;  // a length-1 mode contributes no key bits
                 g.idx[g.nlev] = lev_src[j];
                 g.shift[g.nlev] = shift;
@@ -460,6 +482,7 @@ sptt_status csf_build_device(const sptt_coo *coo, int32_t root, const int32_t *o
             l = lo_level;
         }
         perm = vals;
+        sorted_keys = keys;
     }
 
     // 3. gather sorted coordinates (level order) and values
@@ -476,7 +499,7 @@ sptt_status csf_build_device(const sptt_coo *coo, int32_t root, const int32_t *o
         SPTT_TRY(sv_store.alloc<float>(n, st));
         IdxPtrs lp{};
         for (int l = 0; l < N; ++l) lp.p[l] = lev_src[l];
-        gather_sorted_kernel<<<grid_for(n), kThreads, 0, st>>>(lp, N, coo->vals, perm, n, so,
+        gather_sorted_kernel<<<grid_for(n), kThreads, 0, st>>>(lp, N, coo->vals, perm, sorted_keys, dec, n, so,
                                                                sv_store.as<float>());
         SPTT_CHECK_LAUNCH("gather_sorted_kernel");
     }
