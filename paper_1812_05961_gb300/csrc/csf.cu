@@ -36,31 +36,31 @@ struct IdxPtrs {
     const int32_t *p[kMaxModes];
 };
 
-__global__ void check_indices_kernel(IdxPtrs inds, int nmodes, int64_t nnz, const int64_t *dims_dev_unused,
-                                     int64_t d0, int64_t d1, int64_t d2, int64_t d3, int64_t d4,
-                                     int32_t *err) {
-    const int64_t dims[kMaxModes] = {d0, d1, d2, d3, d4};
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nnz;
-         k += (int64_t)gridDim.x * blockDim.x) {
-        for (int m = 0; m < nmodes; ++m) {
-            int32_t x = inds.p[m][k];
-            if (x < 0 || (int64_t)x >= dims[m]) atomicOr(err, 1);
-        }
-    }
-}
-
 // key[k] = sum over the group's levels of idx << shift, taken at src(k).
+// Every index of the group's levels (length-1 modes included, which add no
+// key bits) is checked against its mode length on the way: each level
+// belongs to one group, so every index of the tensor is checked once.
 struct KeyGroup {
     int nlev;
     const int32_t *idx[kMaxModes];
     int shift[kMaxModes];
+    int nchk;
+    const int32_t *chk[kMaxModes];
+    int64_t dim[kMaxModes];
 };
 
 __global__ void build_keys_kernel(KeyGroup g, const uint32_t *__restrict__ perm, int64_t n,
-                                  uint64_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+                                  uint64_t *__restrict__ keys, uint32_t *__restrict__ vals,
+                                  int32_t *__restrict__ err) {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
          k += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t src = perm ? perm[k] : (uint32_t)k;
+        bool bad = false;
+        for (int j = 0; j < g.nchk; ++j) {
+            const int32_t x = g.chk[j][src];
+            bad |= x < 0 || (int64_t)x >= g.dim[j];
+        }
+        if (bad) atomicOr(err, 1);
         uint64_t key = 0;
         for (int j = 0; j < g.nlev; ++j) key |= (uint64_t)(uint32_t)g.idx[j][src] << g.shift[j];
         keys[k] = key;
@@ -107,6 +107,34 @@ __global__ void prefix_flags_kernel(IdxPtrs s, int upto, int64_t n, int32_t *__r
                 if (s.p[l][k] != s.p[l][k - 1]) { f = 1; break; }
         flags[k] = f;
     }
+}
+
+// d[k] = the first level whose index differs from position k - 1 (0 at
+// k = 0; nlev when all are equal, i.e. a duplicate coordinate). Fiber
+// starts, duplicate runs and the CSF's per-leaf level flags all follow.
+__global__ void level_diff_kernel(IdxPtrs s, int nlev, int64_t n, uint8_t *__restrict__ d,
+                                  unsigned long long *__restrict__ ndup) {
+    unsigned long long dup = 0;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        int x = 0;
+        if (k > 0) {
+            x = nlev;
+            for (int l = 0; l < nlev; ++l)
+                if (s.p[l][k] != s.p[l][k - 1]) { x = l; break; }
+        }
+        dup += (x == nlev);
+        d[k] = (uint8_t)x;
+    }
+    for (int o = 16; o > 0; o >>= 1) dup += __shfl_xor_sync(0xffffffffu, dup, o);
+    if ((threadIdx.x & 31) == 0 && dup) atomicAdd(ndup, dup);
+}
+
+// flags[k] = 1 when position k starts a new fiber of level l (d[k] <= l).
+__global__ void level_flags_kernel(const uint8_t *__restrict__ d, int l, int64_t n, int32_t *__restrict__ flags) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x)
+        flags[k] = d[k] <= l;
 }
 
 // For each distinct coordinate u starting at k: starts[u] = k.
@@ -160,18 +188,6 @@ __global__ void fill_levels_kernel(IdxPtrs s, LevelScan ls, int nlev, int64_t n)
 }
 
 // lvl[k] = first level whose coordinate changes at k (0 for k = 0).
-__global__ void leaf_level_kernel(IdxPtrs s, int nlev, int64_t n, uint8_t *__restrict__ lvl) {
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
-         k += (int64_t)gridDim.x * blockDim.x) {
-        int d = 0;
-        if (k > 0) {
-            d = nlev - 1;
-            for (int l = 0; l < nlev; ++l)
-                if (s.p[l][k] != s.p[l][k - 1]) { d = l; break; }
-        }
-        lvl[k] = (uint8_t)d;
-    }
-}
 
 // part[c*(N-1) + l] = level-l fiber holding leaf c*chunk (binary search up the tree).
 struct FptrPtrs {
@@ -412,23 +428,13 @@ sptt_status csf_build_device(const sptt_coo *coo, int32_t root, const int32_t *o
         ~Guard() { if (c) csf_destroy(c); }
     } guard{c};
 
-    // 1. validate indices
-    if (n > 0) {
-        DevBuf err;
-        SPTT_TRY(err.alloc<int32_t>(1, st));
-        SPTT_TRY(fill_zero_launch(err.p, sizeof(int32_t), st));
-        IdxPtrs ip{};
-        for (int m = 0; m < N; ++m) ip.p[m] = coo->inds[m];
-        int64_t d[kMaxModes] = {1, 1, 1, 1, 1};
-        for (int m = 0; m < N; ++m) d[m] = coo->dims[m];
-        check_indices_kernel<<<grid_for(n), kThreads, 0, st>>>(ip, N, n, nullptr, d[0], d[1], d[2], d[3],
-                                                               d[4], err.as<int32_t>());
-        SPTT_CHECK_LAUNCH("check_indices_kernel");
-        int32_t herr = 0;
-        SPTT_CUDA(cudaMemcpyAsync(&herr, err.p, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-        SPTT_CUDA(cudaStreamSynchronize(st));
-        if (herr) return set_error(SPTT_ERR_BAD_ARG, "an index is outside [0, dim) of its mode");
-    }
+    // 1. the indices are checked while the sort keys are built (step 2); the
+    // error word and the duplicate count are read back together (step 4)
+    DevBuf word;  // [0] index error flag (int32), [1] duplicate count (u64)
+    SPTT_TRY(word.alloc<unsigned long long>(2, st));
+    SPTT_TRY(fill_zero_launch(word.p, 2 * sizeof(unsigned long long), st));
+    int32_t *d_err = reinterpret_cast<int32_t *>(word.as<unsigned long long>());
+    unsigned long long *d_ndup = word.as<unsigned long long>() + 1;
 
     // 2. sort positions by level-ordered keys, least significant word first
     const int32_t *lev_src[kMaxModes];
@@ -464,6 +470,9 @@ sptt_status csf_build_device(const sptt_coo *coo, int32_t root, const int32_t *o
                     dec.shift[j] = shift;
                     dec.bits[j] = b;
                 }
+                g.chk[g.nchk] = lev_src[j];
+                g.dim[g.nchk] = c->dims[order[j]];
+                ++g.nchk;
                 if (b == 0) continue;  // a length-1 mode contributes no key bits
                 g.idx[g.nlev] = lev_src[j];
                 g.shift[g.nlev] = shift;
@@ -471,7 +480,7 @@ sptt_status csf_build_device(const sptt_coo *coo, int32_t root, const int32_t *o
                 ++g.nlev;
             }
             build_keys_kernel<<<grid_for(n), kThreads, 0, st>>>(g, first ? nullptr : vals, n, keys_alt,
-                                                                vals_alt);
+                                                                vals_alt, d_err);
             SPTT_CHECK_LAUNCH("build_keys_kernel");
             {
                 uint64_t *t = keys; keys = keys_alt; keys_alt = t;
@@ -508,23 +517,30 @@ sptt_status csf_build_device(const sptt_coo *coo, int32_t root, const int32_t *o
     vA.reset();
     vB.reset();
 
-    // 4. coalesce duplicates
+    // 4. coalesce duplicates. dlev[k] = first level whose index differs from
+    // position k - 1 (N: a duplicate); it gives the fiber starts of every
+    // level and the CSF's per-leaf level flags.
     int64_t u = n;
-    DevBuf flags, scan;
+    DevBuf flags, scan, dlev;
     float *sv = sv_store.as<float>();
     std::vector<DevBuf> c_store(N);
     DevBuf cv_store;
     if (n > 0) {
+        SPTT_TRY(dlev.alloc<uint8_t>(n, st));
+        level_diff_kernel<<<grid_for(n), kThreads, 0, st>>>(s, N, n, dlev.as<uint8_t>(), d_ndup);
+        SPTT_CHECK_LAUNCH("level_diff_kernel");
+        unsigned long long hw[2] = {0, 0};
+        SPTT_CUDA(cudaMemcpyAsync(hw, word.p, sizeof(hw), cudaMemcpyDeviceToHost, st));
+        SPTT_CUDA(cudaStreamSynchronize(st));
+        if ((int32_t)(hw[0] & 0xffffffffu))
+            return set_error(SPTT_ERR_BAD_ARG, "an index is outside [0, dim) of its mode");
         SPTT_TRY(flags.alloc<int32_t>(n, st));
         SPTT_TRY(scan.alloc<int32_t>(n + 1, st));
-        prefix_flags_kernel<<<grid_for(n), kThreads, 0, st>>>(s, N - 1, n, flags.as<int32_t>());
-        SPTT_CHECK_LAUNCH("prefix_flags_kernel");
-        SPTT_TRY(scan_exclusive_i32(flags.as<int32_t>(), scan.as<int32_t>(), n, true, st));
-        int32_t hu = 0;
-        SPTT_CUDA(cudaMemcpyAsync(&hu, scan.as<int32_t>() + n, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-        SPTT_CUDA(cudaStreamSynchronize(st));
-        u = hu;
-        if (u < n) {
+        if (hw[1] > 0) {  // duplicates: sum each run, then the level bytes of the coalesced tensor
+            prefix_flags_kernel<<<grid_for(n), kThreads, 0, st>>>(s, N - 1, n, flags.as<int32_t>());
+            SPTT_CHECK_LAUNCH("prefix_flags_kernel");
+            SPTT_TRY(scan_exclusive_i32(flags.as<int32_t>(), scan.as<int32_t>(), n, true, st));
+            u = n - (int64_t)hw[1];
             DevBuf starts;
             SPTT_TRY(starts.alloc<int32_t>(u + 1, st));
             run_starts_kernel<<<grid_for(n), kThreads, 0, st>>>(scan.as<int32_t>(), n, starts.as<int32_t>());
@@ -540,6 +556,8 @@ sptt_status csf_build_device(const sptt_coo *coo, int32_t root, const int32_t *o
             SPTT_CHECK_LAUNCH("coalesce_kernel");
             for (int l = 0; l < N; ++l) s.p[l] = co.p[l];
             sv = cv_store.as<float>();
+            level_diff_kernel<<<grid_for(u), kThreads, 0, st>>>(s, N, u, dlev.as<uint8_t>(), d_ndup);
+            SPTT_CHECK_LAUNCH("level_diff_kernel");
         }
     }
 
@@ -549,8 +567,8 @@ sptt_status csf_build_device(const sptt_coo *coo, int32_t root, const int32_t *o
     if (u > 0) {
         for (int l = 0; l < N - 1; ++l) {
             SPTT_TRY(fidx[l].alloc<int32_t>(u + 1, st));
-            prefix_flags_kernel<<<grid_for(u), kThreads, 0, st>>>(s, l, u, flags.as<int32_t>());
-            SPTT_CHECK_LAUNCH("prefix_flags_kernel");
+            level_flags_kernel<<<grid_for(u), kThreads, 0, st>>>(dlev.as<uint8_t>(), l, u, flags.as<int32_t>());
+            SPTT_CHECK_LAUNCH("level_flags_kernel");
             SPTT_TRY(scan_exclusive_i32(flags.as<int32_t>(), fidx[l].as<int32_t>(), u, true, st));
         }
         std::vector<int32_t> tot(N, 0);
@@ -578,8 +596,7 @@ sptt_status csf_build_device(const sptt_coo *coo, int32_t root, const int32_t *o
         }
         fill_levels_kernel<<<grid_for(u), kThreads, 0, st>>>(s, ls, N, u);
         SPTT_CHECK_LAUNCH("fill_levels_kernel");
-        leaf_level_kernel<<<grid_for(u), kThreads, 0, st>>>(s, N, u, c->lvl);
-        SPTT_CHECK_LAUNCH("leaf_level_kernel");
+        SPTT_CUDA(cudaMemcpyAsync(c->lvl, dlev.p, (size_t)u, cudaMemcpyDeviceToDevice, st));
         SPTT_CUDA(cudaMemcpyAsync(c->fids[N - 1], s.p[N - 1], u * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
         SPTT_CUDA(cudaMemcpyAsync(c->vals, sv, u * sizeof(float), cudaMemcpyDeviceToDevice, st));
     } else {
