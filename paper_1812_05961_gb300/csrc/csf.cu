@@ -130,12 +130,6 @@ __global__ void level_diff_kernel(IdxPtrs s, int nlev, int64_t n, uint8_t *__res
     if ((threadIdx.x & 31) == 0 && dup) atomicAdd(ndup, dup);
 }
 
-// flags[k] = 1 when position k starts a new fiber of level l (d[k] <= l).
-__global__ void level_flags_kernel(const uint8_t *__restrict__ d, int l, int64_t n, int32_t *__restrict__ flags) {
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
-         k += (int64_t)gridDim.x * blockDim.x)
-        flags[k] = d[k] <= l;
-}
 
 // For each distinct coordinate u starting at k: starts[u] = k.
 __global__ void run_starts_kernel(const int32_t *__restrict__ uid, int64_t n,
@@ -169,15 +163,16 @@ struct LevelScan {
     int32_t *fptr[kMaxModes];
 };
 
-__global__ void fill_levels_kernel(IdxPtrs s, LevelScan ls, int nlev, int64_t n) {
+// Position k starts a level-l fiber when d[k] <= l (then it starts one at
+// every deeper level too); its fiber index is the exclusive scan fidx[l][k].
+__global__ void fill_levels_kernel(IdxPtrs s, LevelScan ls, const uint8_t *__restrict__ d, int nlev, int64_t n) {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
          k += (int64_t)gridDim.x * blockDim.x) {
-        for (int l = 0; l < nlev - 1; ++l) {
+        const int dk = d[k];
+        for (int l = dk; l < nlev - 1; ++l) {
             const int32_t f = ls.fidx[l][k];
-            if (ls.fidx[l][k + 1] != f) {
-                ls.fids[l][f] = s.p[l][k];
-                ls.fptr[l][f] = (l == nlev - 2) ? (int32_t)k : ls.fidx[l + 1][k];
-            }
+            ls.fids[l][f] = s.p[l][k];
+            ls.fptr[l][f] = (l == nlev - 2) ? (int32_t)k : ls.fidx[l + 1][k];
         }
         if (k == 0)
             for (int l = 0; l < nlev - 1; ++l) {
@@ -567,9 +562,7 @@ sptt_status csf_build_device(const sptt_coo *coo, int32_t root, const int32_t *o
     if (u > 0) {
         for (int l = 0; l < N - 1; ++l) {
             SPTT_TRY(fidx[l].alloc<int32_t>(u + 1, st));
-            level_flags_kernel<<<grid_for(u), kThreads, 0, st>>>(dlev.as<uint8_t>(), l, u, flags.as<int32_t>());
-            SPTT_CHECK_LAUNCH("level_flags_kernel");
-            SPTT_TRY(scan_exclusive_i32(flags.as<int32_t>(), fidx[l].as<int32_t>(), u, true, st));
+            SPTT_TRY(scan_exclusive_level(dlev.as<uint8_t>(), l, fidx[l].as<int32_t>(), u, true, st));
         }
         std::vector<int32_t> tot(N, 0);
         for (int l = 0; l < N - 1; ++l)
@@ -594,7 +587,7 @@ sptt_status csf_build_device(const sptt_coo *coo, int32_t root, const int32_t *o
             ls.fids[l] = c->fids[l];
             ls.fptr[l] = c->fptr[l];
         }
-        fill_levels_kernel<<<grid_for(u), kThreads, 0, st>>>(s, ls, N, u);
+        fill_levels_kernel<<<grid_for(u), kThreads, 0, st>>>(s, ls, dlev.as<uint8_t>(), N, u);
         SPTT_CHECK_LAUNCH("fill_levels_kernel");
         SPTT_CUDA(cudaMemcpyAsync(c->lvl, dlev.p, (size_t)u, cudaMemcpyDeviceToDevice, st));
         SPTT_CUDA(cudaMemcpyAsync(c->fids[N - 1], s.p[N - 1], u * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));

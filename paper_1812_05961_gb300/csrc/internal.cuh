@@ -88,6 +88,9 @@ int device_sm_count();
 // Workspace is allocated internally on the stream.
 sptt_status scan_exclusive_i32(const int32_t *in, int32_t *out, int64_t n, bool with_total,
                                cudaStream_t st);
+// The same scan of the predicate d[i] <= level over a byte array.
+sptt_status scan_exclusive_level(const uint8_t *d, int level, int32_t *out, int64_t n, bool with_total,
+                                 cudaStream_t st);
 
 // Stable LSD radix sort of (key, value) pairs by the low `nbits` bits of key,
 // ping-ponging between (keys, vals) and (keys_alt, vals_alt); on return

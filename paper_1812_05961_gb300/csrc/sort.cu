@@ -61,17 +61,28 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int &total) {
 }
 
 // ---------------------------------------------------------------------------
-// Scan
+// Scan (of an int32 array, or of the predicate d[i] <= level over a byte array)
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const int32_t *__restrict__ in,
-                                                                   int64_t n,
+struct InI32 {
+    const int32_t *p;
+    __device__ __forceinline__ int operator()(int64_t i) const { return p[i]; }
+};
+
+struct InLevelLE {
+    const uint8_t *d;
+    int level;
+    __device__ __forceinline__ int operator()(int64_t i) const { return d[i] <= level; }
+};
+
+template <typename In>
+__global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const In in, int64_t n,
                                                                    int32_t *__restrict__ tile_sums) {
     const int64_t base = (int64_t)blockIdx.x * kScanTile;
     int s = 0;
 #pragma unroll
     for (int j = 0; j < kScanItems; ++j) {
         int64_t i = base + j * kScanThreads + threadIdx.x;
-        if (i < n) s += in[i];
+        if (i < n) s += in(i);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
@@ -104,7 +115,8 @@ __global__ void __launch_bounds__(1024) scan_spine_kernel(int32_t *__restrict__ 
     if (threadIdx.x == 0 && total) *total = tot;
 }
 
-__global__ void __launch_bounds__(kScanThreads) scan_down_kernel(const int32_t *in,  // may alias out
+template <typename In>
+__global__ void __launch_bounds__(kScanThreads) scan_down_kernel(const In in,  // may alias out
                                                                  int32_t *out, int64_t n,
                                                                  const int32_t *__restrict__ tile_off) {
     __shared__ int s[kScanTile + kScanTile / 32];
@@ -113,7 +125,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_down_kernel(const int32_t *
     for (int j = 0; j < kScanItems; ++j) {
         int li = j * kScanThreads + threadIdx.x;
         int64_t i = base + li;
-        s[pad_idx(li)] = (i < n) ? in[i] : 0;
+        s[pad_idx(li)] = (i < n) ? in(i) : 0;
     }
     __syncthreads();
     int v[kScanItems];
@@ -254,8 +266,8 @@ __global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(
 
 }  // namespace
 
-sptt_status scan_exclusive_i32(const int32_t *in, int32_t *out, int64_t n, bool with_total,
-                               cudaStream_t st) {
+template <typename In>
+sptt_status scan_exclusive(const In in, int32_t *out, int64_t n, bool with_total, cudaStream_t st) {
     if (n <= 0) {
         if (with_total) return fill_zero_launch(out, sizeof(int32_t), st);
         return SPTT_OK;
@@ -263,13 +275,23 @@ sptt_status scan_exclusive_i32(const int32_t *in, int32_t *out, int64_t n, bool 
     const int64_t ntiles = (n + kScanTile - 1) / kScanTile;
     DevBuf sums;
     SPTT_TRY(sums.alloc<int32_t>(ntiles, st));
-    scan_reduce_kernel<<<(unsigned)ntiles, kScanThreads, 0, st>>>(in, n, sums.as<int32_t>());
+    scan_reduce_kernel<In><<<(unsigned)ntiles, kScanThreads, 0, st>>>(in, n, sums.as<int32_t>());
     SPTT_CHECK_LAUNCH("scan_reduce_kernel");
     scan_spine_kernel<<<1, 1024, 0, st>>>(sums.as<int32_t>(), ntiles, with_total ? out + n : nullptr);
     SPTT_CHECK_LAUNCH("scan_spine_kernel");
-    scan_down_kernel<<<(unsigned)ntiles, kScanThreads, 0, st>>>(in, out, n, sums.as<int32_t>());
+    scan_down_kernel<In><<<(unsigned)ntiles, kScanThreads, 0, st>>>(in, out, n, sums.as<int32_t>());
     SPTT_CHECK_LAUNCH("scan_down_kernel");
     return SPTT_OK;
+}
+
+sptt_status scan_exclusive_i32(const int32_t *in, int32_t *out, int64_t n, bool with_total,
+                               cudaStream_t st) {
+    return scan_exclusive(InI32{in}, out, n, with_total, st);
+}
+
+sptt_status scan_exclusive_level(const uint8_t *d, int level, int32_t *out, int64_t n, bool with_total,
+                                 cudaStream_t st) {
+    return scan_exclusive(InLevelLE{d, level}, out, n, with_total, st);
 }
 
 sptt_status radix_sort_pairs(uint64_t *&keys, uint32_t *&vals, uint64_t *&keys_alt,
