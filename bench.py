@@ -72,6 +72,24 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(x, dist, device):
+    """The maximum of a per-rank number over all ranks (x itself without a
+    process group)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, seconds):
+    """Whole-job throughput in G units/s: every rank's units over the slowest
+    rank's time (replicas: the per-rank work is fixed, so this is weak
+    scaling)."""
+    return units_per_rank * world / seconds / 1e9
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -520,13 +538,9 @@ def ours(args, rank, world, local):
     mttkrp_n = tm["mttkrp"][1] - base_timers["mttkrp"][1]
     routines = {k: (tm[k][0] - base_timers[k][0]) / args.steps for k in tm}
     fit = cpd.fit()[0]
-    if dist:
-        mt = torch.tensor([ms_total], device=dev)
-        dist.all_reduce(mt, op=dist.ReduceOp.MAX)
-        ms_total = float(mt.item())
+    ms_total = max_over_ranks(ms_total, dist, dev)
     ms_step = ms_total / args.steps
-    units = 3 * nnz * R * args.steps * world
-    value = units / (ms_total * 1e-3) / 1e9
+    value = job_rate(3 * nnz * R * args.steps, world, ms_total * 1e-3)
 
     peak, peak_kind = measured_peaks()
     # MTTKRP routine (zero-fill + kernel) per launch; the three roots differ,
@@ -569,13 +583,10 @@ def ours(args, rank, world, local):
                               lambda_out=h_lam, seed=1)
             times.append(time.perf_counter() - t0)
         e2e_t = sum(times) / len(times)
-        if dist:
-            tt = torch.tensor([e2e_t], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            e2e_t = float(tt.item())
+        e2e_t = max_over_ranks(e2e_t, dist, dev)
         h2d = sum(x.numel() * 4 for x in h_inds) + h_vals.numel() * 4
         d2h = sum(d * R * 4 for d in dims) + R * 8 + 8
-        e2e = {"value": 3 * nnz * R * args.e2e_iters * world / e2e_t / 1e9, "unit": UNIT,
+        e2e = {"value": job_rate(3 * nnz * R * args.e2e_iters, world, e2e_t), "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "seconds_per_call": e2e_t, "als_iters_per_call": args.e2e_iters}
         del h_inds, h_vals
