@@ -49,9 +49,12 @@ struct KeyGroup {
     int64_t dim[kMaxModes];
 };
 
+// vals[k] = src, or (when the whole key is this one group) the bits of the
+// value at src, which the sort then carries: the sorted values need no
+// gather through a permutation.
 __global__ void build_keys_kernel(KeyGroup g, const uint32_t *__restrict__ perm, int64_t n,
                                   uint64_t *__restrict__ keys, uint32_t *__restrict__ vals,
-                                  int32_t *__restrict__ err) {
+                                  int32_t *__restrict__ err, const float *__restrict__ carry_vals) {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
          k += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t src = perm ? perm[k] : (uint32_t)k;
@@ -64,7 +67,7 @@ __global__ void build_keys_kernel(KeyGroup g, const uint32_t *__restrict__ perm,
         uint64_t key = 0;
         for (int j = 0; j < g.nlev; ++j) key |= (uint64_t)(uint32_t)g.idx[j][src] << g.shift[j];
         keys[k] = key;
-        vals[k] = src;
+        vals[k] = carry_vals ? __float_as_uint(carry_vals[src]) : src;
     }
 }
 
@@ -80,12 +83,14 @@ struct Decode {
     int bits[kMaxModes];
 };
 
+// perm = NULL: every level is in the key and sorted_bits holds the values.
 __global__ void gather_sorted_kernel(IdxPtrs lev_inds, int nlev, const float *__restrict__ vals,
-                                     const uint32_t *__restrict__ perm, const uint64_t *__restrict__ keys,
-                                     Decode dec, int64_t n, OutPtrs out, float *__restrict__ out_vals) {
+                                     const uint32_t *__restrict__ perm, const uint32_t *__restrict__ sorted_bits,
+                                     const uint64_t *__restrict__ keys, Decode dec, int64_t n, OutPtrs out,
+                                     float *__restrict__ out_vals) {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
          k += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t src = perm[k];
+        const uint32_t src = perm ? perm[k] : 0u;
         const uint64_t key = keys[k];
         for (int l = 0; l < nlev; ++l) {
             if (dec.shift[l] >= 0)
@@ -93,7 +98,7 @@ __global__ void gather_sorted_kernel(IdxPtrs lev_inds, int nlev, const float *__
             else
                 out.p[l][k] = lev_inds.p[l][src];
         }
-        out_vals[k] = vals[src];
+        out_vals[k] = perm ? vals[src] : __uint_as_float(sorted_bits[k]);
     }
 }
 
@@ -436,6 +441,7 @@ sptt_status csf_build_device(const sptt_coo *coo, int32_t root, const int32_t *o
     for (int l = 0; l < N; ++l) lev_src[l] = coo->inds[order[l]];
     DevBuf kA, kB, vA, vB;
     uint32_t *perm = nullptr;
+    uint32_t *sorted_bits = nullptr;  // the values, when the sort carried them
     uint64_t *sorted_keys = nullptr;
     Decode dec{};
     for (int j = 0; j < kMaxModes; ++j) dec.shift[j] = -1;
@@ -474,18 +480,20 @@ sptt_status csf_build_device(const sptt_coo *coo, int32_t root, const int32_t *o
                 shift += b;
                 ++g.nlev;
             }
+            const bool carry = first && last;  // one group: the sort carries the values
             build_keys_kernel<<<grid_for(n), kThreads, 0, st>>>(g, first ? nullptr : vals, n, keys_alt,
-                                                                vals_alt, d_err);
+                                                                vals_alt, d_err, carry ? coo->vals : nullptr);
             SPTT_CHECK_LAUNCH("build_keys_kernel");
             {
                 uint64_t *t = keys; keys = keys_alt; keys_alt = t;
                 uint32_t *tv = vals; vals = vals_alt; vals_alt = tv;
             }
             SPTT_TRY(radix_sort_pairs(keys, vals, keys_alt, vals_alt, n, bits, st));
+            if (carry) sorted_bits = vals;
             first = false;
             l = lo_level;
         }
-        perm = vals;
+        perm = sorted_bits ? nullptr : vals;
         sorted_keys = keys;
     }
 
@@ -503,8 +511,8 @@ sptt_status csf_build_device(const sptt_coo *coo, int32_t root, const int32_t *o
         SPTT_TRY(sv_store.alloc<float>(n, st));
         IdxPtrs lp{};
         for (int l = 0; l < N; ++l) lp.p[l] = lev_src[l];
-        gather_sorted_kernel<<<grid_for(n), kThreads, 0, st>>>(lp, N, coo->vals, perm, sorted_keys, dec, n, so,
-                                                               sv_store.as<float>());
+        gather_sorted_kernel<<<grid_for(n), kThreads, 0, st>>>(lp, N, coo->vals, perm, sorted_bits, sorted_keys,
+                                                               dec, n, so, sv_store.as<float>());
         SPTT_CHECK_LAUNCH("gather_sorted_kernel");
     }
     kA.reset();
