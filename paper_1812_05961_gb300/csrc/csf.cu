@@ -295,17 +295,17 @@ void csf_destroy(sptt_csf *c) {
     if (!c) return;
     cudaDeviceSynchronize();  // no pending work may still read the arrays
     for (int l = 0; l < kMaxModes; ++l) {
-        if (c->fptr[l]) cudaFree(c->fptr[l]);
-        if (c->fids[l]) cudaFree(c->fids[l]);
-        if (c->hslot[l]) cudaFree(c->hslot[l]);
-        if (c->hrow[l]) cudaFree(c->hrow[l]);
+        if (c->fptr[l]) dev_free(c->fptr[l], nullptr);
+        if (c->fids[l]) dev_free(c->fids[l], nullptr);
+        if (c->hslot[l]) dev_free(c->hslot[l], nullptr);
+        if (c->hrow[l]) dev_free(c->hrow[l], nullptr);
     }
-    if (c->vals) cudaFree(c->vals);
-    if (c->lvl) cudaFree(c->lvl);
-    if (c->part) cudaFree(c->part);
-    if (c->hidx) cudaFree(c->hidx);
-    if (c->leafrec) cudaFree(c->leafrec);
-    if (c->err) cudaFree(c->err);
+    if (c->vals) dev_free(c->vals, nullptr);
+    if (c->lvl) dev_free(c->lvl, nullptr);
+    if (c->part) dev_free(c->part, nullptr);
+    if (c->hidx) dev_free(c->hidx, nullptr);
+    if (c->leafrec) dev_free(c->leafrec, nullptr);
+    if (c->err) dev_free(c->err, nullptr);
     delete c;
 }
 
@@ -316,11 +316,13 @@ sptt_status csf_ensure_partition(sptt_csf *c, int32_t chunk, cudaStream_t st) {
     const int64_t nchunks = (nnz + chunk - 1) / chunk;
     if (c->part) {
         SPTT_CUDA(cudaStreamSynchronize(st));
-        cudaFree(c->part);
+        dev_free(c->part, st);
         c->part = nullptr;
     }
-    if (!c->hidx) SPTT_CUDA(cudaMalloc(&c->hidx, (size_t)(c->nfibs[0] + 64) * sizeof(int32_t)));
-    SPTT_CUDA(cudaMalloc(&c->part, (size_t)(nchunks * (N - 1) + 1) * sizeof(int32_t)));
+    if (!c->hidx) SPTT_TRY(dev_alloc(reinterpret_cast<void **>(&c->hidx),
+                       (size_t)(c->nfibs[0] + 64) * sizeof(int32_t), st));
+    SPTT_TRY(dev_alloc(reinterpret_cast<void **>(&c->part),
+                       (size_t)(nchunks * (N - 1) + 1) * sizeof(int32_t), st));
     c->part_chunk = chunk;
     c->part_nchunks = nchunks;
     c->nheavy = 0;
@@ -369,7 +371,8 @@ sptt_status csf_ensure_leafrec(sptt_csf *c, cudaStream_t st) {
     if (c->leafrec) return SPTT_OK;
     const int N = c->nmodes;
     const int64_t nnz = c->nfibs[N - 1];
-    SPTT_CUDA(cudaMalloc(&c->leafrec, (size_t)(nnz + kLeafSlack) * sizeof(uint4)));
+    SPTT_TRY(dev_alloc(reinterpret_cast<void **>(&c->leafrec),
+                       (size_t)(nnz + kLeafSlack) * sizeof(uint4), st));
     SPTT_TRY(fill_zero_launch(c->leafrec + nnz, (size_t)kLeafSlack * sizeof(uint4), st));
     if (nnz > 0) {
         leafrec_kernel<<<grid_for(nnz), kThreads, 0, st>>>(c->fids[N - 1], c->vals, c->lvl, nnz, c->leafrec);
@@ -580,13 +583,19 @@ sptt_status csf_build_device(const sptt_coo *coo, int32_t root, const int32_t *o
         for (int l = 0; l < N - 1; ++l) c->nfibs[l] = tot[l];
     }
     for (int l = 0; l < N - 1; ++l) {
-        SPTT_CUDA(cudaMalloc(&c->fptr[l], (size_t)(c->nfibs[l] + 1 + 64) * sizeof(int32_t)));
-        SPTT_CUDA(cudaMalloc(&c->fids[l], (size_t)(c->nfibs[l] + 64) * sizeof(int32_t)));
+        SPTT_TRY(dev_alloc(reinterpret_cast<void **>(&c->fptr[l]),
+                       (size_t)(c->nfibs[l] + 1 + 64) * sizeof(int32_t), st));
+        SPTT_TRY(dev_alloc(reinterpret_cast<void **>(&c->fids[l]),
+                       (size_t)(c->nfibs[l] + 64) * sizeof(int32_t), st));
     }
-    SPTT_CUDA(cudaMalloc(&c->fids[N - 1], (size_t)(u + kLeafSlack) * sizeof(int32_t)));
-    SPTT_CUDA(cudaMalloc(&c->vals, (size_t)(u + kLeafSlack) * sizeof(float)));
-    SPTT_CUDA(cudaMalloc(&c->lvl, (size_t)(u + kLeafSlack)));
-    SPTT_CUDA(cudaMalloc(&c->err, sizeof(int32_t)));
+    SPTT_TRY(dev_alloc(reinterpret_cast<void **>(&c->fids[N - 1]),
+                       (size_t)(u + kLeafSlack) * sizeof(int32_t), st));
+    SPTT_TRY(dev_alloc(reinterpret_cast<void **>(&c->vals),
+                       (size_t)(u + kLeafSlack) * sizeof(float), st));
+    SPTT_TRY(dev_alloc(reinterpret_cast<void **>(&c->lvl),
+                       (size_t)(u + kLeafSlack), st));
+    SPTT_TRY(dev_alloc(reinterpret_cast<void **>(&c->err),
+                       sizeof(int32_t), st));
     SPTT_TRY(fill_zero_launch(c->err, sizeof(int32_t), st));
     if (u > 0) {
         LevelScan ls{};

@@ -269,8 +269,10 @@ sptt_status ensure_hot(sptt_csf *c, int L, int32_t ld, cudaStream_t st) {
     const int64_t rows = c->dims[c->order[L]];
     const int64_t n = c->nfibs[L];
     if (!c->hslot[L]) {
-        SPTT_CUDA(cudaMalloc(&c->hslot[L], (size_t)(rows + 64) * sizeof(int32_t)));
-        SPTT_CUDA(cudaMalloc(&c->hrow[L], (size_t)(kHotBytes / (4 * (int)sizeof(float)) + 64) * sizeof(int32_t)));
+        SPTT_TRY(dev_alloc(reinterpret_cast<void **>(&c->hslot[L]),
+                       (size_t)(rows + 64) * sizeof(int32_t), st));
+        SPTT_TRY(dev_alloc(reinterpret_cast<void **>(&c->hrow[L]),
+                       (size_t)(kHotBytes / (4 * (int)sizeof(float)) + 64) * sizeof(int32_t), st));
     }
     DevBuf cnt, hist, counter;
     SPTT_TRY(cnt.alloc<int32_t>((size_t)rows, st));
