@@ -265,7 +265,7 @@ def every_gather_model(csf, R, s_f=4):
 # 0, 1, 2); the traffic is dominated by the leaf-record stream, so it is
 # scaled to other sizes by the number of non-zeros.
 NCU_TRAFFIC = {"kernel": "mttkrp_flag_kernel<3, float, 2, 2, 32, 1, 1>", "variant": 7, "nnz": 20_000_000,
-               "bytes": [368.268032e6, 405.6576e6, 405.596928e6]}
+               "bytes": [368.293888e6, 409.197568e6, 409.038336e6]}
 # FP32 FMA peak from the unit counts and the clock: 152 SMs x 128 FP32
 # lanes x 2 flops x 2.07 GHz.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12

@@ -147,10 +147,12 @@ sptt_status sptt_csf_copy_level(const sptt_csf *csf, int32_t level, int32_t *fpt
  *               staged walk with 32-byte row segments (one 256-bit gather per
  *               lane, half the lanes per row) and batches of 2 leaves; 7 and
  *               8 need ld * element size and every non-root factor 32-byte
- *               aligned, and otherwise run as variant 3 / 6. Variant 7 (and
- *               the default, for F32 gathers) reads packed 16-byte leaf
- *               records that the first call builds (16 bytes per non-zero
- *               on the device, kept with the CSF)
+ *               aligned, and otherwise run as variant 3 / 6; 9 = variant 4
+ *               reading packed leaf records. Variants 7 and 9 (and the
+ *               default, for F32 gathers with ld % 8 == 0 and for BF16
+ *               gathers) read packed 16-byte leaf records that the first
+ *               call builds (16 bytes per non-zero on the device, kept with
+ *               the CSF)
  */
 typedef struct {
     int32_t chunk;

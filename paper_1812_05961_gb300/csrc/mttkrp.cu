@@ -31,6 +31,9 @@ namespace {
 using walk::Lanes;
 using walk::lanes_for;
 
+// The 32-byte-segment flag walk on packed leaf records.
+bool wide_variant(int v) { return v == 7; }
+
 // Each CTA takes a contiguous range of chunks; its lane groups interleave
 // within the range, so a group's consecutive chunks are close together and a
 // heavy slice's partial can be carried from one to the next.
@@ -48,6 +51,8 @@ __device__ __forceinline__ ChunkRange cta_chunks(int64_t nchunks, const Lanes &L
     return r;
 }
 
+// PACKED: the walk reads the packed leaf records (with the cache hints of
+// walk.cuh load_rec_pair) instead of the separate leaf arrays.
 template <int NM, typename T, int B, int MINB, int W = 16, bool PIPE = true, bool PACKED = false>
 __global__ void __launch_bounds__(256, MINB) mttkrp_flag_kernel(const walk::Args a) {
     const Lanes L = lanes_for(a.ld, walk::Raw<T, W>::VEC);
@@ -215,12 +220,13 @@ sptt_status launch_nm(const walk::Args &a, int block, int variant, cudaStream_t 
         case 4: kern = mttkrp_flag_kernel<NM, T, 4, 2>; break;
         case 5: kern = mttkrp_flag_kernel<NM, T, 2, 3>; break;
         case 7: kern = mttkrp_flag_kernel<NM, T, 2, 2, 32, true, true>; break;
+        case 9: kern = mttkrp_flag_kernel<NM, T, 4, 2, 16, true, true>; break;
         default: kern = mttkrp_flag_kernel<NM, T, 4, 3, 16, false>; break;
     }
     int per_sm = 0;
     SPTT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, 0));
     if (per_sm < 1) per_sm = 1;
-    const int vec = variant == 7 ? walk::Raw<T, 32>::VEC : walk::Raw<T>::VEC;
+    const int vec = wide_variant(variant) ? walk::Raw<T, 32>::VEC : walk::Raw<T>::VEC;
     const int64_t groups_per_block = (int64_t)(block / 32) * (32 / (a.ld / vec));
     const int64_t need = (a.nchunks + groups_per_block - 1) / groups_per_block;
     const int64_t cap = (int64_t)device_sm_count() * per_sm;
@@ -269,14 +275,14 @@ static bool staged_variant(int v) { return v == 6 || v == 8; }
 // power-law workload (R = 16 and 32): FP32 rows take the 32-byte-segment
 // walk on packed leaf records (the 16-byte walk at 3 CTAs per SM when ld is
 // not a multiple of 8); BF16 rows of up to 32 bytes the pipelined 16-byte
-// walk at 2 CTAs per SM, wider ones the 32-byte-segment walk.
+// walk on packed records at 2 CTAs per SM, wider ones the 32-byte-segment walk.
 int default_variant(int32_t dtype, int32_t ld) {
-    if (dtype == SPTT_BF16) return ld <= 16 ? 4 : 7;
+    if (dtype == SPTT_BF16) return ld <= 16 ? 9 : 7;
     return ld % 8 == 0 ? 7 : 3;
 }
 
 // Variants that read the packed leaf records (sptt_csf::leafrec).
-static bool packed_variant(int v) { return v == 7; }
+static bool packed_variant(int v) { return v == 7 || v == 9; }
 
 sptt_status mttkrp_prepare(sptt_csf *csf, const sptt_sched *sched, cudaStream_t st) {
     const int32_t chunk = (sched && staged_variant(sched->variant)) ? kStageChunk
@@ -295,14 +301,14 @@ sptt_status mttkrp_launch(sptt_csf *csf, const void *const *factors, int32_t dty
     if (nnz == 0) return SPTT_OK;
     int variant = sched ? sched->variant : 0;
     if (variant == 0) variant = default_variant(dtype, ld);
-    if (variant == 7 || variant == 8) {
+    if (wide_variant(variant) || variant == 8) {
         // 32-byte row segments need ld * sizeof(T) and every gathered factor
         // 32-byte aligned; otherwise the 16-byte form of the same walk runs
         const int esz = dtype == SPTT_BF16 ? 2 : 4;
         bool wide_ok = (ld * esz) % 32 == 0;
         for (int l = 1; l < N; ++l)
             wide_ok = wide_ok && reinterpret_cast<uintptr_t>(factors[csf->order[l]]) % 32 == 0;
-        if (!wide_ok) variant = variant == 7 ? 3 : 6;
+        if (!wide_ok) variant = variant == 8 ? 6 : 3;
     }
     const int32_t chunk = staged_variant(variant) ? kStageChunk
                                                   : ((sched && sched->chunk) ? sched->chunk : default_chunk(csf->nfibs[csf->nmodes - 1]));
