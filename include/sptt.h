@@ -148,11 +148,13 @@ sptt_status sptt_csf_copy_level(const sptt_csf *csf, int32_t level, int32_t *fpt
  *               lane, half the lanes per row) and batches of 2 leaves; 7 and
  *               8 need ld * element size and every non-root factor 32-byte
  *               aligned, and otherwise run as variant 3 / 6; 9 = variant 4
- *               reading packed leaf records. Variants 7 and 9 (and the
- *               default, for F32 gathers with ld % 8 == 0 and for BF16
- *               gathers) read packed 16-byte leaf records that the first
- *               call builds (16 bytes per non-zero on the device, kept with
- *               the CSF)
+ *               reading packed leaf records; 10 / 11 = variant 7 / 9 with
+ *               each leaf added straight into its fiber's parent (one more
+ *               multiply per leaf, no per-fiber fold; 10 falls back to 3
+ *               like 7). Variants 7, 9, 10 and 11 (and the default, for F32
+ *               gathers with ld % 8 == 0 and for BF16 gathers) read packed
+ *               16-byte leaf records that the first call builds (16 bytes
+ *               per non-zero on the device, kept with the CSF)
  */
 typedef struct {
     int32_t chunk;
@@ -475,7 +477,10 @@ typedef struct sptt_batch sptt_batch;
  * builds every tensor's CSF per mode, allocates factors and workspace, and
  * lays out global work lists (MTTKRP chunks and row tiles of all tensors back
  * to back). opts: seed (tensor t is initialised from seed + t), use_graph
- * (replay runs from a captured CUDA graph), sched (chunk size). Synchronises.
+ * (replay runs from a captured CUDA graph), sched (chunk size; variant 3
+ * makes the MTTKRP walk read the separate leaf arrays instead of packed
+ * 16-byte leaf records, which take 16 bytes per non-zero more on the
+ * device). Synchronises.
  */
 sptt_status sptt_batch_create(const sptt_coo *coos, int32_t count, int32_t rank, const sptt_opts *opts,
                               sptt_stream stream, sptt_batch **out);

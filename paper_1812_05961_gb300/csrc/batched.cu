@@ -70,6 +70,7 @@ struct BatchArgs {
     unsigned long long *phase_ns;  // [10] wall time CTA 0 spends in each phase (M, P, S, F, N; the barrier
                                    // that ends it included) and, in [5 + phase], its wait in that barrier
     int32_t zero_first;  // clear A_n before its first update (rows without a slice end at 0)
+    int32_t packed;      // the MTTKRP walk reads the packed leaf records (else the separate arrays)
 };
 
 __device__ __forceinline__ uint64_t globaltimer() {
@@ -161,6 +162,17 @@ __device__ __noinline__ void walk_chunk(const walk::Args &w, int64_t c, int col)
     walk::flush_carry(w, col, cy);
 }
 
+// The same walk on the packed leaf records (two leaves per pair of 16-byte
+// loads, loaded past L1; walk.cuh load_rec_pair).
+template <int NM>
+__device__ __noinline__ void walk_chunk_packed(const walk::Args &w, int64_t c, int col) {
+    using Recs = walk::PackedRecsT<true>;
+    const Recs rec{w.leafrec};
+    walk::Carry<4> cy;
+    walk::flag_chunk<NM, float, 4, Recs, 16, false>(w, c, col, cy, rec);
+    walk::flush_carry(w, col, cy);
+}
+
 __device__ __noinline__ void mttkrp_phase(const BatchArgs &a, int n, int gi, int gpw, int col) {
     const int64_t gwarp = (int64_t)(blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = (int64_t)(gridDim.x * blockDim.x) >> 5;
@@ -169,10 +181,18 @@ __device__ __noinline__ void mttkrp_phase(const BatchArgs &a, int n, int gi, int
         const int tt = __ldg(a.chunk_owner[n] + gc);
         const BTensor &T = a.T[tt];
         const int64_t c = gc - __ldg(prefix + tt);
-        switch (T.nmodes) {
-            case 2: walk_chunk<2>(T.w[n], c, col); break;
-            case 3: walk_chunk<3>(T.w[n], c, col); break;
-            default: walk_chunk<4>(T.w[n], c, col); break;
+        if (a.packed) {
+            switch (T.nmodes) {
+                case 2: walk_chunk_packed<2>(T.w[n], c, col); break;
+                case 3: walk_chunk_packed<3>(T.w[n], c, col); break;
+                default: walk_chunk_packed<4>(T.w[n], c, col); break;
+            }
+        } else {
+            switch (T.nmodes) {
+                case 2: walk_chunk<2>(T.w[n], c, col); break;
+                case 3: walk_chunk<3>(T.w[n], c, col); break;
+                default: walk_chunk<4>(T.w[n], c, col); break;
+            }
         }
     }
 }
@@ -398,6 +418,11 @@ void batch_destroy(sptt_batch *b) {
     delete b;
 }
 
+// The batched MTTKRP walk reads the packed leaf records (16 bytes per
+// non-zero more on the device) unless the schedule names variant 3, the same
+// walk on the separate leaf arrays.
+bool batch_packed(const sptt_sched *sched) { return !(sched && sched->variant == 3); }
+
 template <typename T>
 sptt_status batch_alloc(sptt_batch *b, T **p, size_t n, bool zero) {
     SPTT_TRY(dev_alloc_n(p, n, b->st));
@@ -428,6 +453,7 @@ sptt_status launch_batch(sptt_batch *b, int32_t iters) {
     a.skip_block = b->skip_block;
     a.phase_ns = b->d_phase;
     a.zero_first = b->zero_first ? 1 : 0;
+    a.packed = batch_packed(b->has_sched ? &b->sched : nullptr) ? 1 : 0;
     SPTT_TRY(fill_zero_launch(b->d_bar, 2 * sizeof(unsigned), b->st));
     SPTT_TRY(fill_zero_launch(b->d_err, sizeof(int32_t), b->st));
     const int rp = b->rank <= 16 ? 16 : 32;
@@ -495,8 +521,8 @@ extern "C" sptt_status sptt_batch_create(const sptt_coo *coos, int32_t count, in
                 sptt_csf *cs = nullptr;
                 SPTT_TRY(csf_build_device(&dc.coo, m, nullptr, b->st, &cs));
                 b->csfs[(size_t)t * b->max_modes + m] = cs;
-                // the batched walk reads the separate leaf arrays: partition only
                 SPTT_TRY(csf_ensure_partition(cs, (sched && sched->chunk) ? sched->chunk : 128, b->st));
+                if (batch_packed(sched)) SPTT_TRY(csf_ensure_leafrec(cs, b->st));
             }
         }
         int64_t max_slices = 0, max_heavy = 0;
@@ -532,6 +558,7 @@ extern "C" sptt_status sptt_batch_create(const sptt_coo *coos, int32_t count, in
             }
             w.vals = cs->vals;
             w.lvl = cs->lvl;
+            w.leafrec = cs->leafrec;
             w.part = cs->part;
             w.nchunks = cs->part_nchunks;
             w.nnz = cs->nfibs[c.nmodes - 1];

@@ -13,7 +13,7 @@ namespace sptt {
 
 constexpr int kMaxModes = SPTT_MAX_MODES;
 constexpr int kHeavyChunks = 8;
-constexpr int kMaxVariant = 9;  // largest sptt_sched::variant
+constexpr int kMaxVariant = 11;  // largest sptt_sched::variant
 constexpr int kLeafSlack = 512;  // elements past the end of every leaf array (whole-chunk copies)
 constexpr int kNumSMs = 152;  // GB300: 2 dies x 76 SMs (queried at run time where it matters)
 

@@ -31,8 +31,8 @@ namespace {
 using walk::Lanes;
 using walk::lanes_for;
 
-// The 32-byte-segment flag walk on packed leaf records.
-bool wide_variant(int v) { return v == 7; }
+// The 32-byte-segment flag walks on packed leaf records.
+bool wide_variant(int v) { return v == 7 || v == 10; }
 
 // Each CTA takes a contiguous range of chunks; its lane groups interleave
 // within the range, so a group's consecutive chunks are close together and a
@@ -53,7 +53,7 @@ __device__ __forceinline__ ChunkRange cta_chunks(int64_t nchunks, const Lanes &L
 
 // PACKED: the walk reads the packed leaf records (with the cache hints of
 // walk.cuh load_rec_pair) instead of the separate leaf arrays.
-template <int NM, typename T, int B, int MINB, int W = 16, bool PIPE = true, bool PACKED = false>
+template <int NM, typename T, int B, int MINB, int W = 16, bool PIPE = true, bool PACKED = false, bool DIRECT = false>
 __global__ void __launch_bounds__(256, MINB) mttkrp_flag_kernel(const walk::Args a) {
     const Lanes L = lanes_for(a.ld, walk::Raw<T, W>::VEC);
     if (L.idle) return;  // no warp collectives in the walk
@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(256, MINB) mttkrp_flag_kernel(const walk::Args
     if constexpr (PACKED) {
         const walk::PackedRecs rec{a.leafrec};
         for (int64_t c = r.begin; c < r.end; c += r.step)
-            walk::flag_chunk<NM, T, B, walk::PackedRecs, W, PIPE>(a, c, L.col, cy, rec);
+            walk::flag_chunk<NM, T, B, walk::PackedRecs, W, PIPE, DIRECT>(a, c, L.col, cy, rec);
     } else {
         const walk::GlobalRecs rec{a.vals, a.fids[NM - 1], a.lvl};
         for (int64_t c = r.begin; c < r.end; c += r.step)
@@ -221,6 +221,8 @@ sptt_status launch_nm(const walk::Args &a, int block, int variant, cudaStream_t 
         case 5: kern = mttkrp_flag_kernel<NM, T, 2, 3>; break;
         case 7: kern = mttkrp_flag_kernel<NM, T, 2, 2, 32, true, true>; break;
         case 9: kern = mttkrp_flag_kernel<NM, T, 4, 2, 16, true, true>; break;
+        case 10: kern = mttkrp_flag_kernel<NM, T, 2, 2, 32, true, true, true>; break;
+        case 11: kern = mttkrp_flag_kernel<NM, T, 4, 2, 16, true, true, true>; break;
         default: kern = mttkrp_flag_kernel<NM, T, 4, 3, 16, false>; break;
     }
     int per_sm = 0;
@@ -274,15 +276,16 @@ static bool staged_variant(int v) { return v == 6 || v == 8; }
 // The fastest variant measured per gather type and row width on the 3-mode
 // power-law workload (R = 16 and 32): FP32 rows take the 32-byte-segment
 // walk on packed leaf records (the 16-byte walk at 3 CTAs per SM when ld is
-// not a multiple of 8); BF16 rows of up to 32 bytes the pipelined 16-byte
-// walk on packed records at 2 CTAs per SM, wider ones the 32-byte-segment walk.
+// not a multiple of 8); BF16 rows the same walks with leaves added straight
+// into their fiber's parent (walk.cuh DIRECT): 16-byte segments at 2 CTAs
+// per SM for rows of up to 32 bytes, 32-byte segments for wider ones.
 int default_variant(int32_t dtype, int32_t ld) {
-    if (dtype == SPTT_BF16) return ld <= 16 ? 9 : 7;
+    if (dtype == SPTT_BF16) return ld <= 16 ? 11 : 10;
     return ld % 8 == 0 ? 7 : 3;
 }
 
 // Variants that read the packed leaf records (sptt_csf::leafrec).
-static bool packed_variant(int v) { return v == 7 || v == 9; }
+static bool packed_variant(int v) { return v == 7 || v == 9 || v == 10 || v == 11; }
 
 sptt_status mttkrp_prepare(sptt_csf *csf, const sptt_sched *sched, cudaStream_t st) {
     const int32_t chunk = (sched && staged_variant(sched->variant)) ? kStageChunk

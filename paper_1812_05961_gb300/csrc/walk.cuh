@@ -207,6 +207,22 @@ __device__ __forceinline__ void fma_vec(float (&acc)[VEC], const float (&x)[VEC]
     }
 }
 
+// t = x * y element-wise (packed FP32x2 multiplies with 32-byte segments).
+template <int VEC, bool PACKED>
+__device__ __forceinline__ void mul_vec(float (&t)[VEC], const float (&x)[VEC], const float (&y)[VEC]) {
+    if constexpr (PACKED) {
+#pragma unroll
+        for (int i = 0; i < VEC; i += 2) {
+            const float2 r = __fmul2_rn(make_float2(x[i], x[i + 1]), make_float2(y[i], y[i + 1]));
+            t[i] = r.x;
+            t[i + 1] = r.y;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < VEC; ++i) t[i] = __fmul_rn(x[i], y[i]);
+    }
+}
+
 // acc += s * x element-wise (s broadcast).
 template <int VEC, bool PACKED>
 __device__ __forceinline__ void fma_scalar(float (&acc)[VEC], float s, const float (&x)[VEC]) {
@@ -339,16 +355,30 @@ __device__ __forceinline__ void fetch_batch(const Recs &rec, int64_t kb, float (
 // each hint giving about half; L1::evict_last on the factor rows adds nothing.
 // On the separate leaf arrays the same hints cost 13-20 %: their 4- to
 // 16-byte loads reuse the 32-byte sector that an earlier batch brought to L1.
+// SPLIT issues the pair as two 16-byte loads (ptxas 13.0 stops with a
+// segmentation fault on the 32-byte form inside the batched kernel's
+// non-inlined walk).
+template <bool SPLIT = false>
 __device__ __forceinline__ void load_rec_pair(const uint4 *p, uint32_t (&r)[8]) {
-    asm("ld.global.nc.L1::no_allocate.L2::256B.v8.u32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-        : "l"(p));
+    if constexpr (SPLIT) {
+        asm("ld.global.nc.L1::no_allocate.L2::256B.v4.u32 {%0, %1, %2, %3}, [%4];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "l"(p));
+        asm("ld.global.nc.L1::no_allocate.L2::256B.v4.u32 {%0, %1, %2, %3}, [%4];"
+            : "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]) : "l"(p + 1));
+    } else {
+        asm("ld.global.nc.L1::no_allocate.L2::256B.v8.u32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+            : "l"(p));
+    }
 }
 
-struct PackedRecs {
+template <bool SPLIT = false>
+struct PackedRecsT {
     static constexpr bool kPacked = true;
+    static constexpr bool kSplit = SPLIT;
     const uint4 *rec;
 };
+using PackedRecs = PackedRecsT<false>;
 
 // Records of the B leaves from kb on, and nf: for packed records the index
 // of the fiber each leaf opens; otherwise the indices of the B level-LF
@@ -362,7 +392,7 @@ __device__ __forceinline__ void fetch_all(const Recs &rec, const int32_t *fids_l
 #pragma unroll
         for (int h = 0; h < B; h += 2) {
             uint32_t r[8];
-            load_rec_pair(rec.rec + kb + h, r);
+            load_rec_pair<Recs::kSplit>(rec.rec + kb + h, r);
 #pragma unroll
             for (int q = 0; q < 2; ++q) {
                 const int j = h + q;
@@ -389,7 +419,14 @@ __device__ __forceinline__ void fetch_all(const Recs &rec, const int32_t *fids_l
 // the batch, whose ids are consecutive) is requested before any is used.
 // Rows of fibers at higher levels are requested when the fiber opens and
 // used when it closes.
-template <int NM, typename T, int B, typename Recs = GlobalRecs, int W = 16, bool PIPE = true>
+//
+// DIRECT (N >= 3): a leaf adds v * (row of its level-(N-2) fiber) * (leaf row)
+// straight into the fiber's parent accumulator, instead of summing the
+// fiber's leaves first and multiplying by the fiber's row when it closes.
+// One more multiply per leaf, but an opening fiber only switches the row:
+// no fold and no clearing, which in a warp of 16 lane groups runs at almost
+// every leaf (some group nearly always opens a fiber).
+template <int NM, typename T, int B, typename Recs = GlobalRecs, int W = 16, bool PIPE = true, bool DIRECT = false>
 __device__ __forceinline__ void flag_chunk(const Args &a, int64_t c, int col, Carry<Raw<T, W>::VEC> &cy,
                                            const Recs &rec) {
     using Rw = Raw<T, W>;
@@ -412,6 +449,9 @@ __device__ __forceinline__ void flag_chunk(const Args &a, int64_t c, int col, Ca
     Row rowc[NL];  // rows of the open fibers, levels 1..NL-1
 #pragma unroll
     for (int l = 1; l < NL; ++l) rowc[l] = Rw::load(a.fac[l], __ldg(a.fids[l] + f[l]), ld, col);
+    constexpr bool kDirect = DIRECT && LF >= 1;
+    float rf[VEC];  // DIRECT: the open leaf-parent fiber's row, widened
+    if constexpr (kDirect) Rw::widen(rowc[LF], rf);
     bool first_slice = true;
     take_carry<VEC>(a, col, cy, f[0], acc[0]);
 
@@ -477,7 +517,10 @@ __device__ __forceinline__ void flag_chunk(const Args &a, int64_t c, int col, Ca
             if (j >= nvalid) break;
             if ((sm >> j) & 1u) {
                 const int d = (int)((lw[j >> 2] >> (8 * (j & 3))) & 0xffu);
-                if constexpr (LF >= 1) {
+                if constexpr (kDirect) {
+                    ++f[LF];
+                    Rw::widen(nr[j], rf);
+                } else if constexpr (LF >= 1) {
                     fold<T, W>(acc[LF - 1], acc[LF], rowc[LF]);
                     ++f[LF];
                     rowc[LF] = nr[j];
@@ -501,7 +544,13 @@ __device__ __forceinline__ void flag_chunk(const Args &a, int64_t c, int col, Ca
             }
             float xr[VEC];
             Rw::widen(x[j], xr);
-            fma_scalar<VEC, W == 32>(acc[LF], v[j], xr);
+            if constexpr (kDirect) {
+                float t[VEC];
+                mul_vec<VEC, W == 32>(t, rf, xr);
+                fma_scalar<VEC, W == 32>(acc[LF - 1], v[j], t);
+            } else {
+                fma_scalar<VEC, W == 32>(acc[LF], v[j], xr);
+            }
         }
         if (more) {
 #pragma unroll
@@ -517,7 +566,7 @@ __device__ __forceinline__ void flag_chunk(const Args &a, int64_t c, int col, Ca
     // chunk end: fold the open fibers; the open slice's partial is added
     // (or held back when the slice is heavy)
 #pragma unroll
-    for (int l = LF; l >= 1; --l) fold<T, W>(acc[l - 1], acc[l], rowc[l]);
+    for (int l = kDirect ? LF - 1 : LF; l >= 1; --l) fold<T, W>(acc[l - 1], acc[l], rowc[l]);
     end_chunk<VEC>(a, col, cy, f[0], acc[0]);
 }
 

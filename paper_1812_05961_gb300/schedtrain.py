@@ -62,9 +62,10 @@ def train(ds: Dataset, steps: int = 2000, lr: float = 3e-3, seed: int = 0, devic
 
 def default_index(rank: int = 16, dtype: int = SPTT_F32, nnz: int = 1 << 30, sms: int = 152) -> int:
     """Index of the candidate closest to the library's default schedule:
-    ascending order, the default variant for the gather type and rank, and
-    the default chunk (128, halved while nnz / chunk < 256 per SM; the
-    candidates have 64 and 128)."""
+    ascending order, the default variant for the gather type and rank (for
+    BF16 gathers the candidate with the same walk shape: 4 for the default
+    11, 7 for the default 10), and the default chunk (128, halved while
+    nnz / chunk < 256 per SM; the candidates have 64 and 128)."""
     ld = (rank + 7) // 8 * 8
     variant = (4 if ld <= 16 else 7) if dtype != SPTT_F32 else 7
     chunk = 128

@@ -76,6 +76,24 @@ def test_batched_large_skewed_tensors_match_single_path(R, cuda_device):
             assert torch.linalg.norm(Fb - Fc) <= 1e-3 * max(1.0, float(torch.linalg.norm(Fc)))
 
 
+def test_batched_record_sources_agree(cuda_device):
+    # the MTTKRP walk on packed leaf records (default) and on the separate
+    # leaf arrays (schedule variant 3) are the same sums in the same order
+    items = _batch(16, seed=13, dim_hi=2000, nnz_hi=40000)
+    R = 16
+    runs = []
+    for sched in (None, (0, 0, 3, 0)):
+        kw = {} if sched is None else {"sched": sched}
+        b = sptt.Batch([(d, i, v) for d, i, v, _ in items], R, seed=21, **kw).init()
+        b.run(4)
+        runs.append(b)
+    for t in range(len(items)):
+        np.testing.assert_allclose(runs[0].fit_history(t), runs[1].fit_history(t), atol=1e-6, err_msg="tensor %d" % t)
+        for m in range(len(items[t][0])):
+            Fa, Fb = runs[0].factor(t, m), runs[1].factor(t, m)
+            assert torch.linalg.norm(Fa - Fb) <= 1e-4 * max(1.0, float(torch.linalg.norm(Fb)))
+
+
 def test_batched_graph_replay(cuda_device):
     items = _batch(12, seed=9)
     R = 8
