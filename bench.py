@@ -62,6 +62,8 @@ def parse():
     p.add_argument("--sched-heldout", type=int, default=40)
     p.add_argument("--variant", type=int, default=0, help="MTTKRP kernel variant for every mode (0 = default)")
     p.add_argument("--chunk", type=int, default=0, help="MTTKRP chunk size (0 = default)")
+    p.add_argument("--precision", default="fp32", choices=["fp32", "bf16"],
+                   help="factor gathers of the timed CP-ALS iterations (bf16: FP32 accumulation, FP64 solve)")
     return p.parse_args()
 
 
@@ -266,6 +268,9 @@ def every_gather_model(csf, R, s_f=4):
 # scaled to other sizes by the number of non-zeros.
 NCU_TRAFFIC = {"kernel": "mttkrp_flag_kernel<3, float, 2, 2, 32, 1, 1>", "variant": 7, "nnz": 20_000_000,
                "bytes": [368.293888e6, 409.197568e6, 409.038336e6]}
+# The same for the default BF16-gather kernel (variant 11).
+NCU_TRAFFIC_BF16 = {"kernel": "mttkrp_flag_kernel<3, __nv_bfloat16, 4, 2, 16, 1, 1, 1>", "variant": 11,
+                    "nnz": 20_000_000, "bytes": [367.383296e6, 360.050944e6, 358.682368e6]}
 # FP32 FMA peak from the unit counts and the clock: 152 SMs x 128 FP32
 # lanes x 2 flops x 2.07 GHz.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
@@ -501,15 +506,18 @@ def ours(args, rank, world, local):
 
     # CSFs (one per root) are built inside the handle; build them here too for the byte model
     csfs = [sptt.Csf(dims, t.inds, t.vals, r) for r in range(3)]
-    bytes_per = [byte_model(c, dims, R, distinct) for c in csfs]
+    bf16 = args.precision == "bf16"
+    s_f = 2 if bf16 else 4
+    bytes_per = [byte_model(c, dims, R, distinct, s_f) for c in csfs]
     flops_per = [flop_model(c, R) for c in csfs]
-    gather_per = [every_gather_model(c, R) for c in csfs]
+    gather_per = [every_gather_model(c, R, s_f) for c in csfs]
     nfibs = [c.nfibs for c in csfs]
     del csfs
 
     t_build = time.time()
     sched = None if (args.variant == 0 and args.chunk == 0) else (args.chunk, 256, args.variant, 0)
-    cpd = sptt.Cpd(dims, t.inds, t.vals, R, seed=1, profile=1, sched=sched)
+    cpd = sptt.Cpd(dims, t.inds, t.vals, R, seed=1, profile=1, sched=sched,
+                   precision=sptt.SPTT_BF16 if bf16 else sptt.SPTT_F32)
     t_build = time.time() - t_build
     cpd.init()
     stream = torch.cuda.current_stream()
@@ -549,14 +557,15 @@ def ours(args, rank, world, local):
     achieved = alg_bytes / (mttkrp_ms * 1e-3) / 1e9
     # measured traffic applies while the timed kernel is the captured one
     traffic = None
-    if sched is None and R in (16,) and len(dims) == 3:
-        traffic = sum(NCU_TRAFFIC["bytes"]) / 3 * nnz / NCU_TRAFFIC["nnz"]
+    ncu = NCU_TRAFFIC_BF16 if bf16 else NCU_TRAFFIC
+    if sched is None and R in (16,) and len(dims) == 3 and ncu is not None:
+        traffic = sum(ncu["bytes"]) / 3 * nnz / ncu["nnz"]
     flops_s = sum(flops_per) * args.steps / (mttkrp_ms * 1e-3) / 1e12
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "traffic_source": None if traffic is None else
                 "ncu dram__bytes_read.sum + dram__bytes_write.sum of %s at %d nnz, scaled by nnz (mean of the 3 roots)"
-                % (NCU_TRAFFIC["kernel"], NCU_TRAFFIC["nnz"]),
+                % (ncu["kernel"], ncu["nnz"]),
                 "every_gather_bytes_per_launch": [int(b) for b in gather_per],
                 "fp32_fma": {"achieved_tflops": flops_s, "peak_tflops": FP32_PEAK_TFLOPS,
                              "frac": flops_s / FP32_PEAK_TFLOPS, "peak_kind": "derived from unit counts and clock"},
@@ -574,13 +583,14 @@ def ours(args, rank, world, local):
         h_vals = t.vals.cpu().pin_memory()
         h_out = [torch.empty(d, R).pin_memory() for d in dims]
         h_lam = torch.empty(R, dtype=torch.float64).pin_memory()
-        sptt.sptt_cpd_als(dims, h_inds, h_vals, R, 1, factors_out=h_out, lambda_out=h_lam, seed=1)
+        prec = sptt.SPTT_BF16 if bf16 else sptt.SPTT_F32
+        sptt.sptt_cpd_als(dims, h_inds, h_vals, R, 1, factors_out=h_out, lambda_out=h_lam, seed=1, precision=prec)
         torch.cuda.synchronize()
         times = []
         for _ in range(args.e2e_steps):
             t0 = time.perf_counter()
             sptt.sptt_cpd_als(dims, h_inds, h_vals, R, args.e2e_iters, factors_out=h_out,
-                              lambda_out=h_lam, seed=1)
+                              lambda_out=h_lam, seed=1, precision=prec)
             times.append(time.perf_counter() - t0)
         e2e_t = sum(times) / len(times)
         e2e_t = max_over_ranks(e2e_t, dist, dev)
@@ -588,7 +598,8 @@ def ours(args, rank, world, local):
         d2h = sum(d * R * 4 for d in dims) + R * 8 + 8
         e2e = {"value": job_rate(3 * nnz * R * args.e2e_iters, world, e2e_t), "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-               "seconds_per_call": e2e_t, "als_iters_per_call": args.e2e_iters}
+               "seconds_per_call": e2e_t, "als_iters_per_call": args.e2e_iters,
+               "fp32_refinement_sweeps_per_call": 1 if bf16 else 0}
         del h_inds, h_vals
 
     extras = {}
@@ -645,8 +656,9 @@ def ours(args, rank, world, local):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16+f32" if bf16 else "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "rank": R, "step": "one CP-ALS iteration (3 mode updates + fit)",
+                       "factor_gathers": "bf16 (fp32 accumulate, fp64 solve)" if bf16 else "fp32",
                        "mttkrp_sched": "default" if sched is None else list(sched),
                        "l2": "inputs larger than L2 (CSF about 0.8 GB per mode)",
                        "parallelism": "replicas" if world > 1 else "single",
