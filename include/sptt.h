@@ -477,10 +477,13 @@ typedef struct sptt_batch sptt_batch;
  * builds every tensor's CSF per mode, allocates factors and workspace, and
  * lays out global work lists (MTTKRP chunks and row tiles of all tensors back
  * to back). opts: seed (tensor t is initialised from seed + t), use_graph
- * (replay runs from a captured CUDA graph), sched (chunk size; variant 3
- * makes the MTTKRP walk read the separate leaf arrays instead of packed
- * 16-byte leaf records, which take 16 bytes per non-zero more on the
- * device). Synchronises.
+ * (replay runs from a captured CUDA graph), sched (chunk size; the MTTKRP
+ * walk reads packed 16-byte leaf records, 16 bytes per non-zero more on the
+ * device, and with the factor row width a multiple of 8 floats (rank 8, 16,
+ * 32) gathers 32-byte row segments in a build of the kernel with one CTA per
+ * SM; variant 4 keeps 16-byte segments at two CTAs per SM, variant 3 also
+ * reads the separate leaf arrays instead of the packed records).
+ * Synchronises.
  */
 sptt_status sptt_batch_create(const sptt_coo *coos, int32_t count, int32_t rank, const sptt_opts *opts,
                               sptt_stream stream, sptt_batch **out);

@@ -70,7 +70,7 @@ struct BatchArgs {
     unsigned long long *phase_ns;  // [10] wall time CTA 0 spends in each phase (M, P, S, F, N; the barrier
                                    // that ends it included) and, in [5 + phase], its wait in that barrier
     int32_t zero_first;  // clear A_n before its first update (rows without a slice end at 0)
-    int32_t packed;      // the MTTKRP walk reads the packed leaf records (else the separate arrays)
+    int32_t walk;        // MTTKRP walk (batch_walk): 0 leaf arrays, 1 packed records, 2 packed, 32-byte rows
 };
 
 __device__ __forceinline__ uint64_t globaltimer() {
@@ -173,6 +173,38 @@ __device__ __noinline__ void walk_chunk_packed(const walk::Args &w, int64_t c, i
     walk::flush_carry(w, col, cy);
 }
 
+// The walk with 32-byte row segments (2 lanes per R = 16 row), batches of 2
+// leaves, software-pipelined, on the packed records; its row and record
+// loads are split in 16-byte halves (walk.cuh SPLIT). It needs more
+// registers than a CTA of the 2-per-SM build has, so it runs in the
+// 1-CTA-per-SM build (batch_walk).
+template <int NM>
+__device__ __noinline__ void walk_chunk_wide(const walk::Args &w, int64_t c, int col) {
+    using Recs = walk::PackedRecsT<true>;
+    const Recs rec{w.leafrec};
+    walk::Carry<8> cy;
+    walk::flag_chunk<NM, float, 2, Recs, 32, true>(w, c, col, cy, rec);
+    walk::flush_carry(w, col, cy);
+}
+
+__device__ __noinline__ void mttkrp_phase_wide(const BatchArgs &a, int n) {
+    const walk::Lanes L = walk::lanes_for(a.ld, 8);
+    if (L.idle) return;
+    const int64_t gwarp = (int64_t)(blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = (int64_t)(gridDim.x * blockDim.x) >> 5;
+    const int64_t *prefix = a.chunk_prefix[n];
+    for (int64_t gc = gwarp * L.gpw + L.gi; gc < a.total_chunks[n]; gc += nwarps * L.gpw) {
+        const int tt = __ldg(a.chunk_owner[n] + gc);
+        const BTensor &T = a.T[tt];
+        const int64_t c = gc - __ldg(prefix + tt);
+        switch (T.nmodes) {
+            case 2: walk_chunk_wide<2>(T.w[n], c, L.col); break;
+            case 3: walk_chunk_wide<3>(T.w[n], c, L.col); break;
+            default: walk_chunk_wide<4>(T.w[n], c, L.col); break;
+        }
+    }
+}
+
 __device__ __noinline__ void mttkrp_phase(const BatchArgs &a, int n, int gi, int gpw, int col) {
     const int64_t gwarp = (int64_t)(blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = (int64_t)(gridDim.x * blockDim.x) >> 5;
@@ -181,7 +213,7 @@ __device__ __noinline__ void mttkrp_phase(const BatchArgs &a, int n, int gi, int
         const int tt = __ldg(a.chunk_owner[n] + gc);
         const BTensor &T = a.T[tt];
         const int64_t c = gc - __ldg(prefix + tt);
-        if (a.packed) {
+        if (a.walk == 1) {
             switch (T.nmodes) {
                 case 2: walk_chunk_packed<2>(T.w[n], c, col); break;
                 case 3: walk_chunk_packed<3>(T.w[n], c, col); break;
@@ -277,8 +309,8 @@ __device__ __noinline__ void normalize_phase(const BatchArgs &a, int n) {
     }
 }
 
-template <int RP>
-__global__ void __launch_bounds__(kBThreads, 2) batched_cpals_kernel(const BatchArgs a) {
+template <int RP, int MINB = 2>
+__global__ void __launch_bounds__(kBThreads, MINB) batched_cpals_kernel(const BatchArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     double *prep_sm = reinterpret_cast<double *>(smem);
     dense::SolveTile<RP> &solve_sm = *reinterpret_cast<dense::SolveTile<RP> *>(smem);
@@ -302,7 +334,8 @@ __global__ void __launch_bounds__(kBThreads, 2) batched_cpals_kernel(const Batch
     for (int it = 0; it < a.iters; ++it) {
         for (int n = 0; n < a.max_modes; ++n) {
             // M: MTTKRP of mode n over the global chunk list
-            if (gi < gpw) mttkrp_phase(a, n, gi, gpw, col);
+            if (a.walk == 2) mttkrp_phase_wide(a, n);
+            else if (gi < gpw) mttkrp_phase(a, n, gi, gpw, col);
             if (!grid_barrier(a, 0)) return;
             phase_done(0);
             // P: normal equations per tensor
@@ -379,6 +412,8 @@ struct sptt_batch {
     sptt_opts opts{};
     sptt_sched sched{};
     bool has_sched = false;
+    int walk = 1;  // MTTKRP walk (batch_walk)
+    int minb = 2;  // CTAs per SM the kernel is built for (1 for the 32-byte walk)
     cudaStream_t st = nullptr;
     std::vector<sptt_csf *> csfs;       // count * max_modes (null where absent)
     std::vector<BTensor> host;          // descriptors as copied to the device
@@ -419,9 +454,25 @@ void batch_destroy(sptt_batch *b) {
 }
 
 // The batched MTTKRP walk reads the packed leaf records (16 bytes per
-// non-zero more on the device) unless the schedule names variant 3, the same
-// walk on the separate leaf arrays.
+// non-zero more on the device) unless the schedule names variant 3 (the
+// 16-byte walk on the separate leaf arrays). With ld a multiple of 8 (R = 8,
+// 16, 32) it is the 32-byte-segment walk in the 1-CTA-per-SM build of the
+// kernel, unless the schedule names variant 4 (the 16-byte walk on packed
+// records, 2 CTAs per SM). Measured on the 512-tensor batch at R = 16: 0.43 s
+// per run against 0.49 s for the 16-byte walk (its MTTKRP phase is 23 %
+// faster, the other phases slower with half the CTAs).
 bool batch_packed(const sptt_sched *sched) { return !(sched && sched->variant == 3); }
+int batch_walk(const sptt_sched *sched, int32_t ld) {
+    if (!batch_packed(sched)) return 0;
+    if (ld % 8 == 0 && !(sched && sched->variant == 4)) return 2;
+    return 1;
+}
+
+using BatchKernel = void (*)(const BatchArgs);
+BatchKernel batch_kernel(int rp, int minb) {
+    if (minb == 1) return rp == 16 ? batched_cpals_kernel<16, 1> : batched_cpals_kernel<32, 1>;
+    return rp == 16 ? batched_cpals_kernel<16, 2> : batched_cpals_kernel<32, 2>;
+}
 
 template <typename T>
 sptt_status batch_alloc(sptt_batch *b, T **p, size_t n, bool zero) {
@@ -453,7 +504,7 @@ sptt_status launch_batch(sptt_batch *b, int32_t iters) {
     a.skip_block = b->skip_block;
     a.phase_ns = b->d_phase;
     a.zero_first = b->zero_first ? 1 : 0;
-    a.packed = batch_packed(b->has_sched ? &b->sched : nullptr) ? 1 : 0;
+    a.walk = b->walk;
     SPTT_TRY(fill_zero_launch(b->d_bar, 2 * sizeof(unsigned), b->st));
     SPTT_TRY(fill_zero_launch(b->d_err, sizeof(int32_t), b->st));
     const int rp = b->rank <= 16 ? 16 : 32;
@@ -468,8 +519,7 @@ sptt_status launch_batch(sptt_batch *b, int32_t iters) {
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (rp == 16) SPTT_CUDA(cudaLaunchKernelEx(&cfg, batched_cpals_kernel<16>, a));
-    else SPTT_CUDA(cudaLaunchKernelEx(&cfg, batched_cpals_kernel<32>, a));
+    SPTT_CUDA(cudaLaunchKernelEx(&cfg, batch_kernel(rp, b->minb), a));
     count_launch();
     return SPTT_OK;
 }
@@ -617,7 +667,14 @@ extern "C" sptt_status sptt_batch_create(const sptt_coo *coos, int32_t count, in
     // a grid that is fully resident (cooperative launch)
     const int rp = rank <= 16 ? 16 : 32;
     const size_t smem = batched_smem_bytes(rank, rp);
-    auto kern = rp == 16 ? batched_cpals_kernel<16> : batched_cpals_kernel<32>;
+    b->walk = batch_walk(sched, b->ld);
+    if (b->walk == 2) {  // 32-byte row loads need 32-byte aligned factors
+        for (int t = 0; t < count; ++t)
+            for (int m = 0; m < b->host[t].nmodes; ++m)
+                if (reinterpret_cast<uintptr_t>(b->host[t].A[m]) % 32) b->walk = 1;
+    }
+    b->minb = b->walk == 2 ? 1 : 2;
+    auto kern = batch_kernel(rp, b->minb);
     SPTT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     SPTT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBThreads, smem));

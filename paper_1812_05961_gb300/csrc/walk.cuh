@@ -80,7 +80,9 @@ struct Seg {
     uint32_t w[W / 4];
 };
 
-template <typename T, int W = 16>
+// SPLIT: a 32-byte segment is loaded as two 16-byte loads (for the batched
+// kernel's non-inlined walk, where ptxas 13.0 fails on the 32-byte form).
+template <typename T, int W = 16, bool SPLIT = false>
 struct Raw {
     static_assert(W == 16 || W == 32, "16- or 32-byte row segments");
     static constexpr int VEC = W / (int)sizeof(T);
@@ -91,6 +93,11 @@ struct Raw {
         if constexpr (W == 16) {
             const uint4 u = __ldg(reinterpret_cast<const uint4 *>(p));
             r.w[0] = u.x; r.w[1] = u.y; r.w[2] = u.z; r.w[3] = u.w;
+        } else if constexpr (SPLIT) {
+            const uint4 u0 = __ldg(reinterpret_cast<const uint4 *>(p));
+            const uint4 u1 = __ldg(reinterpret_cast<const uint4 *>(p) + 1);
+            r.w[0] = u0.x; r.w[1] = u0.y; r.w[2] = u0.z; r.w[3] = u0.w;
+            r.w[4] = u1.x; r.w[5] = u1.y; r.w[6] = u1.z; r.w[7] = u1.w;
         } else {
             asm("ld.global.nc.v8.u32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
                 : "=r"(r.w[0]), "=r"(r.w[1]), "=r"(r.w[2]), "=r"(r.w[3]),
@@ -256,6 +263,7 @@ __device__ __forceinline__ void fold(float (&parent)[Raw<T, W>::VEC], float (&ch
 // from: global memory, or a copy staged in shared memory.
 struct GlobalRecs {
     static constexpr bool kPacked = false;
+    static constexpr bool kSplit = false;
     const float *vals;
     const int32_t *idx;
     const uint8_t *lvl;
@@ -272,6 +280,7 @@ struct GlobalRecs {
 
 struct SharedRecs {  // shared-memory addresses of the chunk's copy; k0 = the chunk's first leaf
     static constexpr bool kPacked = false;
+    static constexpr bool kSplit = false;
     uint32_t sv, si, sl;
     int64_t k0;
     __device__ __forceinline__ float4 v4(int64_t k) const {
@@ -429,7 +438,7 @@ __device__ __forceinline__ void fetch_all(const Recs &rec, const int32_t *fids_l
 template <int NM, typename T, int B, typename Recs = GlobalRecs, int W = 16, bool PIPE = true, bool DIRECT = false>
 __device__ __forceinline__ void flag_chunk(const Args &a, int64_t c, int col, Carry<Raw<T, W>::VEC> &cy,
                                            const Recs &rec) {
-    using Rw = Raw<T, W>;
+    using Rw = Raw<T, W, Recs::kSplit>;
     using Row = typename Rw::Row;
     constexpr int VEC = Rw::VEC;
     constexpr int NL = NM - 1;  // accumulator levels 0..NM-2

@@ -77,21 +77,27 @@ def test_batched_large_skewed_tensors_match_single_path(R, cuda_device):
 
 
 def test_batched_record_sources_agree(cuda_device):
-    # the MTTKRP walk on packed leaf records (default) and on the separate
-    # leaf arrays (schedule variant 3) are the same sums in the same order
+    # the batched MTTKRP walks - 32-byte rows on packed leaf records in the
+    # 1-CTA-per-SM kernel (the default at R = 16), 16-byte rows on packed
+    # records (schedule variant 4) and on the separate leaf arrays (variant
+    # 3) - add the same products in the same order per output element; only
+    # the order of the split-slice atomics differs
     items = _batch(16, seed=13, dim_hi=2000, nnz_hi=40000)
     R = 16
     runs = []
-    for sched in (None, (0, 0, 3, 0)):
+    for sched in (None, (0, 0, 4, 0), (0, 0, 3, 0)):
         kw = {} if sched is None else {"sched": sched}
         b = sptt.Batch([(d, i, v) for d, i, v, _ in items], R, seed=21, **kw).init()
         b.run(4)
         runs.append(b)
-    for t in range(len(items)):
-        np.testing.assert_allclose(runs[0].fit_history(t), runs[1].fit_history(t), atol=1e-6, err_msg="tensor %d" % t)
-        for m in range(len(items[t][0])):
-            Fa, Fb = runs[0].factor(t, m), runs[1].factor(t, m)
-            assert torch.linalg.norm(Fa - Fb) <= 1e-4 * max(1.0, float(torch.linalg.norm(Fb)))
+    assert runs[0].info()[0] * 2 == runs[1].info()[0] == runs[2].info()[0]  # 1 against 2 CTAs per SM
+    for other in runs[1:]:
+        for t in range(len(items)):
+            np.testing.assert_allclose(runs[0].fit_history(t), other.fit_history(t), atol=1e-6,
+                                       err_msg="tensor %d" % t)
+            for m in range(len(items[t][0])):
+                Fa, Fb = runs[0].factor(t, m), other.factor(t, m)
+                assert torch.linalg.norm(Fa - Fb) <= 1e-4 * max(1.0, float(torch.linalg.norm(Fb)))
 
 
 def test_batched_graph_replay(cuda_device):
