@@ -26,6 +26,20 @@ inline unsigned grid_for(int64_t n, int threads = kThreads) {
     return (unsigned)(g < 1 ? 1 : g);
 }
 
+// The streaming passes over the non-zeros take kItems elements per thread,
+// blockDim apart (each of a warp's loads stays coalesced), and issue all of
+// their loads before the first use, so a thread keeps several requests in
+// flight instead of one dependent chain.
+constexpr int kItems = 4;
+inline unsigned grid_items(int64_t n) {
+    const int64_t per = (int64_t)kThreads * kItems;
+    int64_t g = (n + per - 1) / per;
+    return (unsigned)(g < 1 ? 1 : g);
+}
+__device__ __forceinline__ int64_t item_index(int j) {
+    return (int64_t)blockIdx.x * (kThreads * kItems) + (int64_t)j * kThreads + threadIdx.x;
+}
+
 inline int bits_for(int64_t dim) {  // bits to hold 0..dim-1
     int b = 0;
     while (b < 63 && (int64_t(1) << b) < dim) ++b;
@@ -41,34 +55,50 @@ struct IdxPtrs {
 // key bits) is checked against its mode length on the way: each level
 // belongs to one group, so every index of the tensor is checked once.
 struct KeyGroup {
-    int nlev;
-    const int32_t *idx[kMaxModes];
-    int shift[kMaxModes];
-    int nchk;
+    int nchk;                        // the group's levels, length-1 modes included
     const int32_t *chk[kMaxModes];
     int64_t dim[kMaxModes];
+    int shift[kMaxModes];            // bit position in the key, or -1 (a length-1 mode adds no bits)
 };
 
 // vals[k] = src, or (when the whole key is this one group) the bits of the
 // value at src, which the sort then carries: the sorted values need no
 // gather through a permutation.
-__global__ void build_keys_kernel(KeyGroup g, const uint32_t *__restrict__ perm, int64_t n,
-                                  uint64_t *__restrict__ keys, uint32_t *__restrict__ vals,
-                                  int32_t *__restrict__ err, const float *__restrict__ carry_vals) {
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
-         k += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t src = perm ? perm[k] : (uint32_t)k;
-        bool bad = false;
-        for (int j = 0; j < g.nchk; ++j) {
-            const int32_t x = g.chk[j][src];
-            bad |= x < 0 || (int64_t)x >= g.dim[j];
-        }
-        if (bad) atomicOr(err, 1);
-        uint64_t key = 0;
-        for (int j = 0; j < g.nlev; ++j) key |= (uint64_t)(uint32_t)g.idx[j][src] << g.shift[j];
-        keys[k] = key;
-        vals[k] = carry_vals ? __float_as_uint(carry_vals[src]) : src;
+__global__ void __launch_bounds__(kThreads) build_keys_kernel(KeyGroup g, const uint32_t *__restrict__ perm, int64_t n,
+                                                              uint64_t *__restrict__ keys, uint32_t *__restrict__ vals,
+                                                              int32_t *__restrict__ err,
+                                                              const float *__restrict__ carry_vals) {
+    uint32_t src[kItems];
+#pragma unroll
+    for (int j = 0; j < kItems; ++j) {
+        const int64_t k = item_index(j);
+        src[j] = k < n ? (perm ? perm[k] : (uint32_t)k) : 0u;
     }
+    int32_t x[kItems][kMaxModes];
+    uint32_t cv[kItems];
+#pragma unroll
+    for (int m = 0; m < kMaxModes; ++m)
+#pragma unroll
+        for (int j = 0; j < kItems; ++j)
+            x[j][m] = (m < g.nchk && item_index(j) < n) ? g.chk[m][src[j]] : 0;
+#pragma unroll
+    for (int j = 0; j < kItems; ++j) cv[j] = (carry_vals && item_index(j) < n) ? __float_as_uint(carry_vals[src[j]]) : 0u;
+    bool bad = false;
+#pragma unroll
+    for (int j = 0; j < kItems; ++j) {
+        const int64_t k = item_index(j);
+        if (k >= n) continue;
+        uint64_t key = 0;
+#pragma unroll
+        for (int m = 0; m < kMaxModes; ++m) {
+            if (m >= g.nchk) break;
+            bad |= x[j][m] < 0 || (int64_t)x[j][m] >= g.dim[m];
+            if (g.shift[m] >= 0) key |= (uint64_t)(uint32_t)x[j][m] << g.shift[m];
+        }
+        keys[k] = key;
+        vals[k] = carry_vals ? cv[j] : src[j];
+    }
+    if (bad) atomicOr(err, 1);
 }
 
 struct OutPtrs {
@@ -84,21 +114,43 @@ struct Decode {
 };
 
 // perm = NULL: every level is in the key and sorted_bits holds the values.
-__global__ void gather_sorted_kernel(IdxPtrs lev_inds, int nlev, const float *__restrict__ vals,
-                                     const uint32_t *__restrict__ perm, const uint32_t *__restrict__ sorted_bits,
-                                     const uint64_t *__restrict__ keys, Decode dec, int64_t n, OutPtrs out,
-                                     float *__restrict__ out_vals) {
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
-         k += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t src = perm ? perm[k] : 0u;
-        const uint64_t key = keys[k];
-        for (int l = 0; l < nlev; ++l) {
-            if (dec.shift[l] >= 0)
-                out.p[l][k] = dec.bits[l] ? (int32_t)((key >> dec.shift[l]) & ((uint64_t(1) << dec.bits[l]) - 1)) : 0;
-            else
-                out.p[l][k] = lev_inds.p[l][src];
+__global__ void __launch_bounds__(kThreads) gather_sorted_kernel(IdxPtrs lev_inds, int nlev, const float *__restrict__ vals,
+                                                                 const uint32_t *__restrict__ perm,
+                                                                 const uint32_t *__restrict__ sorted_bits,
+                                                                 const uint64_t *__restrict__ keys, Decode dec, int64_t n,
+                                                                 OutPtrs out, float *__restrict__ out_vals) {
+    uint32_t src[kItems], vb[kItems];
+    uint64_t key[kItems];
+#pragma unroll
+    for (int j = 0; j < kItems; ++j) {
+        const int64_t k = item_index(j);
+        const bool in = k < n;
+        src[j] = (perm && in) ? perm[k] : 0u;
+        key[j] = in ? keys[k] : 0ull;
+        vb[j] = (!perm && in) ? sorted_bits[k] : 0u;
+    }
+    int32_t g[kItems][kMaxModes];
+#pragma unroll
+    for (int l = 0; l < kMaxModes; ++l)
+#pragma unroll
+        for (int j = 0; j < kItems; ++j)
+            g[j][l] = (l < nlev && dec.shift[l] < 0 && item_index(j) < n) ? lev_inds.p[l][src[j]] : 0;
+    if (perm) {
+#pragma unroll
+        for (int j = 0; j < kItems; ++j) vb[j] = item_index(j) < n ? __float_as_uint(vals[src[j]]) : 0u;
+    }
+#pragma unroll
+    for (int j = 0; j < kItems; ++j) {
+        const int64_t k = item_index(j);
+        if (k >= n) continue;
+#pragma unroll
+        for (int l = 0; l < kMaxModes; ++l) {
+            if (l >= nlev) break;
+            out.p[l][k] = dec.shift[l] >= 0
+                              ? (dec.bits[l] ? (int32_t)((key[j] >> dec.shift[l]) & ((uint64_t(1) << dec.bits[l]) - 1)) : 0)
+                              : g[j][l];
         }
-        out_vals[k] = perm ? vals[src] : __uint_as_float(sorted_bits[k]);
+        out_vals[k] = __uint_as_float(vb[j]);
     }
 }
 
@@ -117,16 +169,29 @@ __global__ void prefix_flags_kernel(IdxPtrs s, int upto, int64_t n, int32_t *__r
 // d[k] = the first level whose index differs from position k - 1 (0 at
 // k = 0; nlev when all are equal, i.e. a duplicate coordinate). Fiber
 // starts, duplicate runs and the CSF's per-leaf level flags all follow.
-__global__ void level_diff_kernel(IdxPtrs s, int nlev, int64_t n, uint8_t *__restrict__ d,
-                                  unsigned long long *__restrict__ ndup) {
+__global__ void __launch_bounds__(kThreads) level_diff_kernel(IdxPtrs s, int nlev, int64_t n, uint8_t *__restrict__ d,
+                                                              unsigned long long *__restrict__ ndup) {
+    int32_t cur[kItems][kMaxModes], prv[kItems][kMaxModes];
+#pragma unroll
+    for (int l = 0; l < kMaxModes; ++l)
+#pragma unroll
+        for (int j = 0; j < kItems; ++j) {
+            const int64_t k = item_index(j);
+            const bool in = l < nlev && k < n;
+            cur[j][l] = in ? s.p[l][k] : 0;
+            prv[j][l] = (in && k > 0) ? s.p[l][k - 1] : 0;
+        }
     unsigned long long dup = 0;
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
-         k += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int j = 0; j < kItems; ++j) {
+        const int64_t k = item_index(j);
+        if (k >= n) continue;
         int x = 0;
         if (k > 0) {
             x = nlev;
-            for (int l = 0; l < nlev; ++l)
-                if (s.p[l][k] != s.p[l][k - 1]) { x = l; break; }
+#pragma unroll
+            for (int l = kMaxModes - 1; l >= 0; --l)
+                if (l < nlev && cur[j][l] != prv[j][l]) x = l;  // the lowest differing level
         }
         dup += (x == nlev);
         d[k] = (uint8_t)x;
@@ -134,7 +199,6 @@ __global__ void level_diff_kernel(IdxPtrs s, int nlev, int64_t n, uint8_t *__res
     for (int o = 16; o > 0; o >>= 1) dup += __shfl_xor_sync(0xffffffffu, dup, o);
     if ((threadIdx.x & 31) == 0 && dup) atomicAdd(ndup, dup);
 }
-
 
 // For each distinct coordinate u starting at k: starts[u] = k.
 __global__ void run_starts_kernel(const int32_t *__restrict__ uid, int64_t n,
@@ -170,20 +234,40 @@ struct LevelScan {
 
 // Position k starts a level-l fiber when d[k] <= l (then it starts one at
 // every deeper level too); its fiber index is the exclusive scan fidx[l][k].
-__global__ void fill_levels_kernel(IdxPtrs s, LevelScan ls, const uint8_t *__restrict__ d, int nlev, int64_t n) {
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
-         k += (int64_t)gridDim.x * blockDim.x) {
-        const int dk = d[k];
-        for (int l = dk; l < nlev - 1; ++l) {
-            const int32_t f = ls.fidx[l][k];
-            ls.fids[l][f] = s.p[l][k];
-            ls.fptr[l][f] = (l == nlev - 2) ? (int32_t)k : ls.fidx[l + 1][k];
+__global__ void __launch_bounds__(kThreads) fill_levels_kernel(IdxPtrs s, LevelScan ls, const uint8_t *__restrict__ d,
+                                                               int nlev, int64_t n) {
+    int dk[kItems];
+#pragma unroll
+    for (int j = 0; j < kItems; ++j) {
+        const int64_t k = item_index(j);
+        dk[j] = k < n ? d[k] : nlev;
+    }
+#pragma unroll
+    for (int l = 0; l < kMaxModes - 1; ++l) {
+        if (l >= nlev - 1) break;
+        int32_t f[kItems], id[kItems], nx[kItems];
+#pragma unroll
+        for (int j = 0; j < kItems; ++j) {
+            const int64_t k = item_index(j);
+            const bool starts = dk[j] <= l;  // k opens a level-l fiber (dk = nlev past the end)
+            f[j] = starts ? ls.fidx[l][k] : 0;
+            id[j] = starts ? s.p[l][k] : 0;
+            nx[j] = (starts && l < nlev - 2) ? ls.fidx[l + 1][k] : (int32_t)k;
         }
-        if (k == 0)
-            for (int l = 0; l < nlev - 1; ++l) {
-                const int32_t nl = ls.fidx[l][n];
-                ls.fptr[l][nl] = (l == nlev - 2) ? (int32_t)n : ls.fidx[l + 1][n];
-            }
+#pragma unroll
+        for (int j = 0; j < kItems; ++j) {
+            if (dk[j] > l) continue;
+            ls.fids[l][f[j]] = id[j];
+            ls.fptr[l][f[j]] = nx[j];
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+#pragma unroll
+        for (int l = 0; l < kMaxModes - 1; ++l) {
+            if (l >= nlev - 1) break;
+            const int32_t nl = ls.fidx[l][n];
+            ls.fptr[l][nl] = (l == nlev - 2) ? (int32_t)n : ls.fidx[l + 1][n];
+        }
     }
 }
 
@@ -476,15 +560,12 @@ sptt_status csf_build_device(const sptt_coo *coo, int32_t root, const int32_t *o
                 }
                 g.chk[g.nchk] = lev_src[j];
                 g.dim[g.nchk] = c->dims[order[j]];
+                g.shift[g.nchk] = b ? shift : -1;  // a length-1 mode contributes no key bits
                 ++g.nchk;
-                if (b == 0) continue;  // a length-1 mode contributes no key bits
-                g.idx[g.nlev] = lev_src[j];
-                g.shift[g.nlev] = shift;
                 shift += b;
-                ++g.nlev;
             }
             const bool carry = first && last;  // one group: the sort carries the values
-            build_keys_kernel<<<grid_for(n), kThreads, 0, st>>>(g, first ? nullptr : vals, n, keys_alt,
+            build_keys_kernel<<<grid_items(n), kThreads, 0, st>>>(g, first ? nullptr : vals, n, keys_alt,
                                                                 vals_alt, d_err, carry ? coo->vals : nullptr);
             SPTT_CHECK_LAUNCH("build_keys_kernel");
             {
@@ -514,7 +595,7 @@ sptt_status csf_build_device(const sptt_coo *coo, int32_t root, const int32_t *o
         SPTT_TRY(sv_store.alloc<float>(n, st));
         IdxPtrs lp{};
         for (int l = 0; l < N; ++l) lp.p[l] = lev_src[l];
-        gather_sorted_kernel<<<grid_for(n), kThreads, 0, st>>>(lp, N, coo->vals, perm, sorted_bits, sorted_keys,
+        gather_sorted_kernel<<<grid_items(n), kThreads, 0, st>>>(lp, N, coo->vals, perm, sorted_bits, sorted_keys,
                                                                dec, n, so, sv_store.as<float>());
         SPTT_CHECK_LAUNCH("gather_sorted_kernel");
     }
@@ -533,7 +614,7 @@ sptt_status csf_build_device(const sptt_coo *coo, int32_t root, const int32_t *o
     DevBuf cv_store;
     if (n > 0) {
         SPTT_TRY(dlev.alloc<uint8_t>(n, st));
-        level_diff_kernel<<<grid_for(n), kThreads, 0, st>>>(s, N, n, dlev.as<uint8_t>(), d_ndup);
+        level_diff_kernel<<<grid_items(n), kThreads, 0, st>>>(s, N, n, dlev.as<uint8_t>(), d_ndup);
         SPTT_CHECK_LAUNCH("level_diff_kernel");
         unsigned long long hw[2] = {0, 0};
         SPTT_CUDA(cudaMemcpyAsync(hw, word.p, sizeof(hw), cudaMemcpyDeviceToHost, st));
@@ -562,7 +643,7 @@ sptt_status csf_build_device(const sptt_coo *coo, int32_t root, const int32_t *o
             SPTT_CHECK_LAUNCH("coalesce_kernel");
             for (int l = 0; l < N; ++l) s.p[l] = co.p[l];
             sv = cv_store.as<float>();
-            level_diff_kernel<<<grid_for(u), kThreads, 0, st>>>(s, N, u, dlev.as<uint8_t>(), d_ndup);
+            level_diff_kernel<<<grid_items(u), kThreads, 0, st>>>(s, N, u, dlev.as<uint8_t>(), d_ndup);
             SPTT_CHECK_LAUNCH("level_diff_kernel");
         }
     }
@@ -604,7 +685,7 @@ sptt_status csf_build_device(const sptt_coo *coo, int32_t root, const int32_t *o
             ls.fids[l] = c->fids[l];
             ls.fptr[l] = c->fptr[l];
         }
-        fill_levels_kernel<<<grid_for(u), kThreads, 0, st>>>(s, ls, dlev.as<uint8_t>(), N, u);
+        fill_levels_kernel<<<grid_items(u), kThreads, 0, st>>>(s, ls, dlev.as<uint8_t>(), N, u);
         SPTT_CHECK_LAUNCH("fill_levels_kernel");
         SPTT_CUDA(cudaMemcpyAsync(c->lvl, dlev.p, (size_t)u, cudaMemcpyDeviceToDevice, st));
         SPTT_CUDA(cudaMemcpyAsync(c->fids[N - 1], s.p[N - 1], u * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));

@@ -162,13 +162,17 @@ __global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(const uint64_t
     for (int i = threadIdx.x; i < kSortWarps * kRadix; i += kSortThreads) (&hist[0][0])[i] = 0;
     __syncthreads();
     const int64_t base = (int64_t)blockIdx.x * kSortTile;
-#pragma unroll 4
+    // all of the thread's keys are requested before the first is counted
+    uint64_t k[kSortItems];
+#pragma unroll
     for (int j = 0; j < kSortItems; ++j) {
-        int64_t i = base + j * kSortThreads + threadIdx.x;
-        if (i < n) {
-            int d = (int)((keys[i] >> shift) & (kRadix - 1));
-            atomicAdd(&hist[warp][d], 1);
-        }
+        const int64_t i = base + j * kSortThreads + threadIdx.x;
+        k[j] = i < n ? keys[i] : 0ull;
+    }
+#pragma unroll
+    for (int j = 0; j < kSortItems; ++j) {
+        const int64_t i = base + j * kSortThreads + threadIdx.x;
+        if (i < n) atomicAdd(&hist[warp][(int)((k[j] >> shift) & (kRadix - 1))], 1);
     }
     __syncthreads();
     int d = threadIdx.x;
