@@ -436,10 +436,23 @@ sptt_status csf_ensure_partition(sptt_csf *c, int32_t chunk, cudaStream_t st) {
 
 namespace {
 
-__global__ void leafrec_kernel(const int32_t *__restrict__ idx, const float *__restrict__ vals,
-                               const uint8_t *__restrict__ lvl, int64_t nnz, uint4 *__restrict__ rec) {
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nnz; k += (int64_t)gridDim.x * blockDim.x)
-        rec[k] = make_uint4((uint32_t)idx[k], __float_as_uint(vals[k]), 0u, (uint32_t)lvl[k]);
+__global__ void __launch_bounds__(kThreads) leafrec_kernel(const int32_t *__restrict__ idx, const float *__restrict__ vals,
+                                                           const uint8_t *__restrict__ lvl, int64_t nnz,
+                                                           uint4 *__restrict__ rec) {
+    uint32_t x[kItems], v[kItems], d[kItems];
+#pragma unroll
+    for (int j = 0; j < kItems; ++j) {
+        const int64_t k = item_index(j);
+        const bool in = k < nnz;
+        x[j] = in ? (uint32_t)idx[k] : 0u;
+        v[j] = in ? __float_as_uint(vals[k]) : 0u;
+        d[j] = in ? (uint32_t)lvl[k] : 0u;
+    }
+#pragma unroll
+    for (int j = 0; j < kItems; ++j) {
+        const int64_t k = item_index(j);
+        if (k < nnz) rec[k] = make_uint4(x[j], v[j], 0u, d[j]);
+    }
 }
 
 // The leaf that starts level-LF fiber f carries that fiber's index.
@@ -459,7 +472,7 @@ sptt_status csf_ensure_leafrec(sptt_csf *c, cudaStream_t st) {
                        (size_t)(nnz + kLeafSlack) * sizeof(uint4), st));
     SPTT_TRY(fill_zero_launch(c->leafrec + nnz, (size_t)kLeafSlack * sizeof(uint4), st));
     if (nnz > 0) {
-        leafrec_kernel<<<grid_for(nnz), kThreads, 0, st>>>(c->fids[N - 1], c->vals, c->lvl, nnz, c->leafrec);
+        leafrec_kernel<<<grid_items(nnz), kThreads, 0, st>>>(c->fids[N - 1], c->vals, c->lvl, nnz, c->leafrec);
         SPTT_CHECK_LAUNCH("leafrec_kernel");
         if (N >= 3) {
             // level N-2 fibers: fptr[N-2][f] is the first leaf of fiber f

@@ -74,16 +74,18 @@ __global__ void __launch_bounds__(kThreads) gram_kernel(const float *__restrict_
         }
 }
 
-// out[e] = sum_b partials[b][e]: 8 lanes per element each sum every 8th
-// block, then the 8 lane sums are added in lane order (deterministic).
-constexpr int kRedLanes = 8;
+// out[e] = sum_b partials[b][e]: 32 lanes per element each sum every 32nd
+// block, then the 32 lane sums are added in lane order (deterministic).
+constexpr int kRedLanes = 32;
 __global__ void reduce_partials_kernel(const double *__restrict__ partials, int nblocks, int pstride, int nelem,
                                        double *__restrict__ out) {
     __shared__ double s[kRedLanes][33];
     const int e = blockIdx.x * 32 + threadIdx.x;
     double v = 0.0;
-    if (e < nelem)
+    if (e < nelem) {
+#pragma unroll 4
         for (int b = threadIdx.y; b < nblocks; b += kRedLanes) v += partials[(int64_t)b * pstride + e];
+    }
     s[threadIdx.y][threadIdx.x] = v;
     __syncthreads();
     if (threadIdx.y == 0 && e < nelem) {
