@@ -44,7 +44,7 @@ def parse():
     p.add_argument("--rank", type=int, default=16)
     p.add_argument("--nnz", type=int, default=100_000_000)
     p.add_argument("--seed", type=int, default=2)
-    p.add_argument("--e2e-steps", type=int, default=2)
+    p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--e2e-iters", type=int, default=20)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-extras", action="store_true")

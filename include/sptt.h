@@ -43,7 +43,7 @@ typedef int32_t sptt_status;
 #define SPTT_ERR_CUDA (-3)        /* a CUDA runtime call or kernel failed */
 #define SPTT_ERR_TIMEOUT (-4)     /* a bounded device-side wait ran out */
 #define SPTT_ERR_NOT_PD (-5)      /* reported by sptt_cpd_solve_branch only (not an error) */
-#define SPTT_ERR_UNSUPPORTED (-6) /* valid but outside this build's limits (e.g. rank > 64) */
+#define SPTT_ERR_UNSUPPORTED (-6) /* valid but outside the library's limits (e.g. rank > 64) */
 #define SPTT_ERR_INTERNAL (-7)
 
 #define SPTT_MAX_MODES 5
