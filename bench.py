@@ -266,7 +266,7 @@ def every_gather_model(csf, R, s_f=4):
 # from one ncu capture of the 2e7-non-zero case of this workload (roots
 # 0, 1, 2); the traffic is dominated by the leaf-record stream, so it is
 # scaled to other sizes by the number of non-zeros.
-NCU_TRAFFIC = {"kernel": "mttkrp_flag_kernel<3, float, 2, 2, 32, 1, 1>", "variant": 7, "nnz": 20_000_000,
+NCU_TRAFFIC = {"kernel": "mttkrp_flag_kernel<3, float, 2, 2, 32, 1, 1, 0>", "variant": 7, "nnz": 20_000_000,
                "bytes": [368.293888e6, 409.197568e6, 409.038336e6]}
 # The same for the default BF16-gather kernel (variant 11).
 NCU_TRAFFIC_BF16 = {"kernel": "mttkrp_flag_kernel<3, __nv_bfloat16, 4, 2, 16, 1, 1, 1>", "variant": 11,
