@@ -8,21 +8,20 @@
 //
 // GPU mapping (replaces the paper's thread-per-slice loops with locks or
 // privatised outputs, Section IV-A / V-D-2):
-//   * a "lane group" of G = ld / VEC lanes owns one output row segment; lane g
-//     holds columns [g*VEC, g*VEC+VEC) (VEC = 4 for FP32 factors, 8 for BF16)
-//     and gathers them with one 128-bit load per factor row;
+//   * a "lane group" of G = ld / VEC lanes owns one output row; lane g holds
+//     columns [g*VEC, g*VEC+VEC) and gathers them with one 16- or 32-byte load
+//     per factor row (VEC = 4 or 8 FP32 values, 8 or 16 BF16 values);
 //   * the leaves are cut into equal chunks (the CSF's precomputed partition
 //     gives, per chunk, the fiber at every level holding its first leaf); a
 //     lane group walks its chunk in order, keeping one register accumulator
 //     per tree level, so the load is balanced whatever the slice sizes
 //     (power-law slices are split across many chunks);
 //   * output conflicts: a slice that lies entirely inside one chunk is owned
-//     by that lane group and written with a plain 128-bit store; a slice cut
-//     by a chunk boundary is combined with red.global.add.v4.f32 into a
-//     zeroed output (the GPU form of the paper's lock pool: no lock, no spin).
-// Root-mode MTTKRP kernels and the sptt_mttkrp entry point (Section III;
-// Algorithm 1 lines 5, 8, 11). The per-chunk tree walks live in walk.cuh;
-// the kernels here spread the chunks over the lane groups of the grid.
+//     by that lane group and stored; a slice cut by a chunk boundary is
+//     combined with red.global.add.v4.f32 into a zeroed output, a heavy one
+//     in FP64 (the GPU form of the paper's lock pool: no lock, no spin).
+// The per-chunk tree walks live in walk.cuh; the kernels here spread the
+// chunks over the lane groups of the grid and hold the sptt_mttkrp entry point.
 #include "walk.cuh"
 
 namespace sptt {
