@@ -60,3 +60,25 @@ def test_reference_arm_runs_on_rank_zero_only(capsys):
     args = types.SimpleNamespace(seed=2, nnz=1000, rank=16, steps=1, warmup=0, gpus=2)
     assert bench.reference_arm(args, 1, 2) is None  # rank 1: no work, no output
     assert capsys.readouterr().out == ""
+
+
+def test_byte_models_take_the_factor_element_size():
+    # the byte model of one root-mode MTTKRP: 8 bytes per non-zero, 8 per
+    # upper-level fiber, each distinct factor row once per level (s_f bytes
+    # per element), the FP32 output; the "every gather" model counts a row
+    # per fiber and leaf below the root
+    csf = types.SimpleNamespace(nmodes=3, nfibs=[5, 40, 100], order=[2, 0, 1], root=2)
+    dims, R, distinct = [30, 20, 5], 16, [25, 18, 5]
+    for s_f in (4, 2):
+        want = 100 * 8 + (5 + 40) * 8 + (distinct[0] + distinct[1]) * R * s_f + dims[2] * R * 4
+        assert bench.byte_model(csf, dims, R, distinct, s_f) == want
+        assert bench.every_gather_model(csf, R, s_f) == (40 + 100) * R * s_f
+    assert bench.flop_model(csf, R) == 2 * R * (100 + 40)
+
+
+def test_bench_accepts_the_gather_precision(monkeypatch):
+    monkeypatch.setattr("sys.argv", ["bench.py", "--precision", "bf16", "--steps", "2"])
+    a = bench.parse()
+    assert a.precision == "bf16" and a.steps == 2 and a.e2e_steps == 3
+    monkeypatch.setattr("sys.argv", ["bench.py"])
+    assert bench.parse().precision == "fp32"
