@@ -129,7 +129,7 @@ sptt_status sptt_csf_copy_level(const sptt_csf *csf, int32_t level, int32_t *fpt
                                 float *vals, sptt_stream stream);
 
 /* ------------------------------------------------------------------------ */
-/* MTTKRP (Section III; Algorithm 1 lines 5, 8, 11).                        */
+/* MTTKRP (Section III; the MTTKRP step of Algorithm 1).                    */
 /* ------------------------------------------------------------------------ */
 
 /*
@@ -189,8 +189,8 @@ sptt_status sptt_mttkrp(const sptt_csf *csf, const void *const *factors, int32_t
                         int32_t ld, float *out, const sptt_sched *sched, sptt_stream stream);
 
 /*
- * MTTKRP for any mode n of the tensor from one CSF (Section III; Algorithm 1
- * lines 5, 8, 11), the single-CSF form whose output conflicts the paper
+ * MTTKRP for any mode n of the tensor from one CSF (Section III; the MTTKRP
+ * step of Algorithm 1), the single-CSF form whose output conflicts the paper
  * resolves with a lock pool or privatised copies (Section IV-A, V-D-2).
  * mode = the CSF's root runs sptt_mttkrp. For a mode at tree level L >= 1,
  * each level-L fiber (each leaf when L = N-1) adds the Hadamard product of
@@ -217,7 +217,7 @@ sptt_status sptt_mttkrp_mode(const sptt_csf *csf, int32_t mode, const void *cons
                              sptt_stream stream);
 
 /* ------------------------------------------------------------------------ */
-/* Dense R x R pieces (Algorithm 1 lines 4, 7, 10).                          */
+/* Dense R x R pieces (the Gram products of Algorithm 1).                   */
 /* ------------------------------------------------------------------------ */
 
 /*
@@ -311,7 +311,7 @@ sptt_status sptt_cpd_create(const sptt_coo *coo, int32_t rank, const sptt_opts *
 void sptt_cpd_free(sptt_cpd *cpd);
 
 /*
- * Initialise the factors (Algorithm 1 line 2). init = NULL: U(0,1) from the
+ * Initialise the factors (Algorithm 1, initialisation). init = NULL: U(0,1) from the
  * Philox4x64-10 stream of opts.seed (key (seed, mode), counter (e/4,0,0,0),
  * word e mod 4, e = row*rank + col; value ((w >> 41) + 0.5) / 2^23). Else
  * init is a host array of nmodes pointers (host or device) to dims[m] x rank
@@ -320,7 +320,7 @@ void sptt_cpd_free(sptt_cpd *cpd);
 sptt_status sptt_cpd_init(sptt_cpd *cpd, const float *const *init);
 
 /*
- * Run up to `iters` ALS iterations (Algorithm 1 lines 3-13): per mode n in
+ * Run up to `iters` ALS iterations (the loop of Algorithm 1): per mode n in
  * order, V = Hadamard of the other modes' Grams, A^(n) = MTTKRP_n V^dagger
  * (Cholesky in FP64; pseudo-inverse when V is not positive definite),
  * normalise the columns into lambda, refresh G_n; then the fit. With

@@ -351,7 +351,7 @@ void oracle_pinv_sym(int32_t n, const double *V, double *P) {
 }
 
 /*
- * Row-wise normal-equation solve A = M V^dagger (Algorithm 1, lines 5/8/11),
+ * Row-wise normal-equation solve A = M V^dagger (Algorithm 1, the solve of each mode update),
  * in place on M (rows x n). Through Cholesky (forward then back substitution
  * per row) when V is positive definite, else through the pseudo-inverse.
  * Returns 0 on the Cholesky branch, 1 on the pseudo-inverse branch.
@@ -438,7 +438,7 @@ double oracle_fit(int32_t nmodes, int32_t rank, double normx_sq, const double *c
 }
 
 /*
- * One factor update of Algorithm 1 for mode n (lines 4-6 for n = 1):
+ * One factor update of Algorithm 1 for mode n (the first three steps of the loop body for n = 1):
  *   V = Hadamard of G_m over m != n;  A^(n) = MTTKRP_n V^dagger;  normalise;
  *   G_n = A^(n)T A^(n).
  * factors[n] (dims[n] x rank) and grams[n] are overwritten; lambda receives

@@ -2,11 +2,11 @@
 //
 // Per iteration, for each mode n in order (Gauss-Seidel: every update sees the
 // latest factors):
-//   MTTKRP over the CSF rooted at n                       (lines 5/8/11)
-//   V = Hadamard of the other modes' Grams, W = V^dagger  (lines 4/7/10)
-//   A_un = M W, fused with Gram(A_un) and the fit's dots  (lines 5/8/11)
-//   lambda = column norms, G_n = D^-1 Gram(A_un) D^-1, normalise A (6/9/12)
-// then the fit (line 13). All of it is enqueued on the handle's stream; the
+//   MTTKRP over the CSF rooted at n
+//   V = Hadamard of the other modes' Grams, W = V^dagger
+//   A_un = M W, fused with Gram(A_un) and the fit's dots
+//   lambda = column norms, G_n = D^-1 Gram(A_un) D^-1, normalise A
+// then the fit at the end of the iteration. All of it is enqueued on the handle's stream; the
 // host reads back only when asked (tol > 0, or an accessor).
 #include <math.h>
 #include <string.h>

@@ -1,7 +1,6 @@
-// Dense R x R work of CP-ALS (Algorithm 1): Grams and their Hadamard product
-// (lines 4, 7, 10), the normal-equation solve A = M V^dagger (lines 5, 8, 11;
-// V^dagger through Cholesky, Section V-A), column normalisation into lambda
-// (lines 6, 9, 12) and the fit (line 13).
+// Dense R x R work of CP-ALS (Algorithm 1): Grams and their Hadamard product,
+// the normal-equation solve A = M V^dagger (V^dagger through Cholesky,
+// Section V-A), column normalisation into lambda and the fit.
 //
 // Precision: the R x R matrices (Grams, V, its factor and inverse) are FP64.
 // The row-wise work over I_n x R data runs on FP32 CUDA cores: products in

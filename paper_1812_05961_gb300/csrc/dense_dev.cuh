@@ -26,7 +26,7 @@ __device__ __forceinline__ double block_sum_d(double v, double *red) {
 }
 
 // ---------------------------------------------------------------------------
-// Row solve after each MTTKRP (Algorithm 1 lines 5-6, 8-9, 11-12): for one
+// Row solve after each MTTKRP (Algorithm 1: solve and normalise): for one
 // tile of TR = 4096 / RP rows of the compact MTTKRP result M (heavy slices
 // from their FP64 rows), A_un = M W is written to A at the slices' mode
 // indices, and each thread adds its share of the Gram A_un^T A_un and of the

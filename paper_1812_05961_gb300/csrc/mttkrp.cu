@@ -1,4 +1,4 @@
-// Root-mode MTTKRP over CSF (Section III; Algorithm 1 lines 5, 8, 11).
+// Root-mode MTTKRP over CSF (Section III; the MTTKRP step of Algorithm 1).
 //
 // For the CSF rooted at mode n with level order (n, o_1, ..., o_{N-1}):
 //   M[i, :] = sum_{level-1 fibers f of slice i} A^(o_1)[j_f, :] *

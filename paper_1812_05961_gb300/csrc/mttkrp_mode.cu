@@ -1,4 +1,4 @@
-// MTTKRP for any mode from one CSF (Section III; Algorithm 1 lines 5, 8, 11),
+// MTTKRP for any mode from one CSF (Section III; the MTTKRP step of Algorithm 1),
 // the single-CSF form of SPLATT that the paper's lock pool and privatised
 // outputs serve (Section IV-A, Section V-D-2).
 //

@@ -1,5 +1,5 @@
 // Device-side walk of one work chunk of a CSF tree for the root-mode MTTKRP
-// (Section III; Algorithm 1 lines 5, 8, 11). Shared by the standalone MTTKRP
+// (Section III; the MTTKRP step of Algorithm 1). Shared by the standalone MTTKRP
 // kernels and the batched CP-ALS kernel.
 //
 // For the CSF rooted at mode n with level order (n, o_1, ..., o_{N-1}):

@@ -162,7 +162,7 @@ def test_residual_non_increasing():
 
 def test_mode_update_is_one_step_of_als():
     """One call of the mode update equals a literal numpy restatement of
-    Algorithm 1 lines 4-6 (Hadamard of Grams, solve, normalise)."""
+    one mode update of Algorithm 1 (Hadamard of Grams, solve, normalise)."""
     rng = np.random.default_rng(12)
     dims = (8, 7, 6)
     nnz = 120
