@@ -15,7 +15,7 @@
  *  - initial factors: U(0,1) from a Philox4x64-10 stream (key = (seed, mode),
  *    counter = (e/4, 0, 0, 0), word e%4, e = row*rank + col);
  *  - duplicate coordinates are summed (coalesced) in input order;
- *  - "normalize columns" uses the 2-norm every iteration; a zero column keeps
+ *  - the column normalisation uses the 2-norm every iteration; a zero column keeps
  *    lambda = 0 and is left at zero;
  *  - V^dagger is applied through a Cholesky factorisation (Section V-A: potrf /
  *    potrs); when V is not positive definite (a pivot <= 1e-14 * max diag) the
@@ -23,7 +23,7 @@
  *    eigenvalues below n * eps * max|eig| treated as zero;
  *  - the fit is computed once per iteration after the last mode, as
  *    1 - sqrt(max(0, |X|^2 + |Xhat|^2 - 2<X,Xhat>)) / |X|, and iteration stops
- *    when |fit - fit_prev| < tol ("fit ceases to improve", Algorithm 1).
+ *    when |fit - fit_prev| < tol (Algorithm 1 stops once the fit no longer improves).
  *
  * Parity pins: every function here is pinned in tests/test_oracle_*.py against
  * brute force (dense unfolding times explicit Khatri-Rao), closed forms,
@@ -397,7 +397,7 @@ int oracle_solve_normals(int64_t rows, int32_t n, const double *V, double *M) {
 }
 
 /* Normalise the columns of A (rows x rank) by their 2-norms, stored in lambda
- * (Algorithm 1, "normalize columns ... storing norms as lambda"). */
+ * (Algorithm 1 scales each column to unit norm and keeps the norms as lambda). */
 void oracle_normalize(int64_t rows, int32_t rank, double *A, double *lambda) {
     for (int r = 0; r < rank; ++r) {
         double s = 0.0;
@@ -410,7 +410,7 @@ void oracle_normalize(int64_t rows, int32_t rank, double *A, double *lambda) {
 }
 
 /*
- * Fit of the model (Algorithm 1, "fit ceases to improve"):
+ * Fit of the model (Algorithm 1 checks it once per iteration):
  *   |X - Xhat|^2 = |X|^2 + lambda^T (*_m G_m) lambda - 2 sum_r lambda_r sum_i M[i,r] A[i,r]
  * where G_m are the Grams of the (normalised) factors, M is the MTTKRP of the
  * last-updated mode n and A its normalised factor. Returns 1 - |X - Xhat| / |X|
