@@ -32,13 +32,33 @@ _u8p = ctypes.POINTER(ctypes.c_uint8)
 
 
 def build(force: bool = False) -> str:
-    """Compile ``oracle.c`` into ``liboracle.so`` next to it (gcc, no GPU)."""
+    """Compile ``oracle.c`` into ``liboracle.so`` next to it (gcc, no GPU),
+    with OpenMP when the compiler has it (the threaded MTTKRP; see
+    ``set_threads``), else without."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + ".%d.tmp" % os.getpid()
-        subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"],
-                       check=True)
+        base = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+        r = subprocess.run(base[:1] + ["-fopenmp"] + base[1:], capture_output=True, text=True)
+        if r.returncode != 0:
+            subprocess.run(base, check=True)
         os.replace(tmp, _LIB)
     return _LIB
+
+
+def set_threads(n: int) -> int:
+    """Host threads of the oracle's MTTKRP (1 = the literal single loop, the
+    default). Returns the number in effect (1 without OpenMP). Only the FP64
+    summation order depends on it."""
+    _threads_now[0] = int(_load().oracle_set_threads(int(n)))
+    return _threads_now[0]
+
+
+def threads() -> int:
+    """The number of threads the MTTKRP currently uses."""
+    return _threads_now[0]
+
+
+_threads_now = [1]
 
 
 def _load():
@@ -84,6 +104,8 @@ def _load():
             lib.oracle_mlp_forward.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _f64p,
                                                ctypes.c_int64, _f64p, _f64p]
             lib.oracle_mlp_loss_grad.restype = ctypes.c_double
+            lib.oracle_set_threads.restype = ctypes.c_int32
+            lib.oracle_set_threads.argtypes = [ctypes.c_int32]
             lib.oracle_mlp_loss_grad.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _f64p,
                                                  ctypes.c_int64, _f64p, _f64p, _f64p]
             _lib = lib

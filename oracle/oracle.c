@@ -33,6 +33,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 /* ------------------------------------------------------------------------ */
 /* Philox4x64-10 counter-based generator, from its published definition     */
@@ -217,14 +220,28 @@ void oracle_csf(int32_t nmodes, int64_t nnz, const int32_t *const *sorted_inds,
  * element-wise tolerances). row_mask, if not NULL, restricts the work to the
  * rows i with row_mask[i] != 0; other rows are left at zero.
  */
-void oracle_mttkrp(int32_t nmodes, int64_t nnz, const int64_t *dims,
-                   const int32_t *const *inds, const float *vals,
-                   const double *const *factors, int32_t rank, int32_t mode,
-                   double *out, double *out_abs, const uint8_t *row_mask) {
-    int64_t rows = dims[mode];
-    memset(out, 0, (size_t)(rows * rank) * sizeof(double));
-    if (out_abs) memset(out_abs, 0, (size_t)(rows * rank) * sizeof(double));
-    for (int64_t k = 0; k < nnz; ++k) {
+/* Threads of the MTTKRP (1 = the literal single-loop order). */
+static int32_t g_threads = 1;
+
+/*
+ * Set the number of host threads oracle_mttkrp uses (n < 1 means 1) and
+ * return the number in effect: 1 when the oracle was compiled without OpenMP.
+ */
+int32_t oracle_set_threads(int32_t n) {
+#ifdef _OPENMP
+    g_threads = n < 1 ? 1 : n;
+#else
+    (void)n;
+    g_threads = 1;
+#endif
+    return g_threads;
+}
+
+/* M[i_n, :] += v * prod_{m != n} A^(m)[i_m, :] over non-zeros [k0, k1). */
+static void mttkrp_range(int32_t nmodes, int64_t k0, int64_t k1, const int32_t *const *inds,
+                         const float *vals, const double *const *factors, int32_t rank, int32_t mode,
+                         double *out, double *out_abs, const uint8_t *row_mask) {
+    for (int64_t k = k0; k < k1; ++k) {
         int64_t i = inds[mode][k];
         if (row_mask && !row_mask[i]) continue;
         double v = (double)vals[k];
@@ -243,12 +260,58 @@ void oracle_mttkrp(int32_t nmodes, int64_t nnz, const int64_t *dims,
     }
 }
 
+void oracle_mttkrp(int32_t nmodes, int64_t nnz, const int64_t *dims,
+                   const int32_t *const *inds, const float *vals,
+                   const double *const *factors, int32_t rank, int32_t mode,
+                   double *out, double *out_abs, const uint8_t *row_mask) {
+    int64_t rows = dims[mode];
+    size_t cells = (size_t)(rows * rank);
+    memset(out, 0, cells * sizeof(double));
+    if (out_abs) memset(out_abs, 0, cells * sizeof(double));
+#ifdef _OPENMP
+    /*
+     * With T > 1 threads: thread t sums non-zeros [nnz*t/T, nnz*(t+1)/T) into
+     * its own zeroed copy of M, and the copies are added in thread order.
+     * Only the FP64 summation order differs from the single loop.
+     */
+    int32_t T = g_threads;
+    if (T > 1 && nnz >= 4096) {
+        size_t per = cells * (out_abs ? 2 : 1);
+        double *priv = (double *)calloc((size_t)T * per, sizeof(double));
+        if (priv) {
+#pragma omp parallel num_threads(T)
+            {
+                int t = omp_get_thread_num();
+                double *mine = priv + (size_t)t * per;
+                mttkrp_range(nmodes, nnz * t / T, nnz * (t + 1) / T, inds, vals, factors, rank, mode, mine,
+                             out_abs ? mine + cells : NULL, row_mask);
+            }
+#pragma omp parallel for num_threads(T) schedule(static)
+            for (int64_t e = 0; e < (int64_t)cells; ++e) {
+                double s = 0.0, sa = 0.0;
+                for (int t = 0; t < T; ++t) {
+                    s += priv[(size_t)t * per + e];
+                    if (out_abs) sa += priv[(size_t)t * per + cells + e];
+                }
+                out[e] = s;
+                if (out_abs) out_abs[e] = sa;
+            }
+            free(priv);
+            return;
+        }
+    }
+#endif
+    mttkrp_range(nmodes, 0, nnz, inds, vals, factors, rank, mode, out, out_abs, row_mask);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Dense R x R algebra of Algorithm 1.                                      */
 /* ------------------------------------------------------------------------ */
 
 /* G = A^T A (Algorithm 1, "A^(m)T A^(m)"), A rows x rank row-major. */
 void oracle_gram(int64_t rows, int32_t rank, const double *A, double *G) {
+    /* entries are independent; each keeps the row order of its sum */
+#pragma omp parallel for num_threads(g_threads) if (g_threads > 1) schedule(static)
     for (int a = 0; a < rank; ++a)
         for (int b = 0; b < rank; ++b) {
             double s = 0.0;
@@ -360,34 +423,48 @@ int oracle_solve_normals(int64_t rows, int32_t n, const double *V, double *M) {
     double *L = (double *)malloc((size_t)n * n * sizeof(double));
     double *y = (double *)malloc((size_t)n * sizeof(double));
     int branch;
+    /* rows are independent: with several threads each takes a block of
+       rows and its own y, and every row's arithmetic is unchanged */
     if (oracle_cholesky(n, V, L) == 0) {
         branch = 0;
-        for (int64_t i = 0; i < rows; ++i) {
-            double *m = M + i * n;
-            /* V x = m, i.e. L y = m then L^T x = y (V symmetric, so x^T = m^T V^-1) */
-            for (int a = 0; a < n; ++a) {
-                double s = m[a];
-                for (int b = 0; b < a; ++b) s -= L[a * n + b] * y[b];
-                y[a] = s / L[a * n + a];
+#pragma omp parallel num_threads(g_threads) if (g_threads > 1)
+        {
+            double *yt = g_threads > 1 ? (double *)malloc((size_t)n * sizeof(double)) : y;
+#pragma omp for schedule(static)
+            for (int64_t i = 0; i < rows; ++i) {
+                double *m = M + i * n;
+                /* V x = m, i.e. L y = m then L^T x = y (V symmetric, so x^T = m^T V^-1) */
+                for (int a = 0; a < n; ++a) {
+                    double s = m[a];
+                    for (int b = 0; b < a; ++b) s -= L[a * n + b] * yt[b];
+                    yt[a] = s / L[a * n + a];
+                }
+                for (int a = n - 1; a >= 0; --a) {
+                    double s = yt[a];
+                    for (int b = a + 1; b < n; ++b) s -= L[b * n + a] * m[b];
+                    m[a] = s / L[a * n + a];
+                }
             }
-            for (int a = n - 1; a >= 0; --a) {
-                double s = y[a];
-                for (int b = a + 1; b < n; ++b) s -= L[b * n + a] * m[b];
-                m[a] = s / L[a * n + a];
-            }
+            if (yt != y) free(yt);
         }
     } else {
         branch = 1;
         double *P = (double *)malloc((size_t)n * n * sizeof(double));
         oracle_pinv_sym(n, V, P);
-        for (int64_t i = 0; i < rows; ++i) {
-            double *m = M + i * n;
-            for (int a = 0; a < n; ++a) {
-                double s = 0.0;
-                for (int b = 0; b < n; ++b) s += m[b] * P[b * n + a];
-                y[a] = s;
+#pragma omp parallel num_threads(g_threads) if (g_threads > 1)
+        {
+            double *yt = g_threads > 1 ? (double *)malloc((size_t)n * sizeof(double)) : y;
+#pragma omp for schedule(static)
+            for (int64_t i = 0; i < rows; ++i) {
+                double *m = M + i * n;
+                for (int a = 0; a < n; ++a) {
+                    double s = 0.0;
+                    for (int b = 0; b < n; ++b) s += m[b] * P[b * n + a];
+                    yt[a] = s;
+                }
+                memcpy(m, yt, (size_t)n * sizeof(double));
             }
-            memcpy(m, y, (size_t)n * sizeof(double));
+            if (yt != y) free(yt);
         }
         free(P);
     }
@@ -399,6 +476,8 @@ int oracle_solve_normals(int64_t rows, int32_t n, const double *V, double *M) {
 /* Normalise the columns of A (rows x rank) by their 2-norms, stored in lambda
  * (Algorithm 1 scales each column to unit norm and keeps the norms as lambda). */
 void oracle_normalize(int64_t rows, int32_t rank, double *A, double *lambda) {
+    /* columns are independent; each keeps the row order of its sum */
+#pragma omp parallel for num_threads(g_threads) if (g_threads > 1) schedule(static)
     for (int r = 0; r < rank; ++r) {
         double s = 0.0;
         for (int64_t i = 0; i < rows; ++i) s += A[i * rank + r] * A[i * rank + r];
