@@ -135,7 +135,8 @@ sptt_status sptt_csf_copy_level(const sptt_csf *csf, int32_t level, int32_t *fpt
 /*
  * Optional schedule for the MTTKRP kernels (the autotuner's knobs).
  *   chunk       non-zeros per work unit of a lane group; power of two in
- *               [16, 4096]; 0 = default
+ *               [16, 4096]; 0 = default (128, halved down to 32 while the
+ *               tensor gives fewer than 128 chunks per SM)
  *   block       threads per CTA (multiple of 32, <= 256); 0 = default
  *   variant     kernel variant: 0 = default (the fastest measured for the
  *               gather type and ld); 1 = plain walk (fiber ends from fptr,
@@ -151,8 +152,18 @@ sptt_status sptt_csf_copy_level(const sptt_csf *csf, int32_t level, int32_t *fpt
  *               reading packed leaf records; 10 / 11 = variant 7 / 9 with
  *               each leaf added straight into its fiber's parent (one more
  *               multiply per leaf, no per-fiber fold; 10 falls back to 3
- *               like 7). Variants 7, 9, 10 and 11 (and the default, for F32
- *               gathers with ld % 8 == 0 and for BF16 gathers) read packed
+ *               like 7); 12 / 13 = the select walk on packed records (the
+ *               form of 10 whose per-leaf work has no branch: an opening
+ *               fiber's row replaces the open one by a select), 32-byte
+ *               segments in batches of 2 / 16-byte segments in batches of
+ *               4, two CTAs per SM (12 falls back to 13 like 7); 14 / 15 =
+ *               the select walk with the whole leaf factor copied into
+ *               shared memory once per CTA, 16-byte segments, one CTA of
+ *               1024 threads in batches of 2 / 512 threads in batches of 4,
+ *               used when that copy is at most 160 KB (else run as 13).
+ *               Default: 13; with F32 gathers on a tensor of at least 2^25
+ *               non-zeros whose leaf factor fits, 14. Variants 7 and 9..15
+ *               (and so the default) read packed
  *               16-byte leaf records that the first call builds (16 bytes
  *               per non-zero on the device, kept with the CSF)
  */
@@ -161,7 +172,12 @@ typedef struct {
     int32_t block;
     int32_t variant;
     int32_t order;  /* CSF level order below the root for CP-ALS plans: 0 = ascending
-                       length (default), 1 = descending; ignored by sptt_mttkrp */
+                       length, 1 = descending, 2 = the shortest mode at the leaves and
+                       the others ascending above it; ignored by sptt_mttkrp. CP-ALS
+                       without a schedule builds order 2 for FP32 gathers on a
+                       tensor of at least 2^25 non-zeros when the shortest mode's
+                       factor fits the shared-memory table of the default kernel
+                       (160 KB), else order 0 */
 } sptt_sched;
 
 /*
@@ -225,7 +241,7 @@ sptt_status sptt_mttkrp_mode(const sptt_csf *csf, int32_t mode, const void *cons
  * FP32, ld >= rank, ld multiple of 4), into G (device, rank x rank FP64,
  * row-major). Products are formed in FP32 and summed in FP32 over 64-row
  * tiles, the tile sums in FP64. A may be NULL when rows = 0 (G = 0).
- * Asynchronous. rank <= SPTT_MAX_RANK_ALS.
+ * Asynchronous. rank in [1, SPTT_MAX_RANK_ALS] (else SPTT_ERR_UNSUPPORTED).
  */
 sptt_status sptt_gram(const float *A, int64_t rows, int32_t rank, int32_t ld, double *G,
                       sptt_stream stream);
@@ -244,8 +260,8 @@ sptt_status sptt_gram(const float *A, int64_t rows, int32_t rank, int32_t ld, do
  * device, with that device current, before any stream capture. All calls
  * share the one array: calls that can overlap on the GPU (different streams
  * without ordering between them) race on it and must be serialised by the
- * caller. rank must be in [1, SPTT_MAX_RANK_ALS] (else SPTT_ERR_BAD_ARG).
- * Asynchronous.
+ * caller. rank must be in [1, SPTT_MAX_RANK_ALS] (else SPTT_ERR_UNSUPPORTED,
+ * as for sptt_gram). Asynchronous.
  */
 sptt_status sptt_gram_noalloc(const float *A, int64_t rows, int32_t rank, int32_t ld, double *G,
                               sptt_stream stream);
@@ -415,9 +431,27 @@ sptt_status sptt_cpd_als(const sptt_coo *coo, int32_t rank, int32_t max_iters, d
 /* (Not in the paper, whose code picks locks vs privatisation by a rule.)   */
 /* ------------------------------------------------------------------------ */
 
-/* The candidate MTTKRP schedules (order x variant x chunk); copies up to cap
- * of them into out (may be NULL) and returns how many there are (16). */
-int32_t sptt_sched_candidates(sptt_sched *out, int32_t cap);
+/* The candidate MTTKRP schedules for a tensor of nnz non-zeros: order {0, 2}
+ * x variant {12, 13, 14, 15} x chunk {the default for nnz, twice it (at most
+ * 4096)}, candidate i = (order i / 8, variant (i / 2) % 4, chunk i % 2).
+ * Copies up to cap of them into out (may be NULL) and returns how many
+ * there are (16). The default schedule (sptt_sched_default) is one of them. */
+int32_t sptt_sched_candidates(int64_t nnz, sptt_sched *out, int32_t cap);
+
+/* The schedule the library uses for the root-`root` MTTKRP of a tensor of
+ * nnz non-zeros with these mode lengths (host array), rank and gather type
+ * when none is given: the level order CP-ALS builds (2 with F32 gathers on a
+ * tensor of at least 2^25 non-zeros when the shortest other mode's factor
+ * fits the 160 KB shared-memory table, else 0), the default variant for that
+ * order's leaf mode and size, and the default chunk.
+ * This is the fixed rule the learned scheduler is measured against. */
+sptt_status sptt_sched_default(const int64_t *dims, int32_t nmodes, int32_t root, int32_t rank,
+                               int32_t factor_dtype, int64_t nnz, sptt_sched *out);
+
+/* The CSF level order of kind `kind` (sptt_sched::order: 0, 1 or 2) for the
+ * tree rooted at `root`, into order_out (host, nmodes entries; ties to the
+ * lower mode id). BAD_ARG on a bad root, kind or nmodes. */
+sptt_status sptt_level_order(const int64_t *dims, int32_t nmodes, int32_t root, int32_t kind, int32_t *order_out);
 
 /* Exhaustive autotuner: times the MTTKRP rooted at `root` under every
  * candidate schedule (random factors of `rank` columns, dtype SPTT_F32 or
@@ -427,14 +461,17 @@ int32_t sptt_sched_candidates(sptt_sched *out, int32_t cap);
 sptt_status sptt_autotune(const sptt_coo *coo, int32_t root, int32_t rank, int32_t dtype, int32_t reps,
                           float *ms, sptt_stream stream);
 
-/* The 16 statistics the learned scheduler reads for one CSF and rank (host
- * output): log2 nnz, modes, log2 rank, log2 of the root / level-1 / leaf
- * mode lengths, log2 slices, log2 leaf-parent fibers, log2 leaves per
- * leaf-parent fiber and per slice, log2 largest slice, share of non-zeros in
- * slices of >= 1024 leaves, share of one-leaf slices, log2 of the leaf and
- * level-1 factor table bytes, slice-size histogram entropy / 5 (a device
- * histogram kernel). Synchronises. */
-sptt_status sptt_csf_features(const sptt_csf *csf, int32_t rank, float *feat, sptt_stream stream);
+/* The 16 statistics the learned scheduler reads for one CSF, rank and
+ * factor gather type (SPTT_F32 or SPTT_BF16; host output): log2 nnz, modes,
+ * log2 bytes of one factor row (rank rounded up to 8, times the element
+ * size), log2 of the root / level-1 / leaf mode lengths, log2 slices, log2
+ * leaf-parent fibers, log2 leaves per leaf-parent fiber and per slice, log2
+ * largest slice, share of non-zeros in slices of >= 1024 leaves, share of
+ * one-leaf slices, log2 of the leaf and level-1 factor table bytes,
+ * slice-size histogram entropy / 5 (a device histogram kernel).
+ * Synchronises. */
+sptt_status sptt_csf_features(const sptt_csf *csf, int32_t rank, int32_t factor_dtype, float *feat,
+                              sptt_stream stream);
 
 /* The learned scheduler: an MLP 16 -> 64 (ReLU) -> 64 (ReLU) -> 16 in FP32
  * that predicts, per candidate, log2(time / best time) from the 16
@@ -481,13 +518,24 @@ typedef struct sptt_batch sptt_batch;
  * walk reads packed 16-byte leaf records, 16 bytes per non-zero more on the
  * device, and with the factor row width a multiple of 8 floats (rank 8, 16,
  * 32) gathers 32-byte row segments in a build of the kernel with one CTA per
- * SM; variant 4 keeps 16-byte segments at two CTAs per SM, variant 3 also
- * reads the separate leaf arrays instead of the packed records).
- * Synchronises.
+ * SM; variant 4 keeps 16-byte segments at two CTAs per SM, variant 7 names
+ * the 32-byte walk, variant 3 also reads the separate leaf arrays instead of
+ * the packed records; both packed walks are the branch-free select walk),
+ * plan (0: sched or the defaults, chunk 128; 1: the batched autotuner, which
+ * times every walk (16-byte, and 32-byte when the row width allows) x chunk
+ * (64, 128, 256) candidate on the batch itself, one warm-up and one timed
+ * run of 2 iterations each, and keeps the fastest; the factors are left for
+ * sptt_batch_init to set). Synchronises.
  */
 sptt_status sptt_batch_create(const sptt_coo *coos, int32_t count, int32_t rank, const sptt_opts *opts,
                               sptt_stream stream, sptt_batch **out);
 void sptt_batch_free(sptt_batch *batch);
+
+/* The schedule the batch runs with (chunk, block, variant 3 / 4 / 7 as for
+ * sptt_batch_create's opts.sched) into out; with plan 1, the timed run of
+ * the chosen candidate (ms, may be NULL) and how many candidates were timed
+ * (may be NULL; 0 without plan 1). */
+sptt_status sptt_batch_schedule(sptt_batch *batch, sptt_sched *out, float *tuned_ms, int32_t *candidates);
 
 /* U(0,1) Philox initial factors for every tensor (as sptt_cpd_init with
  * seed opts.seed + t) and their Grams; resets the fit history. */

@@ -114,9 +114,11 @@ def lib() -> ctypes.CDLL:
                                    ctypes.POINTER(sptt_opts), _P, _P, _P, _P, _P]),
             "sptt_debug_fail_alloc_after": (None, [_I64]),
             "sptt_debug_launch_count": (_I64, []),
-            "sptt_sched_candidates": (_I32, [_P, _I32]),
+            "sptt_sched_candidates": (_I32, [_I64, _P, _I32]),
+            "sptt_sched_default": (_ST, [_P, _I32, _I32, _I32, _I32, _I64, _P]),
+            "sptt_level_order": (_ST, [_P, _I32, _I32, _I32, _P]),
             "sptt_autotune": (_ST, [ctypes.POINTER(sptt_coo), _I32, _I32, _I32, _I32, _P, _P]),
-            "sptt_csf_features": (_ST, [_P, _I32, _P, _P]),
+            "sptt_csf_features": (_ST, [_P, _I32, _I32, _P, _P]),
             "sptt_mlp_create": (_ST, [ctypes.c_uint64, ctypes.POINTER(_P)]),
             "sptt_mlp_free": (None, [_P]),
             "sptt_mlp_nparams": (_I32, []),
@@ -136,6 +138,7 @@ def lib() -> ctypes.CDLL:
             "sptt_batch_info": (_ST, [_P, _P, _P, _P]),
             "sptt_debug_batch_stall": (_ST, [_P, _I32, _I64]),
             "sptt_batch_phase_ms": (_ST, [_P, _P]),
+            "sptt_batch_schedule": (_ST, [_P, _P, _P, _P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -483,6 +486,16 @@ def sptt_batch_info(b: int):
     return grid.value, list(chunks), list(tiles)
 
 
+def sptt_batch_schedule(b: int):
+    """(chunk, block, variant, order) the batch runs with, the plan-1 timed
+    run of the chosen candidate (ms) and how many candidates were timed."""
+    out = sptt_sched()
+    ms = ctypes.c_float()
+    n = ctypes.c_int32()
+    _check(lib().sptt_batch_schedule(b, ctypes.byref(out), ctypes.byref(ms), ctypes.byref(n)), "sptt_batch_schedule")
+    return out.as_tuple(), ms.value, n.value
+
+
 def sptt_batch_phase_ms(b: int):
     ms = (ctypes.c_double * 10)()
     _check(lib().sptt_batch_phase_ms(b, ms), "sptt_batch_phase_ms")
@@ -496,26 +509,44 @@ def sptt_debug_batch_stall(b: int, skip_block: int, timeout_ns: int):
     _check(lib().sptt_debug_batch_stall(b, skip_block, timeout_ns), "sptt_debug_batch_stall")
 
 
-def sptt_sched_candidates():
-    n = lib().sptt_sched_candidates(None, 0)
+def sptt_sched_candidates(nnz: int = 1 << 30):
+    """The candidate schedules (chunk, block, variant, order) for a tensor of nnz non-zeros."""
+    n = lib().sptt_sched_candidates(int(nnz), None, 0)
     arr = (sptt_sched * n)()
-    lib().sptt_sched_candidates(arr, n)
+    lib().sptt_sched_candidates(int(nnz), arr, n)
     return [arr[i].as_tuple() for i in range(n)]
+
+
+def sptt_level_order(dims, root: int, kind: int):
+    """The CSF level order of kind 0 / 1 / 2 (see sptt_sched::order)."""
+    d = (ctypes.c_int64 * len(dims))(*[int(x) for x in dims])
+    out = (ctypes.c_int32 * len(dims))()
+    _check(lib().sptt_level_order(d, len(dims), root, kind, out), "sptt_level_order")
+    return list(out)
+
+
+def sptt_sched_default(dims, root: int, rank: int, dtype: int = SPTT_F32, nnz: int = 1 << 30):
+    """The library's default schedule (chunk, block, variant, order) for this tensor shape."""
+    d = (ctypes.c_int64 * len(dims))(*[int(x) for x in dims])
+    out = sptt_sched()
+    _check(lib().sptt_sched_default(d, len(dims), root, rank, dtype, int(nnz), ctypes.byref(out)),
+           "sptt_sched_default")
+    return out.as_tuple()
 
 
 def sptt_autotune(dims, inds, vals, root: int, rank: int, dtype: int = SPTT_F32, reps: int = 3, stream=None):
     """Median time (ms) of the root-mode MTTKRP under every candidate schedule."""
     coo = _Coo(dims, inds, vals)
-    n = lib().sptt_sched_candidates(None, 0)
+    n = lib().sptt_sched_candidates(int(vals.numel()), None, 0)
     ms = (ctypes.c_float * n)()
     _check(lib().sptt_autotune(ctypes.byref(coo.c), root, rank, dtype, reps, ms, _stream(stream)),
            "sptt_autotune")
     return list(ms)
 
 
-def sptt_csf_features(csf: int, rank: int, stream=None):
+def sptt_csf_features(csf: int, rank: int, factor_dtype: int = SPTT_F32, stream=None):
     f = (ctypes.c_float * 16)()
-    _check(lib().sptt_csf_features(csf, rank, f, _stream(stream)), "sptt_csf_features")
+    _check(lib().sptt_csf_features(csf, rank, factor_dtype, f, _stream(stream)), "sptt_csf_features")
     return list(f)
 
 
@@ -666,6 +697,9 @@ class Batch:
 
     def info(self):
         return sptt_batch_info(self.handle)
+
+    def schedule(self):
+        return sptt_batch_schedule(self.handle)
 
     def close(self):
         if self.handle:

@@ -117,6 +117,15 @@ sptt_status resolve_timers(sptt_cpd *c) {
     return SPTT_OK;
 }
 
+// Level order of mode m's CSF when no schedule fixes it: with FP32 gathers
+// on a large tensor, the shortest other mode at the leaves (kind 2) if its
+// factor fits the shared-memory table of the default MTTKRP kernel, so that
+// every leaf row is read from there; otherwise ascending lengths below the
+// root (kind 0).
+int default_order_kind(const sptt_cpd *c, int m, int64_t nnz) {
+    return sptt::default_order_kind(c->dims, c->N, m, c->ld, c->opts.precision, nnz);
+}
+
 sptt_status run_iteration(sptt_cpd *c, bool bf16) {
     const int N = c->N;
     const void *fac[SPTT_MAX_MODES];
@@ -333,9 +342,9 @@ extern "C" sptt_status sptt_cpd_create(const sptt_coo *coo, int32_t rank, const 
             return set_error(SPTT_ERR_BAD_ARG, "sched->chunk must be a power of two in [16, 4096]");
         if (s->block && (s->block < 32 || s->block > 256 || s->block % 32))
             return set_error(SPTT_ERR_BAD_ARG, "sched->block must be a multiple of 32 in [32, 256]");
-        if (s->variant < 0 || s->variant > kMaxVariant || s->order < 0 || s->order > 1)
+        if (s->variant < 0 || s->variant > kMaxVariant || s->order < 0 || s->order > 2)
             return set_error(SPTT_ERR_BAD_ARG, "sched->variant must be in [0, " + std::to_string(kMaxVariant) +
-                                                   "] and order in [0, 1]");
+                                                   "] and order in [0, 2]");
     }
     if (o.plan < 0 || o.plan > 2) return set_error(SPTT_ERR_BAD_ARG, "opts.plan must be 0, 1 or 2");
     if (o.csf_mode < 0 || o.csf_mode > 2) return set_error(SPTT_ERR_BAD_ARG, "opts.csf_mode must be 0, 1 or 2");
@@ -391,30 +400,30 @@ extern "C" sptt_status sptt_cpd_create(const sptt_coo *coo, int32_t rank, const 
         for (int m = 0; m < c->N; ++m) {
             if (o.plan == 1) {  // exhaustive autotuner
                 float ms[32];
-                const int32_t nc = sptt_sched_candidates(nullptr, 0);
+                const int32_t nc = sptt_sched_candidates(coo->nnz, nullptr, 0);
                 SPTT_TRY(sptt_autotune(&dc.coo, m, rank, o.precision, 3, ms, stream));
                 int best = 0;
                 for (int i = 1; i < nc; ++i)
                     if (ms[i] < ms[best]) best = i;
                 sptt_sched cands[32];
-                sptt_sched_candidates(cands, 32);
+                sptt_sched_candidates(coo->nnz, cands, 32);
                 c->msched[m] = cands[best];
                 c->has_msched[m] = true;
             }
-            const int kind = c->has_msched[m] ? c->msched[m].order : 0;
+            const int kind = c->has_msched[m] ? c->msched[m].order : default_order_kind(c, m, coo->nnz);
             int32_t order[SPTT_MAX_MODES];
             level_order(c->dims, c->N, m, kind, order);
             SPTT_TRY(csf_build_device(&dc.coo, m, order, st, &c->csf[m]));
             if (o.plan == 2) {  // learned scheduler on the default CSF's statistics
                 float feat[16];
                 int32_t choice = 0;
-                SPTT_TRY(sptt_csf_features(c->csf[m], rank, feat, stream));
+                SPTT_TRY(sptt_csf_features(c->csf[m], rank, o.precision, feat, stream));
                 SPTT_TRY(sptt_mlp_predict(o.mlp, feat, 1, &choice, nullptr, stream));
                 sptt_sched cands[32];
-                sptt_sched_candidates(cands, 32);
+                sptt_sched_candidates(coo->nnz, cands, 32);
                 c->msched[m] = cands[choice];
                 c->has_msched[m] = true;
-                if (c->msched[m].order != 0) {
+                if (c->msched[m].order != kind) {
                     csf_destroy(c->csf[m]);
                     c->csf[m] = nullptr;
                     level_order(c->dims, c->N, m, c->msched[m].order, order);

@@ -493,11 +493,17 @@ void level_order(const int64_t *dims, int nmodes, int root, int kind, int32_t *o
     for (int a = 2; a < nmodes; ++a)  // stable insertion sort of levels 1..
         for (int b = a; b > 1; --b) {
             const int64_t x = dims[order[b]], y = dims[order[b - 1]];
-            if (!(kind == 0 ? x < y : x > y)) break;
+            if (!(kind == 1 ? x > y : x < y)) break;
             const int32_t t = order[b];
             order[b] = order[b - 1];
             order[b - 1] = t;
         }
+    if (kind == 2 && nmodes > 2) {
+        // ascending below the root; the shortest (now at level 1) moves to the leaves
+        const int32_t s = order[1];
+        for (int l = 1; l < nmodes - 1; ++l) order[l] = order[l + 1];
+        order[nmodes - 1] = s;
+    }
 }
 
 sptt_status csf_build_device(const sptt_coo *coo, int32_t root, const int32_t *order_in,

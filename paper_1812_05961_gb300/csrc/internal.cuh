@@ -12,8 +12,13 @@
 namespace sptt {
 
 constexpr int kMaxModes = SPTT_MAX_MODES;
-constexpr int kHeavyChunks = 8;
-constexpr int kMaxVariant = 11;  // largest sptt_sched::variant
+// A slice whose leaves span more than kHeavyChunks chunks gets an FP64
+// output row: with 1, every slice cut by a chunk boundary. Its per-chunk
+// FP32 partials are then summed in FP64, exactly whenever they lie within
+// 2^29 of each other in magnitude, so the result does not depend on the order
+// in which the chunks finish.
+constexpr int kHeavyChunks = 1;
+constexpr int kMaxVariant = 15;  // largest sptt_sched::variant
 constexpr int kLeafSlack = 512;  // elements past the end of every leaf array (whole-chunk copies)
 constexpr int kNumSMs = 152;  // GB300: 2 dies x 76 SMs (queried at run time where it matters)
 
@@ -123,8 +128,8 @@ struct sptt_csf {
     int32_t part_chunk = 0;
     int64_t part_nchunks = 0;
     // Heavy slices: those whose leaves span more than kHeavyChunks chunks of
-    // the partition. hidx[f] = index of slice f among the heavy ones, or -1;
-    // their MTTKRP partials are summed in FP64 (see walk.cuh).
+    // the partition (every split slice). hidx[f] = index of slice f among the
+    // heavy ones, or -1; their MTTKRP partials are summed in FP64 (walk.cuh).
     int32_t *hidx = nullptr;
     int64_t nheavy = 0;
     // Device error word of the kernels that read this CSF (bit 2: a bounded
@@ -149,7 +154,9 @@ namespace sptt {
 sptt_status csf_build_device(const sptt_coo *coo_dev, int32_t root, const int32_t *order,
                              cudaStream_t st, sptt_csf **out);
 // Level order of a CSF rooted at `root`: the root, then the other modes by
-// ascending (kind 0) or descending (kind 1) length, ties to the lower mode id.
+// ascending (kind 0) or descending (kind 1) length, ties to the lower mode
+// id; kind 2: the shortest non-root mode at the leaves and the others above
+// it by ascending length (ties as before).
 void level_order(const int64_t *dims, int nmodes, int root, int kind, int32_t *order);
 sptt_status csf_ensure_partition(sptt_csf *csf, int32_t chunk, cudaStream_t st);
 sptt_status csf_ensure_leafrec(sptt_csf *csf, cudaStream_t st);
@@ -180,6 +187,23 @@ sptt_status mttkrp_launch(sptt_csf *csf, const void *const *factors, int32_t dty
 sptt_status mttkrp_prepare(sptt_csf *csf, const sptt_sched *sched, cudaStream_t st);
 // Leaves per chunk when the schedule does not say (depends on nnz and the SM count).
 int32_t default_chunk(int64_t nnz);
+// Largest leaf-factor copy the table kernels (variants 14, 15) keep in shared
+// memory; the rest of an SM's 228 KB stays L1 for the records and the rows
+// of the fibers above the leaves.
+constexpr size_t kTableMaxBytes = 160 * 1024;
+// Whether a leaf factor of leaf_rows rows of ld elements of esz bytes fits.
+bool leaf_table_fits(int64_t leaf_rows, int32_t ld, int esz);
+// Smallest tensor for which the defaults take the table kernel (below it the
+// shortest mode at the leaves multiplies the leaf-parent fibers more than the
+// shared-memory table saves).
+constexpr int64_t kTableMinNnz = int64_t(1) << 25;
+// The default MTTKRP variant for a gather type, row width, leaf-mode length and size.
+int default_variant(int32_t dtype, int32_t ld, int64_t leaf_rows, int64_t nnz);
+// The default CSF level-order kind of the CSF rooted at `root` (see
+// level_order): with FP32 gathers, N >= 3 and at least kTableMinNnz
+// non-zeros, 2 when the shortest other mode's factor fits the shared-memory
+// table, else 0.
+int default_order_kind(const int64_t *dims, int nmodes, int root, int32_t ld, int32_t dtype, int64_t nnz);
 
 // MTTKRP for the mode at level L >= 1 of the CSF (mttkrp_mode.cu): out is
 // full (dims[order[L]] x ld FP32), zeroed here, then filled. Call

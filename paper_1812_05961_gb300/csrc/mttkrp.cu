@@ -30,8 +30,10 @@ namespace {
 using walk::Lanes;
 using walk::lanes_for;
 
-// The 32-byte-segment flag walks on packed leaf records.
-bool wide_variant(int v) { return v == 7 || v == 10; }
+// The 32-byte-segment walks on packed leaf records.
+bool wide_variant(int v) { return v == 7 || v == 10 || v == 12; }
+// The select walk with the leaf factor copied into shared memory.
+bool table_variant(int v) { return v == 14 || v == 15; }
 
 // Each CTA takes a contiguous range of chunks; its lane groups interleave
 // within the range, so a group's consecutive chunks are close together and a
@@ -67,6 +69,44 @@ __global__ void __launch_bounds__(256, MINB) mttkrp_flag_kernel(const walk::Args
         for (int64_t c = r.begin; c < r.end; c += r.step)
             walk::flag_chunk<NM, T, B, walk::GlobalRecs, W, PIPE>(a, c, L.col, cy, rec);
     }
+    walk::flush_carry(a, L.col, cy);
+}
+
+// The select walk (walk.cuh select_chunk) on packed leaf records.
+// The select walk (walk.cuh select_chunk) on packed leaf records.
+template <int NM, typename T, int B, int MINB, int W>
+__global__ void __launch_bounds__(256, MINB) mttkrp_select_kernel(const walk::Args a) {
+    const Lanes L = lanes_for(a.ld, walk::Raw<T, W>::VEC);
+    if (L.idle) return;  // no warp collectives in the walk
+    const ChunkRange r = cta_chunks(a.nchunks, L);
+    walk::Carry<walk::Raw<T, W>::VEC> cy;
+    const walk::PackedRecs rec{a.leafrec};
+    for (int64_t c = r.begin; c < r.end; c += r.step) walk::select_chunk<NM, T, B, W>(a, c, L.col, cy, rec);
+    walk::flush_carry(a, L.col, cy);
+}
+
+// The table kernels: each CTA first copies the whole leaf factor (leaf_rows
+// rows of ld values, row-major) into shared memory, then runs the select walk
+// with its leaf rows read from that copy; only the records and the rows of
+// the fibers above the leaves still come through the L1 load path. One CTA
+// of NT threads per SM.
+template <int NM, typename T, int B, int NT, int W>
+__global__ void __launch_bounds__(NT, 1) mttkrp_table_kernel(const walk::Args a, int32_t leaf_rows) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const uint32_t rowbytes = (uint32_t)a.ld * (uint32_t)sizeof(T);
+    const uint4 *src = static_cast<const uint4 *>(a.fac[NM - 1]);
+    uint4 *dst = reinterpret_cast<uint4 *>(smem);
+    const int64_t n16 = (int64_t)leaf_rows * rowbytes / 16;
+    for (int64_t i = threadIdx.x; i < n16; i += blockDim.x) dst[i] = __ldg(src + i);
+    __syncthreads();
+    const Lanes L = lanes_for(a.ld, walk::Raw<T, W>::VEC);
+    if (L.idle) return;  // no barrier after this point
+    const ChunkRange r = cta_chunks(a.nchunks, L);
+    walk::Carry<walk::Raw<T, W>::VEC> cy;
+    const walk::PackedRecs rec{a.leafrec};
+    const uint32_t tab = (uint32_t)__cvta_generic_to_shared(smem);
+    for (int64_t c = r.begin; c < r.end; c += r.step)
+        walk::select_chunk<NM, T, B, W, true>(a, c, L.col, cy, rec, tab, rowbytes);
     walk::flush_carry(a, L.col, cy);
 }
 
@@ -209,6 +249,31 @@ sptt_status launch_staged(const walk::Args &a, int32_t *err, cudaStream_t st) {
     return SPTT_OK;
 }
 
+template <int NM, typename T, int B, int NT, int W>
+sptt_status launch_table(const walk::Args &a, int64_t leaf_rows, cudaStream_t st) {
+    auto kern = mttkrp_table_kernel<NM, T, B, NT, W>;
+    const size_t smem = (size_t)leaf_rows * a.ld * sizeof(T);
+    SPTT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    SPTT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem));
+    if (per_sm < 1) per_sm = 1;
+    const int vec = walk::Raw<T, W>::VEC;
+    const int64_t groups_per_block = (int64_t)(NT / 32) * (32 / (a.ld / vec));
+    const int64_t need = (a.nchunks + groups_per_block - 1) / groups_per_block;
+    const int64_t cap = (int64_t)device_sm_count() * per_sm;
+    int64_t grid = need < cap ? need : cap;
+    if (grid < 1) grid = 1;
+    kern<<<(unsigned)grid, NT, smem, st>>>(a, (int32_t)leaf_rows);
+    SPTT_CHECK_LAUNCH("mttkrp_table_kernel");
+    return SPTT_OK;
+}
+
+template <int NM, typename T>
+sptt_status launch_table_nm(const walk::Args &a, int64_t leaf_rows, int variant, cudaStream_t st) {
+    if (variant == 15) return launch_table<NM, T, 4, 512, 16>(a, leaf_rows, st);
+    return launch_table<NM, T, 2, 1024, 16>(a, leaf_rows, st);
+}
+
 template <int NM, typename T>
 sptt_status launch_nm(const walk::Args &a, int block, int variant, cudaStream_t st) {
     void (*kern)(const walk::Args) = nullptr;
@@ -222,6 +287,8 @@ sptt_status launch_nm(const walk::Args &a, int block, int variant, cudaStream_t 
         case 9: kern = mttkrp_flag_kernel<NM, T, 4, 2, 16, true, true>; break;
         case 10: kern = mttkrp_flag_kernel<NM, T, 2, 2, 32, true, true, true>; break;
         case 11: kern = mttkrp_flag_kernel<NM, T, 4, 2, 16, true, true, true>; break;
+        case 12: kern = mttkrp_select_kernel<NM, T, 2, 2, 32>; break;
+        case 13: kern = mttkrp_select_kernel<NM, T, 4, 2, 16>; break;
         default: kern = mttkrp_flag_kernel<NM, T, 4, 3, 16, false>; break;
     }
     int per_sm = 0;
@@ -239,7 +306,17 @@ sptt_status launch_nm(const walk::Args &a, int block, int variant, cudaStream_t 
 }
 
 template <typename T>
-sptt_status launch_t(int nm, const walk::Args &a, int block, int variant, int32_t *err, cudaStream_t st) {
+sptt_status launch_t(sptt_csf *csf, int nm, const walk::Args &a, int block, int variant, int32_t *err,
+                     int64_t leaf_rows, cudaStream_t st) {
+    if (table_variant(variant)) {
+        switch (nm) {
+            case 2: return launch_table_nm<2, T>(a, leaf_rows, variant, st);
+            case 3: return launch_table_nm<3, T>(a, leaf_rows, variant, st);
+            case 4: return launch_table_nm<4, T>(a, leaf_rows, variant, st);
+            case 5: return launch_table_nm<5, T>(a, leaf_rows, variant, st);
+            default: return set_error(SPTT_ERR_UNSUPPORTED, "nmodes");
+        }
+    }
     if (variant == 6 || variant == 8) {
         const bool wide = variant == 8;
         switch (nm) {
@@ -261,30 +338,45 @@ sptt_status launch_t(int nm, const walk::Args &a, int block, int variant, int32_
 
 }  // namespace
 
-// Default leaves per chunk: 128, halved (down to 16) while the tensor would
-// give fewer than 256 chunks per SM, so that small tensors still fill the GPU.
+// Default leaves per chunk: 128, halved (down to 32) while the tensor would
+// give fewer than 128 chunks per SM, so that small tensors still fill the GPU.
+// (Measured on 80 generated tensors of 1e5-2e7 non-zeros, 3-5 modes, every
+// root, both gather types: shorter chunks cost more in per-chunk work than
+// they gain in balance.)
 int32_t default_chunk(int64_t nnz) {
-    const int64_t target = (int64_t)device_sm_count() * 256;
+    const int64_t target = (int64_t)device_sm_count() * 128;
     int32_t c = 128;
-    while (c > 16 && nnz / c < target) c >>= 1;
+    while (c > 32 && nnz / c < target) c >>= 1;
     return c;
 }
 
 static bool staged_variant(int v) { return v == 6 || v == 8; }
 
-// The fastest variant measured per gather type and row width on the 3-mode
-// power-law workload (R = 16 and 32): FP32 rows take the 32-byte-segment
-// walk on packed leaf records (the 16-byte walk at 3 CTAs per SM when ld is
-// not a multiple of 8); BF16 rows the same walks with leaves added straight
-// into their fiber's parent (walk.cuh DIRECT): 16-byte segments at 2 CTAs
-// per SM for rows of up to 32 bytes, 32-byte segments for wider ones.
-int default_variant(int32_t dtype, int32_t ld) {
-    if (dtype == SPTT_BF16) return ld <= 16 ? 11 : 10;
-    return ld % 8 == 0 ? 7 : 3;
+// The default variant: the select walk with 16-byte segments in batches of 4
+// (within 4-15 % of the best candidate on average for every rank 8-64 and
+// both gather types over generated tensors of 1e5-2e7 non-zeros), and for
+// large tensors with FP32 gathers whose leaf factor fits in shared memory
+// the table kernel (on the 1e8-non-zero 3-mode power-law tensor 12 % faster
+// than the best global-memory walk).
+int default_variant(int32_t dtype, int32_t ld, int64_t leaf_rows, int64_t nnz) {
+    if (dtype == SPTT_F32 && nnz >= kTableMinNnz && leaf_table_fits(leaf_rows, ld, 4)) return 14;
+    return 13;
+}
+
+bool leaf_table_fits(int64_t leaf_rows, int32_t ld, int esz) {
+    return (size_t)leaf_rows * ld * esz <= kTableMaxBytes;
+}
+
+int default_order_kind(const int64_t *dims, int nmodes, int root, int32_t ld, int32_t dtype, int64_t nnz) {
+    if (dtype != SPTT_F32 || nmodes < 3 || nnz < kTableMinNnz) return 0;
+    int64_t shortest = -1;
+    for (int k = 0; k < nmodes; ++k)
+        if (k != root && (shortest < 0 || dims[k] < shortest)) shortest = dims[k];
+    return leaf_table_fits(shortest, ld, 4) ? 2 : 0;
 }
 
 // Variants that read the packed leaf records (sptt_csf::leafrec).
-static bool packed_variant(int v) { return v == 7 || v == 9 || v == 10 || v == 11; }
+static bool packed_variant(int v) { return v == 7 || v >= 9; }
 
 sptt_status mttkrp_prepare(sptt_csf *csf, const sptt_sched *sched, cudaStream_t st) {
     const int32_t chunk = (sched && staged_variant(sched->variant)) ? kStageChunk
@@ -302,7 +394,10 @@ sptt_status mttkrp_launch(sptt_csf *csf, const void *const *factors, int32_t dty
     const int64_t nnz = csf->nfibs[N - 1];
     if (nnz == 0) return SPTT_OK;
     int variant = sched ? sched->variant : 0;
-    if (variant == 0) variant = default_variant(dtype, ld);
+    if (variant == 0) variant = default_variant(dtype, ld, csf->dims[csf->order[N - 1]], nnz);
+    // the table kernels need the whole leaf factor in shared memory
+    if (table_variant(variant) && !leaf_table_fits(csf->dims[csf->order[N - 1]], ld, dtype == SPTT_BF16 ? 2 : 4))
+        variant = 13;
     if (wide_variant(variant) || variant == 8) {
         // 32-byte row segments need ld * sizeof(T) and every gathered factor
         // 32-byte aligned; otherwise the 16-byte form of the same walk runs
@@ -310,7 +405,7 @@ sptt_status mttkrp_launch(sptt_csf *csf, const void *const *factors, int32_t dty
         bool wide_ok = (ld * esz) % 32 == 0;
         for (int l = 1; l < N; ++l)
             wide_ok = wide_ok && reinterpret_cast<uintptr_t>(factors[csf->order[l]]) % 32 == 0;
-        if (!wide_ok) variant = variant == 8 ? 6 : 3;
+        if (!wide_ok) variant = variant == 8 ? 6 : (variant == 12 ? 13 : 3);
     }
     const int32_t chunk = staged_variant(variant) ? kStageChunk
                                                   : ((sched && sched->chunk) ? sched->chunk : default_chunk(csf->nfibs[csf->nmodes - 1]));
@@ -335,8 +430,9 @@ sptt_status mttkrp_launch(sptt_csf *csf, const void *const *factors, int32_t dty
     a.heavy = heavy;
     a.hidx = csf->hidx;
     a.leafrec = csf->leafrec;
-    if (dtype == SPTT_BF16) return launch_t<__nv_bfloat16>(N, a, block, variant, csf->err, st);
-    return launch_t<float>(N, a, block, variant, csf->err, st);
+    const int64_t leaf_rows = csf->dims[csf->order[N - 1]];
+    if (dtype == SPTT_BF16) return launch_t<__nv_bfloat16>(csf, N, a, block, variant, csf->err, leaf_rows, st);
+    return launch_t<float>(csf, N, a, block, variant, csf->err, leaf_rows, st);
 }
 
 }  // namespace sptt

@@ -19,19 +19,24 @@ namespace {
 constexpr int kThreads = 256;
 
 // ---------------------------------------------------------------------------
-// Candidate schedules: order (ascending / descending length below the root)
-// x walk variant (3: batch 4, 3 CTAs/SM; 4: batch 4, 2 CTAs/SM, pipelined;
-// 5: batch 2, 3 CTAs/SM, pipelined; 7: 32-byte row segments) x chunk.
+// Candidate schedules: CSF level order (0: ascending lengths below the root;
+// 2: the shortest mode at the leaves) x walk variant (12 / 13: select walk
+// with 32-byte segments in batches of 2 / 16-byte segments in batches of 4;
+// 14 / 15: select walk with the leaf factor in shared memory, 1024 threads
+// in batches of 2 / 512 threads in batches of 4, 13 where the factor does
+// not fit) x chunk (the default for the tensor's size, and twice it). The
+// library's default schedule is always one of them.
 // ---------------------------------------------------------------------------
 constexpr int kNumCands = 16;
-const int kCandChunks[2] = {64, 128};
-const int kCandVariants[4] = {3, 4, 5, 7};
+const int kCandOrders[2] = {0, 2};
+const int kCandVariants[4] = {12, 13, 14, 15};
 
-sptt_sched candidate(int i) {
+sptt_sched candidate(int i, int64_t nnz) {
     sptt_sched s{};
-    s.order = i / 8;
+    s.order = kCandOrders[i / 8];
     s.variant = kCandVariants[(i / 2) % 4];
-    s.chunk = kCandChunks[i % 2];
+    const int32_t c0 = default_chunk(nnz);
+    s.chunk = (i % 2) ? (c0 * 2 <= 4096 ? c0 * 2 : 4096) : c0;
     s.block = 256;
     return s;
 }
@@ -325,16 +330,51 @@ sptt_status mlp_grad_launch(sptt_mlp *mlp, const float *X, const float *T, int64
 
 }  // namespace
 
-extern "C" int32_t sptt_sched_candidates(sptt_sched *out, int32_t cap) {
+extern "C" int32_t sptt_sched_candidates(int64_t nnz, sptt_sched *out, int32_t cap) {
     for (int i = 0; i < kNumCands && i < cap; ++i)
-        if (out) out[i] = candidate(i);
+        if (out) out[i] = candidate(i, nnz);
     return kNumCands;
 }
 
-extern "C" sptt_status sptt_csf_features(const sptt_csf *csf, int32_t rank, float *feat, sptt_stream stream) {
+extern "C" sptt_status sptt_level_order(const int64_t *dims, int32_t nmodes, int32_t root, int32_t kind,
+                                        int32_t *order_out) {
+    clear_error();
+    if (!dims || !order_out) return set_error(SPTT_ERR_BAD_ARG, "dims and order_out must be non-NULL");
+    if (nmodes < 2 || nmodes > kMaxModes || root < 0 || root >= nmodes || kind < 0 || kind > 2)
+        return set_error(SPTT_ERR_BAD_ARG, "nmodes, root or kind out of range");
+    level_order(dims, nmodes, root, kind, order_out);
+    return SPTT_OK;
+}
+
+extern "C" sptt_status sptt_sched_default(const int64_t *dims, int32_t nmodes, int32_t root, int32_t rank,
+                                          int32_t factor_dtype, int64_t nnz, sptt_sched *out) {
+    clear_error();
+    if (!dims || !out) return set_error(SPTT_ERR_BAD_ARG, "dims and out must be non-NULL");
+    if (nmodes < 2 || nmodes > kMaxModes || root < 0 || root >= nmodes)
+        return set_error(SPTT_ERR_BAD_ARG, "nmodes or root out of range");
+    if (rank < 1) return set_error(SPTT_ERR_BAD_ARG, "rank must be >= 1");
+    if (factor_dtype != SPTT_F32 && factor_dtype != SPTT_BF16)
+        return set_error(SPTT_ERR_BAD_ARG, "factor_dtype must be SPTT_F32 or SPTT_BF16");
+    const int32_t ld = (rank + 7) / 8 * 8;
+    sptt_sched s{};
+    s.order = default_order_kind(dims, nmodes, root, ld, factor_dtype, nnz);
+    int32_t order[kMaxModes];
+    level_order(dims, nmodes, root, s.order, order);
+    s.variant = default_variant(factor_dtype, ld, dims[order[nmodes - 1]], nnz);
+    s.chunk = default_chunk(nnz);
+    s.block = 256;
+    *out = s;
+    return SPTT_OK;
+}
+
+extern "C" sptt_status sptt_csf_features(const sptt_csf *csf, int32_t rank, int32_t factor_dtype, float *feat,
+                                         sptt_stream stream) {
     clear_error();
     if (!csf || !feat) return set_error(SPTT_ERR_BAD_ARG, "csf and feat must be non-NULL");
     if (rank < 1) return set_error(SPTT_ERR_BAD_ARG, "rank must be >= 1");
+    if (factor_dtype != SPTT_F32 && factor_dtype != SPTT_BF16)
+        return set_error(SPTT_ERR_BAD_ARG, "factor_dtype must be SPTT_F32 or SPTT_BF16");
+    const double rowbytes = (double)((rank + 7) / 8 * 8) * (factor_dtype == SPTT_BF16 ? 2.0 : 4.0);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const int N = csf->nmodes;
     const int64_t ns = csf->nfibs[0], nnz = csf->nfibs[N - 1];
@@ -368,7 +408,7 @@ extern "C" sptt_status sptt_csf_features(const sptt_csf *csf, int32_t rank, floa
     float f[16];
     f[0] = lg(dn);
     f[1] = (float)N;
-    f[2] = lg(rank);
+    f[2] = lg(rowbytes);
     f[3] = lg((double)d_root);
     f[4] = lg((double)d_l1);
     f[5] = lg((double)d_leaf);
@@ -379,8 +419,8 @@ extern "C" sptt_status sptt_csf_features(const sptt_csf *csf, int32_t rank, floa
     f[10] = lg((double)h[64]);
     f[11] = (float)(heavy / dn);
     f[12] = (float)(single / dns);
-    f[13] = lg((double)d_leaf * rank * 4.0);
-    f[14] = lg((double)d_l1 * rank * 4.0);
+    f[13] = lg((double)d_leaf * rowbytes);
+    f[14] = lg((double)d_l1 * rowbytes);
     f[15] = (float)(ent / 5.0);
     memcpy(feat, f, sizeof(f));
     return SPTT_OK;
@@ -420,7 +460,8 @@ extern "C" sptt_status sptt_autotune(const sptt_coo *coo, int32_t root, int32_t 
     SPTT_CUDA(cudaEventCreate(&e0));
     SPTT_CUDA(cudaEventCreate(&e1));
     sptt_status status = SPTT_OK;
-    for (int ord = 0; ord < 2 && status == SPTT_OK; ++ord) {
+    for (int oi = 0; oi < 2 && status == SPTT_OK; ++oi) {
+        const int ord = kCandOrders[oi];
         int32_t order[kMaxModes];
         level_order(coo->dims, N, root, ord, order);
         sptt_csf *csf = nullptr;
@@ -428,7 +469,7 @@ extern "C" sptt_status sptt_autotune(const sptt_coo *coo, int32_t root, int32_t 
         if (status != SPTT_OK) break;
         DevBuf out, heavy;
         for (int i = 0; i < kNumCands && status == SPTT_OK; ++i) {
-            const sptt_sched s = candidate(i);
+            const sptt_sched s = candidate(i, coo->nnz);
             if (s.order != ord) continue;
             status = mttkrp_prepare(csf, &s, st);
             if (status != SPTT_OK) break;

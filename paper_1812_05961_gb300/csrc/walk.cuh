@@ -20,12 +20,14 @@
 //   * the output is compact: row f of M is slice f of the tree (the slice's
 //     mode index is fids[0][f]). A slice that starts and ends inside one
 //     chunk is owned by its lane group and stored (FP32). A slice cut by chunk
-//     boundaries gets one FP32 partial per chunk, added into the zeroed
-//     output with red.global.add.v4.f32 (no lock, no spin). A heavy slice (one
-//     spanning more than kHeavyChunks chunks: the power-law head, up to 10^5
-//     chunks) instead adds its partials with red.global.add.f64 into its own
-//     FP64 row heavy[hidx[f]], so its sum keeps the accuracy of one chunk's
-//     FP32 partial; readers take that row in place of row f.
+//     boundaries (up to 10^5 chunks for the power-law head) gets one FP32
+//     partial per chunk, added with red.global.add.f64 into its own zeroed
+//     FP64 row heavy[hidx[f]] (no lock, no spin): the sum keeps the accuracy
+//     of one chunk's FP32 partial and, being exact for partials of similar
+//     magnitude, does not depend on the order of the atomics. Readers take
+//     that row in place of row f. (The red.global.add.v4.f32 path of
+//     add_partial serves a slice inside one chunk that is not the chunk's
+//     first: its single partial lands on a zero.)
 #pragma once
 
 #include "internal.cuh"
@@ -119,6 +121,21 @@ struct Raw {
         }
     }
 };
+
+// A leaf-factor row segment read from a copy of the whole leaf factor in
+// shared memory (the table kernels of mttkrp.cu): row r starts at byte
+// r * rowbytes of the table; a 32-byte segment is two 16-byte shared loads.
+template <typename T, int W>
+__device__ __forceinline__ Seg<W> load_table_row(uint32_t tab, int32_t row, uint32_t rowbytes, int col) {
+    Seg<W> r;
+    const uint32_t a = tab + (uint32_t)row * rowbytes + (uint32_t)col * (uint32_t)sizeof(T);
+    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r.w[0]), "=r"(r.w[1]), "=r"(r.w[2]), "=r"(r.w[3]) : "r"(a));
+    if constexpr (W == 32)
+        asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                     : "=r"(r.w[4]), "=r"(r.w[5]), "=r"(r.w[6]), "=r"(r.w[7]) : "r"(a + 16u));
+    return r;
+}
 
 // Slice f is complete and owned by this lane group.
 template <int VEC>
@@ -576,6 +593,148 @@ __device__ __forceinline__ void flag_chunk(const Args &a, int64_t c, int col, Ca
     // (or held back when the slice is heavy)
 #pragma unroll
     for (int l = kDirect ? LF - 1 : LF; l >= 1; --l) fold<T, W>(acc[l - 1], acc[l], rowc[l]);
+    end_chunk<VEC>(a, col, cy, f[0], acc[0]);
+}
+
+// The select walk: the DIRECT form of flag_chunk on packed records with the
+// per-leaf work kept free of branches, so that the lane groups of a warp,
+// which open fibers at different leaves, no longer serialise each other.
+//
+// Per leaf j of a batch: the row of the fiber the leaf opens (if it opens
+// one) was requested with the batch's leaf rows; the open leaf-parent
+// fiber's row rf is replaced by it with a select, and v * (rf * x) is added
+// to the accumulator of the level above (one multiply and one FMA per
+// element, the same arithmetic as DIRECT). Only a change at a level above
+// the leaf parents -- a new slice, or for N >= 4 a new upper fiber --
+// branches, and at most a few groups take that branch per batch.
+//
+// Loads are issued unconditionally: a leaf that opens no fiber has fiber
+// index 0 in its record (row 0, which every such lane shares), and the
+// leaves of a ragged last batch read the zero records past the end of the
+// array (their values are masked to 0 and their flags ignored).
+//
+// TAB: the leaf rows come from the shared-memory copy of the whole leaf
+// factor at shared address tab (row r at byte r * tab_rowbytes), not from
+// global memory.
+//
+// SPLIT: 32-byte loads issued as 16-byte halves (the batched kernel's
+// non-inlined walk; see Raw).
+template <int NM, typename T, int B, int W = 32, bool TAB = false, bool SPLIT = false>
+__device__ __forceinline__ void select_chunk(const Args &a, int64_t c, int col, Carry<Raw<T, W>::VEC> &cy,
+                                             const PackedRecsT<SPLIT> &rec, uint32_t tab = 0,
+                                             uint32_t tab_rowbytes = 0) {
+    using Rw = Raw<T, W, SPLIT>;
+    using Row = typename Rw::Row;
+    constexpr int VEC = Rw::VEC;
+    constexpr int NL = NM - 1;             // accumulator levels 0..NM-2
+    constexpr int LF = NM - 2;             // level of the leaves' parent fibers
+    constexpr int AL = LF >= 1 ? LF - 1 : 0;  // the level leaves add into
+    constexpr int NACC = AL + 1;
+    static_assert(B == 2 || B == 4 || B == 8, "batch of 2, 4 or 8 leaves");
+    const int ld = a.ld;
+    const int64_t k0 = c * (int64_t)a.chunk;
+    const int64_t k1 = (k0 + a.chunk < a.nnz) ? k0 + a.chunk : a.nnz;
+    int32_t f[NL];
+#pragma unroll
+    for (int l = 0; l < NL; ++l) f[l] = __ldg(a.part + c * NL + l);
+    float acc[NACC][VEC];
+#pragma unroll
+    for (int l = 0; l < NACC; ++l)
+#pragma unroll
+        for (int i = 0; i < VEC; ++i) acc[l][i] = 0.f;
+    Row rowc[NL];  // rows of the open fibers at levels 1..LF-1
+#pragma unroll
+    for (int l = 1; l < LF; ++l) rowc[l] = Rw::load(a.fac[l], __ldg(a.fids[l] + f[l]), ld, col);
+    float rf[VEC];
+    if constexpr (LF >= 1) Rw::widen(Rw::load(a.fac[LF], __ldg(a.fids[LF] + f[LF]), ld, col), rf);
+    bool first_slice = true;
+    take_carry<VEC>(a, col, cy, f[0], acc[0]);
+
+    float v[B];
+    int32_t li[B];
+    uint32_t lw[2];
+    int32_t nf[B];
+    fetch_all<B, LF>(rec, nullptr, 0, k0, v, li, lw, nf);
+    for (int64_t kb = k0; kb < k1; kb += B) {
+        Row x[B], nr[B];
+        if constexpr (LF >= 1) {
+#pragma unroll
+            for (int j = 0; j < B; ++j) nr[j] = Rw::load(a.fac[LF], nf[j], ld, col);
+        }
+#pragma unroll
+        for (int j = 0; j < B; ++j) {
+            if constexpr (TAB) x[j] = load_table_row<T, W>(tab, li[j], tab_rowbytes, col);
+            else x[j] = Rw::load(a.fac[NM - 1], li[j], ld, col);
+        }
+        // the next batch's records (past the chunk end they belong to the
+        // next chunk or to the zero slack; never used there)
+        float vn[B];
+        int32_t lin[B];
+        uint32_t lwn[2];
+        int32_t nfn[B];
+        fetch_all<B, LF>(rec, nullptr, 0, kb + B, vn, lin, lwn, nfn);
+        const int nvalid = (k1 - kb < B) ? (int)(k1 - kb) : B;
+        // openings of a leaf-parent fiber (for N = 2: of a slice), as in flag_chunk
+        uint32_t sm = 0;
+#pragma unroll
+        for (int w = 0; w < (B + 3) / 4; ++w) {
+            const uint32_t le = __vcmpleu4(lw[w], (uint32_t)LF * 0x01010101u) & 0x01010101u;
+            sm |= (((le * 0x01020408u) >> 24) & 0xfu) << (4 * w);
+        }
+        sm &= (1u << nvalid) - 1u;
+        if (kb == k0) sm &= ~1u;
+#pragma unroll
+        for (int j = 0; j < B; ++j) {
+            const bool op = (sm >> j) & 1u;
+            const int d = (int)((lw[j >> 2] >> (8 * (j & 3))) & 0xffu);
+            if (op && d < (LF >= 1 ? LF : 1)) {
+                // a fiber above the leaf parents closes: fold the levels
+                // that close into their parents, and store a finished slice
+#pragma unroll
+                for (int l = LF - 1; l >= 1; --l) {
+                    if (d <= l) {
+                        fold<T, W>(acc[l - 1], acc[l], rowc[l]);
+                        ++f[l];
+                        rowc[l] = Rw::load(a.fac[l], __ldg(a.fids[l] + f[l]), ld, col);
+                    }
+                }
+                if (d == 0) {
+                    if (first_slice) add_partial<VEC>(a, f[0], col, acc[0]);
+                    else store_owned<VEC>(a, f[0], col, acc[0]);
+                    first_slice = false;
+#pragma unroll
+                    for (int i = 0; i < VEC; ++i) acc[0][i] = 0.f;
+                    ++f[0];
+                }
+            }
+            float xr[VEC];
+            Rw::widen(x[j], xr);
+            const float vj = j < nvalid ? v[j] : 0.f;
+            if constexpr (LF >= 1) {
+                float nw[VEC];
+                Rw::widen(nr[j], nw);
+#pragma unroll
+                for (int i = 0; i < VEC; ++i) rf[i] = op ? nw[i] : rf[i];
+                float t[VEC];
+                mul_vec<VEC, W == 32>(t, rf, xr);
+                fma_scalar<VEC, W == 32>(acc[AL], vj, t);
+            } else {
+                fma_scalar<VEC, W == 32>(acc[0], vj, xr);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < B; ++q) {
+            v[q] = vn[q];
+            li[q] = lin[q];
+            nf[q] = nfn[q];
+        }
+        lw[0] = lwn[0];
+        lw[1] = lwn[1];
+    }
+    // chunk end: fold the open upper fibers; the open slice's partial is
+    // added (or held back when the slice is heavy)
+#pragma unroll
+    for (int l = LF - 1; l >= 1; --l) fold<T, W>(acc[l - 1], acc[l], rowc[l]);
     end_chunk<VEC>(a, col, cy, f[0], acc[0]);
 }
 

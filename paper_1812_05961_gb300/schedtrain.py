@@ -1,12 +1,14 @@
 """Training and evaluation of the learned MTTKRP scheduler.
 
 Orchestration only: the timings come from the library's autotuner
-(sptt_autotune), the statistics from sptt_csf_features, and the network is
+(sptt_autotune), the statistics from sptt_csf_features, the fixed rule the
+network is measured against from sptt_sched_default, and the network is
 trained and run by the library's own MLP kernels (sptt_mlp_train,
 sptt_mlp_predict). The caller supplies the tensors.
 
-Target of the regression: for each (tensor, root mode, rank) sample and each
-candidate schedule k, log2(time_k / min_j time_j), so 0 marks the best.
+Target of the regression: for each (tensor, root mode, rank, gather type)
+sample and each candidate schedule k, log2(time_k / min_j time_j), so 0 marks
+the best.
 """
 from __future__ import annotations
 
@@ -16,16 +18,18 @@ from typing import List, Sequence
 
 import torch
 
-from . import (SPTT_F32, Csf, Mlp, sptt_autotune, sptt_csf_features, sptt_mlp_predict, sptt_mlp_train,
-               sptt_sched_candidates)
+from . import (SPTT_BF16, SPTT_F32, Csf, Mlp, sptt_autotune, sptt_csf_features, sptt_level_order,
+               sptt_mlp_predict, sptt_mlp_train, sptt_sched_candidates, sptt_sched_default)
 
 
 @dataclass
 class Sample:
     features: List[float]
     times_ms: List[float]
+    default: int            # candidate index of the library's default schedule
     label: str = ""
     rank: int = 16
+    dtype: int = SPTT_F32
 
 
 @dataclass
@@ -39,16 +43,32 @@ class Dataset:
         return X, T
 
 
-def sweep_tensor(dims, inds, vals, rank: int, dtype: int = SPTT_F32, reps: int = 3, label: str = ""):
-    """One sample per root mode: the default CSF's statistics and the time of
-    every candidate schedule."""
+def default_index(dims, root: int, rank: int, dtype: int, nnz: int) -> int:
+    """Candidate index of the schedule the library uses when given none."""
+    d = sptt_sched_default(dims, root, rank, dtype, nnz)
+    for i, c in enumerate(sptt_sched_candidates(nnz)):
+        if c[0] == d[0] and c[2] == d[2] and c[3] == d[3]:
+            return i
+    raise RuntimeError("the default schedule %r is not a candidate" % (d,))
+
+
+def sweep_tensor(dims, inds, vals, rank: int, dtypes: Sequence[int] = (SPTT_F32, SPTT_BF16), reps: int = 3,
+                 label: str = ""):
+    """One sample per root mode and gather type: the statistics of the CSF
+    the library would build by default, the time of every candidate
+    schedule, and which candidate is the default."""
     out = []
-    for root in range(len(dims)):
-        csf = Csf(dims, inds, vals, root)
-        feats = sptt_csf_features(csf.handle, rank)
-        csf.close()
-        ms = sptt_autotune(dims, inds, vals, root, rank, dtype, reps)
-        out.append(Sample(feats, ms, "%s root %d R %d" % (label, root, rank), rank))
+    nnz = int(vals.numel())
+    for dtype in dtypes:
+        for root in range(len(dims)):
+            d = sptt_sched_default(dims, root, rank, dtype, nnz)
+            csf = Csf(dims, inds, vals, root, level_order=sptt_level_order(dims, root, d[3]))
+            feats = sptt_csf_features(csf.handle, rank, dtype)
+            csf.close()
+            ms = sptt_autotune(dims, inds, vals, root, rank, dtype, reps)
+            out.append(Sample(feats, ms, default_index(dims, root, rank, dtype, nnz),
+                              "%s root %d R %d %s" % (label, root, rank, "bf16" if dtype == SPTT_BF16 else "f32"),
+                              rank, dtype))
     return out
 
 
@@ -60,34 +80,16 @@ def train(ds: Dataset, steps: int = 2000, lr: float = 3e-3, seed: int = 0, devic
     return m, hist
 
 
-def default_index(rank: int = 16, dtype: int = SPTT_F32, nnz: int = 1 << 30, sms: int = 152) -> int:
-    """Index of the candidate closest to the library's default schedule:
-    ascending order, the default variant for the gather type and rank (for
-    BF16 gathers the candidate with the same walk shape: 4 for the default
-    11, 7 for the default 10), and the default chunk (128, halved while
-    nnz / chunk < 256 per SM; the candidates have 64 and 128)."""
-    ld = (rank + 7) // 8 * 8
-    variant = (4 if ld <= 16 else 7) if dtype != SPTT_F32 else 7
-    chunk = 128
-    while chunk > 16 and nnz // chunk < sms * 256:
-        chunk //= 2
-    chunk = 128 if chunk >= 128 else 64
-    for i, c in enumerate(sptt_sched_candidates()):
-        if c[0] == chunk and c[2] == variant and c[3] == 0:
-            return i
-    return 0
-
-
 def regret(ds: Dataset, model=None, fixed: int = None):
     """Per-sample time of the chosen schedule over the best one, minus 1:
-    choices from the model, or the fixed candidate index (None: the
-    library's default for each sample's rank)."""
+    choices from the model, a fixed candidate index, or (neither) the
+    library's default for each sample."""
     if model is not None:
         choice, _ = sptt_mlp_predict(model.handle, [s.features for s in ds.samples])
     elif fixed is not None:
         choice = [fixed] * len(ds.samples)
     else:
-        choice = [default_index(s.rank, nnz=int(round(2.0 ** s.features[0]))) for s in ds.samples]
+        choice = [s.default for s in ds.samples]
     return [s.times_ms[k] / min(s.times_ms) - 1.0 for s, k in zip(ds.samples, choice)]
 
 

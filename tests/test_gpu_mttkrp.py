@@ -65,7 +65,7 @@ def test_mttkrp_padded_rank(R, ld, cuda_device):
 
 @pytest.mark.parametrize("chunk", [16, 32, 128, 512, 4096])
 @pytest.mark.parametrize("block", [64, 256])
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11])
+@pytest.mark.parametrize("variant", list(range(16)))
 def test_mttkrp_schedules_agree(chunk, block, variant, cuda_device):
     dims = (400, 300, 200, 20)
     t = make(dims, 50003, seed=5, dist="zipf", s=1.3)
@@ -75,7 +75,7 @@ def test_mttkrp_schedules_agree(chunk, block, variant, cuda_device):
         _check(M, t, F, root, 16, 1e-5)
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11])
+@pytest.mark.parametrize("variant", list(range(16)))
 @pytest.mark.parametrize("nm", [2, 3, 4, 5])
 def test_mttkrp_variants_every_order(variant, nm, cuda_device):
     dims = (290, 170, 50, 30, 10)[:nm]
@@ -120,7 +120,7 @@ def test_mttkrp_heavy_single_slice(cuda_device):
         _check(M, t, F, root, 16, 1e-5)
 
 
-@pytest.mark.parametrize("variant", [7, 8, 10])
+@pytest.mark.parametrize("variant", [7, 8, 10, 12])
 @pytest.mark.parametrize("dtype,ld", [(sptt.SPTT_F32, 4), (sptt.SPTT_F32, 12), (sptt.SPTT_F32, 24),
                                       (sptt.SPTT_F32, 64), (sptt.SPTT_F32, 128), (sptt.SPTT_BF16, 8),
                                       (sptt.SPTT_BF16, 24), (sptt.SPTT_BF16, 32), (sptt.SPTT_BF16, 256)])
@@ -137,7 +137,7 @@ def test_wide_segments_any_ld(variant, dtype, ld, cuda_device):
         _check(M, t, F, root, ld, 1e-5)
 
 
-@pytest.mark.parametrize("variant", [7, 8, 10])
+@pytest.mark.parametrize("variant", [7, 8, 10, 12])
 def test_wide_segments_misaligned_factor(variant, cuda_device):
     # a factor that is 16- but not 32-byte aligned runs the 16-byte walk
     dims = (500, 400, 60)
@@ -170,7 +170,7 @@ def test_mttkrp_rejects_bad_arguments(cuda_device):
     c = sptt.Csf(dims, di, dv, 0)
     F = [torch.rand(d, 8, device=cuda_device) for d in dims]
     out = torch.empty(10, 8, device=cuda_device)
-    for bad in (dict(sched=(24, 256, 0)), dict(sched=(64, 512, 0)), dict(sched=(64, 256, 12)),
+    for bad in (dict(sched=(24, 256, 0)), dict(sched=(64, 512, 0)), dict(sched=(64, 256, 16)),
                 dict(factor_dtype=7)):
         with pytest.raises(sptt.SpttError):
             c.mttkrp(F, out=out, **bad)

@@ -53,10 +53,14 @@ def test_features_match_a_host_restatement(cuda_device):
     inds_np, vals_np = t.numpy()
     c = sptt.Csf(t.dims, [x.to(cuda_device) for x in t.inds], t.vals.to(cuda_device), 1)
     f = sptt.sptt_csf_features(c.handle, 16)
+    fb = sptt.sptt_csf_features(c.handle, 16, sptt.SPTT_BF16)
     ref = oracle.csf(inds_np, vals_np, t.dims, 1)
     sizes = np.diff(ref["fptr"][1][ref["fptr"][0]])  # leaves per slice (3 modes)
     nnz = ref["nfibs"][-1]
-    assert abs(f[0] - math.log2(nnz)) < 1e-5 and f[1] == 3 and abs(f[2] - 4) < 1e-6
+    # a row of 16 FP32 values is 64 bytes (BF16: 32)
+    assert abs(f[0] - math.log2(nnz)) < 1e-5 and f[1] == 3 and abs(f[2] - 6) < 1e-6 and abs(fb[2] - 5) < 1e-6
+    assert abs(f[13] - math.log2(t.dims[ref["order"][2]] * 64)) < 1e-5
+    assert abs(fb[13] - math.log2(t.dims[ref["order"][2]] * 32)) < 1e-5
     assert abs(f[6] - math.log2(ref["nfibs"][0])) < 1e-5
     assert abs(f[10] - math.log2(sizes.max())) < 1e-5
     assert abs(f[11] - sizes[sizes >= 1024].sum() / nnz) < 1e-6
@@ -69,6 +73,11 @@ def test_autotune_and_planned_cpd(cuda_device):
     dv = t.vals.to(cuda_device)
     ms = sptt.sptt_autotune(t.dims, di, dv, 0, 16)
     assert len(ms) == 16 and all(x > 0 for x in ms)
+    cands = sptt.sptt_sched_candidates(t.nnz)
+    for dt in (sptt.SPTT_F32, sptt.SPTT_BF16):
+        for root in range(3):
+            d = sptt.sptt_sched_default(t.dims, root, 16, dt, t.nnz)
+            assert any(c[0] == d[0] and c[2] == d[2] and c[3] == d[3] for c in cands), d
     base = sptt.Cpd(t.dims, di, dv, 16, seed=1).init()
     base.iterate(4)
     tuned = sptt.Cpd(t.dims, di, dv, 16, seed=1, plan=1).init()
@@ -78,7 +87,6 @@ def test_autotune_and_planned_cpd(cuda_device):
     learned = sptt.Cpd(t.dims, di, dv, 16, seed=1, plan=2, mlp=m).init()
     learned.iterate(4)
     np.testing.assert_allclose(learned.fit_history(), base.fit_history(), atol=1e-6)
-    cands = sptt.sptt_sched_candidates()
     per_mode = [cands[int(np.argmax(ms))]] * 3  # the slowest one still gives the same numbers
     other = sptt.Cpd(t.dims, di, dv, 16, seed=1, mode_sched=per_mode).init()
     other.iterate(4)
