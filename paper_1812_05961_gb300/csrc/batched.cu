@@ -162,28 +162,30 @@ __device__ __noinline__ void walk_chunk(const walk::Args &w, int64_t c, int col)
     walk::flush_carry(w, col, cy);
 }
 
-// The same walk on the packed leaf records (two leaves per pair of 16-byte
-// loads, loaded past L1; walk.cuh load_rec_pair).
+// The select walk on the packed leaf records (walk.cuh select_chunk: no
+// per-leaf branch, two leaves per pair of 16-byte record loads past L1),
+// 16-byte row segments in batches of 2: it fits the 2-CTA-per-SM build
+// without spilling (the flag walk it replaced spilled 160-176 bytes per call).
 template <int NM>
 __device__ __noinline__ void walk_chunk_packed(const walk::Args &w, int64_t c, int col) {
     using Recs = walk::PackedRecsT<true>;
     const Recs rec{w.leafrec};
     walk::Carry<4> cy;
-    walk::flag_chunk<NM, float, 4, Recs, 16, false>(w, c, col, cy, rec);
+    walk::select_chunk<NM, float, 2, 16, false, true>(w, c, col, cy, rec);
     walk::flush_carry(w, col, cy);
 }
 
-// The walk with 32-byte row segments (2 lanes per R = 16 row), batches of 2
-// leaves, software-pipelined, on the packed records; its row and record
-// loads are split in 16-byte halves (walk.cuh SPLIT). It needs more
-// registers than a CTA of the 2-per-SM build has, so it runs in the
+// The select walk with 32-byte row segments (2 lanes per R = 16 row), its
+// row and record loads split in 16-byte halves (walk.cuh SPLIT: ptxas 13.0
+// fails on the 32-byte form inside this non-inlined function). It needs
+// more registers than a CTA of the 2-per-SM build has, so it runs in the
 // 1-CTA-per-SM build (batch_walk).
 template <int NM>
 __device__ __noinline__ void walk_chunk_wide(const walk::Args &w, int64_t c, int col) {
     using Recs = walk::PackedRecsT<true>;
     const Recs rec{w.leafrec};
     walk::Carry<8> cy;
-    walk::flag_chunk<NM, float, 2, Recs, 32, true>(w, c, col, cy, rec);
+    walk::select_chunk<NM, float, 2, 32, false, true>(w, c, col, cy, rec);
     walk::flush_carry(w, col, cy);
 }
 
@@ -438,6 +440,9 @@ struct sptt_batch {
     cudaGraphExec_t graph = nullptr;
     int32_t graph_iters = -1;
     bool zero_first = true;
+    int32_t chunk = 128;                // leaves per MTTKRP chunk of every CSF
+    float tuned_ms = 0.f;               // plan 1: time of the chosen candidate's timed run
+    int32_t tuned_candidates = 0;       // plan 1: candidates timed
 };
 
 namespace {
@@ -467,6 +472,9 @@ int batch_walk(const sptt_sched *sched, int32_t ld) {
     if (ld % 8 == 0 && !(sched && sched->variant == 4)) return 2;
     return 1;
 }
+
+// The schedule variant that names a walk (inverse of batch_walk).
+int32_t walk_variant(int walk) { return walk == 0 ? 3 : (walk == 1 ? 4 : 7); }
 
 using BatchKernel = void (*)(const BatchArgs);
 BatchKernel batch_kernel(int rp, int minb) {
@@ -524,7 +532,108 @@ sptt_status launch_batch(sptt_batch *b, int32_t iters) {
     return SPTT_OK;
 }
 
+// Everything that depends on the chunk size and the walk: every CSF's work
+// partition, the tensors' walk arguments, the global chunk and tile lists,
+// the kernel build (CTAs per SM) and the cooperative grid. Called once, or
+// once per candidate by the plan-1 timing.
+sptt_status batch_layout(sptt_batch *b, int32_t chunk, int walk) {
+    const int count = b->count, rank = b->rank;
+    SPTT_CUDA(cudaStreamSynchronize(b->st));  // no run may still read the old layout
+    b->chunk = chunk;
+    std::vector<int64_t> prefix((size_t)2 * b->max_modes * (count + 1), 0);
+    for (int t = 0; t < count; ++t) {
+        BTensor &T = b->host[t];
+        int64_t heavy = 0;
+        for (int m = 0; m < T.nmodes; ++m) {
+            sptt_csf *cs = b->csfs[(size_t)t * b->max_modes + m];
+            SPTT_TRY(csf_ensure_partition(cs, chunk, b->st));
+            if (cs->nheavy > heavy) heavy = cs->nheavy;
+            walk::Args &w = T.w[m];
+            w = walk::Args{};
+            for (int l = 0; l < T.nmodes; ++l) {
+                w.fptr[l] = cs->fptr[l];
+                w.fids[l] = cs->fids[l];
+                w.fac[l] = l ? T.A[cs->order[l]] : nullptr;
+            }
+            w.vals = cs->vals;
+            w.lvl = cs->lvl;
+            w.leafrec = cs->leafrec;
+            w.part = cs->part;
+            w.nchunks = cs->part_nchunks;
+            w.nnz = cs->nfibs[T.nmodes - 1];
+            w.chunk = cs->part_chunk;
+            w.ld = b->ld;
+            w.out = T.M;
+            w.heavy = T.Mh;
+            w.hidx = cs->hidx;
+            T.hidx[m] = cs->hidx;
+            T.fids0[m] = cs->fids[0];
+            T.nslices[m] = cs->nfibs[0];
+        }
+        if (heavy * b->ld > b->mh_elems[t]) return set_error(SPTT_ERR_INTERNAL, "heavy rows outgrow their buffer");
+    }
+    // global work lists: per mode position, chunk and tile prefix sums over the tensors
+    for (int n = 0; n < b->max_modes; ++n) {
+        int64_t *cp = prefix.data() + (2 * n) * (count + 1);
+        int64_t *tp = prefix.data() + (2 * n + 1) * (count + 1);
+        for (int t = 0; t < count; ++t) {
+            const BTensor &T = b->host[t];
+            const bool has = T.nmodes > n;
+            cp[t + 1] = cp[t] + (has ? T.w[n].nchunks : 0);
+            const int tr = tile_rows(rank <= 16 ? 16 : 32);
+            tp[t + 1] = tp[t] + (has ? (T.nslices[n] + tr - 1) / tr : 0);
+        }
+        b->total_chunks[n] = cp[count];
+        b->total_tiles[n] = tp[count];
+    }
+    SPTT_CUDA(cudaMemcpyAsync(b->d_tensors, b->host.data(), sizeof(BTensor) * count, cudaMemcpyHostToDevice, b->st));
+    SPTT_TRY(batch_alloc(b, &b->d_prefix, prefix.size(), false));
+    SPTT_CUDA(cudaMemcpyAsync(b->d_prefix, prefix.data(), prefix.size() * sizeof(int64_t), cudaMemcpyHostToDevice,
+                              b->st));
+    {
+        // chunk -> tensor tables (one load per chunk in the MTTKRP phase)
+        std::vector<int32_t> owner;
+        for (int n = 0; n < b->max_modes; ++n) {
+            const int64_t *cp = prefix.data() + (2 * n) * (count + 1);
+            owner.assign((size_t)cp[count], 0);
+            for (int t = 0; t < count; ++t)
+                for (int64_t g = cp[t]; g < cp[t + 1]; ++g) owner[(size_t)g] = t;
+            SPTT_TRY(batch_alloc(b, &b->d_owner[n], owner.size() + 1, false));
+            if (!owner.empty())
+                SPTT_CUDA(cudaMemcpyAsync(b->d_owner[n], owner.data(), owner.size() * sizeof(int32_t),
+                                          cudaMemcpyHostToDevice, b->st));
+            SPTT_CUDA(cudaStreamSynchronize(b->st));  // the host vectors are reused
+        }
+    }
+    // a grid that is fully resident (cooperative launch)
+    const int rp = rank <= 16 ? 16 : 32;
+    const size_t smem = batched_smem_bytes(rank, rp);
+    b->walk = walk;
+    if (b->walk == 2) {  // 32-byte row loads need 32-byte aligned factors
+        for (int t = 0; t < count; ++t)
+            for (int m = 0; m < b->host[t].nmodes; ++m)
+                if (reinterpret_cast<uintptr_t>(b->host[t].A[m]) % 32) b->walk = 1;
+    }
+    b->minb = b->walk == 2 ? 1 : 2;
+    auto kern = batch_kernel(rp, b->minb);
+    SPTT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    SPTT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBThreads, smem));
+    if (per_sm < 1) return set_error(SPTT_ERR_INTERNAL, "batched kernel does not fit on an SM");
+    b->grid = device_sm_count() * per_sm;
+    if (b->graph) {  // a captured run belongs to the old layout
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+        b->graph_iters = -1;
+    }
+    SPTT_CUDA(cudaStreamSynchronize(b->st));
+    return SPTT_OK;
+}
+
 }  // namespace
+
+extern "C" sptt_status sptt_batch_init(sptt_batch *b);
+extern "C" sptt_status sptt_batch_run(sptt_batch *b, int32_t iters);
 
 extern "C" sptt_status sptt_batch_create(const sptt_coo *coos, int32_t count, int32_t rank, const sptt_opts *opts,
                                          sptt_stream stream, sptt_batch **out) {
@@ -555,15 +664,20 @@ extern "C" sptt_status sptt_batch_create(const sptt_coo *coos, int32_t count, in
         if (coos[t].nmodes > b->max_modes) b->max_modes = coos[t].nmodes;
     }
     const sptt_sched *sched = b->has_sched ? &b->sched : nullptr;
+    if (b->opts.plan < 0 || b->opts.plan > 1) return set_error(SPTT_ERR_BAD_ARG, "batched opts.plan must be 0 or 1");
+    const bool tune = b->opts.plan == 1;
+    b->chunk = (sched && sched->chunk) ? sched->chunk : 128;
+    // the chunk sizes the layout may take (plan 1 times each of them)
+    std::vector<int32_t> chunks = tune ? std::vector<int32_t>{64, 128, 256} : std::vector<int32_t>{b->chunk};
     b->csfs.assign((size_t)count * b->max_modes, nullptr);
     b->host.resize(count);
-    std::vector<int64_t> prefix((size_t)2 * b->max_modes * (count + 1), 0);
     int64_t max_rows = 0;
     for (int t = 0; t < count; ++t) {
         const sptt_coo &c = coos[t];
         BTensor &T = b->host[t];
         T = BTensor{};
         T.nmodes = c.nmodes;
+        int64_t max_slices = 0, max_heavy = 0;
         {
             DevCoo dc;
             SPTT_TRY(coo_to_device(&c, b->st, &dc));
@@ -571,19 +685,20 @@ extern "C" sptt_status sptt_batch_create(const sptt_coo *coos, int32_t count, in
                 sptt_csf *cs = nullptr;
                 SPTT_TRY(csf_build_device(&dc.coo, m, nullptr, b->st, &cs));
                 b->csfs[(size_t)t * b->max_modes + m] = cs;
-                SPTT_TRY(csf_ensure_partition(cs, (sched && sched->chunk) ? sched->chunk : 128, b->st));
-                if (batch_packed(sched)) SPTT_TRY(csf_ensure_leafrec(cs, b->st));
+                // the FP64 rows of split slices are sized for the largest count any layout gives
+                for (int32_t ch : chunks) {
+                    SPTT_TRY(csf_ensure_partition(cs, ch, b->st));
+                    if (cs->nheavy > max_heavy) max_heavy = cs->nheavy;
+                }
+                if (tune || batch_packed(sched)) SPTT_TRY(csf_ensure_leafrec(cs, b->st));
+                if (cs->nfibs[0] > max_slices) max_slices = cs->nfibs[0];
             }
         }
-        int64_t max_slices = 0, max_heavy = 0;
         for (int m = 0; m < c.nmodes; ++m) {
             T.dims[m] = c.dims[m];
             if (c.dims[m] > max_rows) max_rows = c.dims[m];
             SPTT_TRY(batch_alloc(b, &T.A[m], (size_t)c.dims[m] * b->ld, true));
             SPTT_TRY(batch_alloc(b, &T.G[m], (size_t)rank * rank, true));
-            const sptt_csf *cs = b->csfs[(size_t)t * b->max_modes + m];
-            if (cs->nfibs[0] > max_slices) max_slices = cs->nfibs[0];
-            if (cs->nheavy > max_heavy) max_heavy = cs->nheavy;
         }
         SPTT_TRY(batch_alloc(b, &T.M, (size_t)max_slices * b->ld, true));
         SPTT_TRY(batch_alloc(b, &T.Mh, (size_t)max_heavy * b->ld, true));
@@ -597,89 +712,61 @@ extern "C" sptt_status sptt_batch_create(const sptt_coo *coos, int32_t count, in
         SPTT_TRY(batch_alloc(b, &T.normx2, 1, true));
         SPTT_TRY(batch_alloc(b, &T.fits, kFitRing, true));
         SPTT_TRY(batch_alloc(b, &T.branch, 2, true));
-        for (int m = 0; m < c.nmodes; ++m) {
-            const sptt_csf *cs = b->csfs[(size_t)t * b->max_modes + m];
-            walk::Args &w = T.w[m];
-            w = walk::Args{};
-            for (int l = 0; l < c.nmodes; ++l) {
-                w.fptr[l] = cs->fptr[l];
-                w.fids[l] = cs->fids[l];
-                w.fac[l] = l ? T.A[cs->order[l]] : nullptr;
-            }
-            w.vals = cs->vals;
-            w.lvl = cs->lvl;
-            w.leafrec = cs->leafrec;
-            w.part = cs->part;
-            w.nchunks = cs->part_nchunks;
-            w.nnz = cs->nfibs[c.nmodes - 1];
-            w.chunk = cs->part_chunk;
-            w.ld = b->ld;
-            w.out = T.M;
-            w.heavy = T.Mh;
-            w.hidx = cs->hidx;
-            T.hidx[m] = cs->hidx;
-            T.fids0[m] = cs->fids[0];
-            T.nslices[m] = cs->nfibs[0];
-        }
         const sptt_csf *c0 = b->csfs[(size_t)t * b->max_modes];
         SPTT_TRY(sumsq_launch(c0->vals, c0->nfibs[c.nmodes - 1], T.normx2, b->st));
     }
-    // global work lists: per mode position, chunk and tile prefix sums over the tensors
-    for (int n = 0; n < b->max_modes; ++n) {
-        int64_t *cp = prefix.data() + (2 * n) * (count + 1);
-        int64_t *tp = prefix.data() + (2 * n + 1) * (count + 1);
-        for (int t = 0; t < count; ++t) {
-            const BTensor &T = b->host[t];
-            const bool has = T.nmodes > n;
-            cp[t + 1] = cp[t] + (has ? T.w[n].nchunks : 0);
-            const int tr = tile_rows(rank <= 16 ? 16 : 32);
-            tp[t + 1] = tp[t] + (has ? (T.nslices[n] + tr - 1) / tr : 0);
-        }
-        b->total_chunks[n] = cp[count];
-        b->total_tiles[n] = tp[count];
-    }
     SPTT_TRY(batch_alloc(b, &b->d_tensors, (size_t)count, false));
-    SPTT_CUDA(cudaMemcpyAsync(b->d_tensors, b->host.data(), sizeof(BTensor) * count, cudaMemcpyHostToDevice, b->st));
-    SPTT_TRY(batch_alloc(b, &b->d_prefix, prefix.size(), false));
-    SPTT_CUDA(cudaMemcpyAsync(b->d_prefix, prefix.data(), prefix.size() * sizeof(int64_t), cudaMemcpyHostToDevice,
-                              b->st));
-    {
-        // chunk -> tensor tables (one load per chunk in the MTTKRP phase)
-        std::vector<int32_t> owner;
-        for (int n = 0; n < b->max_modes; ++n) {
-            const int64_t *cp = prefix.data() + (2 * n) * (count + 1);
-            owner.assign((size_t)cp[count], 0);
-            for (int t = 0; t < count; ++t)
-                for (int64_t g = cp[t]; g < cp[t + 1]; ++g) owner[(size_t)g] = t;
-            SPTT_TRY(batch_alloc(b, &b->d_owner[n], owner.size() + 1, false));
-            if (!owner.empty())
-                SPTT_CUDA(cudaMemcpyAsync(b->d_owner[n], owner.data(), owner.size() * sizeof(int32_t),
-                                          cudaMemcpyHostToDevice, b->st));
-            SPTT_CUDA(cudaStreamSynchronize(b->st));  // the host vector is reused
-        }
-    }
     SPTT_TRY(batch_alloc(b, &b->d_bar, 2, true));
     SPTT_TRY(batch_alloc(b, &b->d_err, 1, true));
     SPTT_TRY(batch_alloc(b, &b->d_it_base, 1, true));
     SPTT_TRY(batch_alloc(b, &b->d_phase, 10, true));
     b->gram_blocks = device_sm_count() * 2;
     SPTT_TRY(batch_alloc(b, &b->partials, (size_t)b->gram_blocks * (rank * rank + rank), false));
-    // a grid that is fully resident (cooperative launch)
-    const int rp = rank <= 16 ? 16 : 32;
-    const size_t smem = batched_smem_bytes(rank, rp);
-    b->walk = batch_walk(sched, b->ld);
-    if (b->walk == 2) {  // 32-byte row loads need 32-byte aligned factors
-        for (int t = 0; t < count; ++t)
-            for (int m = 0; m < b->host[t].nmodes; ++m)
-                if (reinterpret_cast<uintptr_t>(b->host[t].A[m]) % 32) b->walk = 1;
+    if (!tune) {
+        SPTT_TRY(batch_layout(b, b->chunk, batch_walk(sched, b->ld)));
+    } else {
+        // plan 1: time every (walk, chunk) candidate on the batch itself, one
+        // warm-up run and one timed run of 2 iterations each from fresh
+        // factors, and keep the fastest (the factors are re-initialised by
+        // sptt_batch_init before the caller's runs)
+        std::vector<int> walks = {1};
+        if (b->ld % 8 == 0) walks.push_back(2);
+        cudaEvent_t e0, e1;
+        SPTT_CUDA(cudaEventCreate(&e0));
+        SPTT_CUDA(cudaEventCreate(&e1));
+        struct Ev {
+            cudaEvent_t a, b;
+            ~Ev() { cudaEventDestroy(a); cudaEventDestroy(b); }
+        } evg{e0, e1};
+        const bool graph = b->opts.use_graph;
+        b->opts.use_graph = 0;
+        float best = -1.f;
+        int best_walk = 1;
+        int32_t best_chunk = 128;
+        for (int wk : walks)
+            for (int32_t ch : chunks) {
+                SPTT_TRY(batch_layout(b, ch, wk));
+                if (b->walk != wk) continue;  // the 32-byte walk was refused (alignment)
+                SPTT_TRY(sptt_batch_init(b));
+                SPTT_TRY(sptt_batch_run(b, 2));
+                SPTT_TRY(sptt_batch_init(b));
+                SPTT_CUDA(cudaEventRecord(e0, b->st));
+                SPTT_TRY(sptt_batch_run(b, 2));
+                SPTT_CUDA(cudaEventRecord(e1, b->st));
+                SPTT_CUDA(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                SPTT_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                ++b->tuned_candidates;
+                if (best < 0.f || ms < best) {
+                    best = ms;
+                    best_walk = wk;
+                    best_chunk = ch;
+                }
+            }
+        b->opts.use_graph = graph;
+        b->tuned_ms = best;
+        SPTT_TRY(batch_layout(b, best_chunk, best_walk));
     }
-    b->minb = b->walk == 2 ? 1 : 2;
-    auto kern = batch_kernel(rp, b->minb);
-    SPTT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int per_sm = 0;
-    SPTT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBThreads, smem));
-    if (per_sm < 1) return set_error(SPTT_ERR_INTERNAL, "batched kernel does not fit on an SM");
-    b->grid = device_sm_count() * per_sm;
     SPTT_CUDA(cudaStreamSynchronize(b->st));
     guard.b = nullptr;
     *out = b;
@@ -804,6 +891,19 @@ extern "C" sptt_status sptt_batch_info(sptt_batch *b, int32_t *grid, int64_t *ch
         if (chunks) chunks[n] = n < b->max_modes ? b->total_chunks[n] : 0;
         if (tiles) tiles[n] = n < b->max_modes ? b->total_tiles[n] : 0;
     }
+    return SPTT_OK;
+}
+
+extern "C" sptt_status sptt_batch_schedule(sptt_batch *b, sptt_sched *out, float *tuned_ms, int32_t *candidates) {
+    clear_error();
+    if (!b || !out) return set_error(SPTT_ERR_BAD_ARG, "batch and out must be non-NULL");
+    sptt_sched s{};
+    s.chunk = b->chunk;
+    s.block = kBThreads;
+    s.variant = walk_variant(b->walk);
+    *out = s;
+    if (tuned_ms) *tuned_ms = b->tuned_ms;
+    if (candidates) *candidates = b->tuned_candidates;
     return SPTT_OK;
 }
 

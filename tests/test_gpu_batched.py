@@ -42,6 +42,22 @@ def test_batched_fits_match_oracle_per_tensor(cuda_device):
             assert np.linalg.norm(F - ref["factors"][m]) <= 1e-3 * max(1.0, np.linalg.norm(ref["factors"][m]))
 
 
+@pytest.mark.parametrize("R", [8, 16])
+def test_autotuned_batch_fits_match_oracle_per_tensor(R, cuda_device):
+    # plan 1: the batch times its walk x chunk candidates on itself, keeps the
+    # fastest and must still give every tensor the oracle's fits
+    items = _batch(24, seed=13)
+    iters = 5
+    b = sptt.Batch([(d, i, v) for d, i, v, _ in items], R, seed=100, plan=1).init()
+    (chunk, _, variant, _), ms, n = b.schedule()
+    assert n >= 3 and ms > 0 and chunk in (64, 128, 256) and variant in (4, 7)
+    b.run(iters)
+    for t, (dims, _, _, x) in enumerate(items):
+        inds_np, vals_np = x.numpy()
+        ref = oracle.cpd_als(inds_np, vals_np, dims, R, iters, seed=100 + t)
+        np.testing.assert_allclose(b.fit_history(t), ref["fits"], atol=1e-4, err_msg="tensor %d" % t)
+
+
 def test_batched_matches_single_tensor_path_and_continues(cuda_device):
     items = _batch(10, seed=5)
     R = 16
