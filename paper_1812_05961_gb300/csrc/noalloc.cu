@@ -56,8 +56,8 @@ extern "C" sptt_status sptt_gram_noalloc(const float *A, int64_t rows, int32_t r
     if (!G || (!A && rows > 0)) return set_error(SPTT_ERR_BAD_ARG, "A (when rows > 0) and G must be non-NULL");
     if (rows < 0) return set_error(SPTT_ERR_BAD_ARG, "rows < 0");
     if (rank < 1 || rank > SPTT_MAX_RANK_ALS)
-        return set_error(SPTT_ERR_BAD_ARG, "sptt_gram_noalloc: rank must be in [1, 64] (the static workspace "
-                                           "holds at most 2^18 partial sums)");
+        return set_error(SPTT_ERR_UNSUPPORTED, "sptt_gram_noalloc: rank must be in [1, 64] (the static "
+                                               "workspace holds at most 2^18 partial sums)");
     if (ld < rank) return set_error(SPTT_ERR_BAD_ARG, "ld < rank");
     double *scratch = nullptr;
     SPTT_TRY(scratch_for_current_device(&scratch));

@@ -32,15 +32,18 @@ def test_gram_matches_numpy(cuda_device):
         assert np.abs(G - ref).max() <= 1e-5 * max(1.0, np.abs(ref).max())
 
 
-@pytest.mark.parametrize("dims,nnz,R,iters", [
-    ((200, 150, 100), 20000, 8, 10),     # the small uniform workload
-    ((300, 250, 200), 40000, 16, 6),
-    ((60, 50, 40, 30), 30000, 12, 6),
-    ((20, 18, 16, 14, 12), 20000, 8, 5),
-    ((400, 300), 20000, 10, 6),
+@pytest.mark.parametrize("dims,nnz,R,iters,dist", [
+    # the small uniform workload: 200 x 150 x 100, 20,000 distinct uniform
+    # coordinates, values U(0,1), R = 8, 10 iterations
+    ((200, 150, 100), 20000, 8, 10, "uniform"),
+    ((200, 150, 100), 20000, 8, 10, "zipf"),
+    ((300, 250, 200), 40000, 16, 6, "zipf"),
+    ((60, 50, 40, 30), 30000, 12, 6, "uniform"),
+    ((20, 18, 16, 14, 12), 20000, 8, 5, "uniform"),
+    ((400, 300), 20000, 10, 6, "uniform"),
 ])
-def test_cpd_als_fit_matches_oracle(dims, nnz, R, iters, cuda_device):
-    t = make(dims, nnz, seed=nnz % 101 + R, dist="zipf" if len(dims) == 3 else "uniform", s=1.1)
+def test_cpd_als_fit_matches_oracle(dims, nnz, R, iters, dist, cuda_device):
+    t = make(dims, nnz, seed=nnz % 101 + R, dist=dist, s=1.1)
     inds_np, vals_np = t.numpy()
     di, dv = to_dev(t, cuda_device)
     cpd = sptt.Cpd(dims, di, dv, R, seed=7).init()
