@@ -15,6 +15,11 @@ import tensorgen
 pytestmark = pytest.mark.gpu
 
 NIN, NH, NOUT = 16, 64, 16
+# the held-out claim: the learned choice's mean regret is at most GAIN_FACTOR
+# times the fixed default's and at most GAIN_ABS (regret = time of the chosen
+# schedule over the autotuner's best, minus 1)
+GAIN_FACTOR = 0.5
+GAIN_ABS = 0.15
 
 
 def test_mlp_forward_and_gradient_match_oracle(cuda_device):
@@ -93,34 +98,29 @@ def test_autotune_and_planned_cpd(cuda_device):
     np.testing.assert_allclose(other.fit_history(), base.fit_history(), atol=1e-6)
 
 
-def _specs(n, seed):
-    g = np.random.default_rng(seed)
-    out = []
-    for i in range(n):
-        nm = int(g.integers(3, 5))
-        dims = [int(math.exp(g.uniform(math.log(100), math.log(200000)))) for _ in range(nm)]
-        space = float(np.prod(dims, dtype=np.float64))
-        nnz = int(min(math.exp(g.uniform(math.log(1e5), math.log(2e6))), space / 4))
-        s = float(g.uniform(0.8, 1.5))
-        R = int(g.choice([8, 16, 32]))
-        out.append((dims, max(nnz, 1000), s, R, seed * 1000 + i))
-    return out
+def test_training_on_sweeps_fits_the_timings(cuda_device):
+    # the library's training kernels on autotuner sweeps of a few generated
+    # tensors: the loss falls and the fitted model beats the fixed rule on
+    # the tensors it saw
+    from paper_1812_05961_gb300 import train_scheduler
+    ds = train_scheduler.sweep(train_scheduler.tensor_specs(12, seed=5, nnz_max=2e6), cuda_device)
+    model, hist = schedtrain.train(ds, steps=1500, lr=3e-3)
+    assert float(hist[-1]) < 0.5 * float(hist[0])
+    r_model = schedtrain.summarize(schedtrain.regret(ds, model))
+    r_default = schedtrain.summarize(schedtrain.regret(ds))
+    assert r_model["mean"] < r_default["mean"], (r_model, r_default)
 
 
-def _dataset(specs, dev):
-    ds = schedtrain.Dataset()
-    for dims, nnz, s, R, sd in specs:
-        t = tensorgen.sample_unique(dims, nnz, sd, dev, "zipf", s=s, values="uniform")
-        ds.samples += schedtrain.sweep_tensor(t.dims, t.inds, t.vals, R, reps=3)
-    return ds
-
-
-def test_learned_scheduler_beats_fixed_default_on_held_out(cuda_device):
-    train = _dataset(_specs(40, seed=11), cuda_device)
-    held = _dataset(_specs(12, seed=99), cuda_device)
-    model, hist = schedtrain.train(train, steps=1500, lr=3e-3)
-    assert float(hist[-1]) < float(hist[0])
+def test_shipped_scheduler_gains_over_the_fixed_default_on_held_out(cuda_device):
+    # the model the package ships (trained by train_scheduler.py on the
+    # autotuner's timings of 2,000 generated tensors) against the library's
+    # fixed default rule, on tensors of the same distribution it never saw
+    # (another seed), timed now by the exhaustive autotuner
+    from paper_1812_05961_gb300 import train_scheduler
+    model = train_scheduler.load()
+    held = train_scheduler.sweep(train_scheduler.tensor_specs(40, seed=4242), cuda_device)
     r_model = schedtrain.summarize(schedtrain.regret(held, model))
-    r_default = schedtrain.summarize(schedtrain.regret(held))  # the library default per rank
+    r_default = schedtrain.summarize(schedtrain.regret(held))
     print("held-out regret: learned %s, default %s" % (r_model, r_default))
-    assert r_model["mean"] <= r_default["mean"] + 0.02
+    assert r_model["mean"] <= GAIN_FACTOR * r_default["mean"], (r_model, r_default)
+    assert r_model["mean"] <= GAIN_ABS, (r_model, r_default)
