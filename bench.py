@@ -49,16 +49,16 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-extras", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
-    p.add_argument("--extra-batched", action="store_true",
-                   help="also time the 512-tensor batched workload (one persistent launch per run)")
-    p.add_argument("--extra-sched", action="store_true",
-                   help="also train the learned scheduler and report its held-out regret")
+    p.add_argument("--no-batched", action="store_true",
+                   help="skip the 512-tensor batched workload (one persistent launch per run, autotuned plan)")
+    p.add_argument("--no-sched", action="store_true",
+                   help="skip the learned scheduler's held-out regret against the fixed default")
     p.add_argument("--extra-one-csf", action="store_true",
                    help="also time one CSF for all modes (non-root MTTKRPs with privatised hot rows)")
-    p.add_argument("--extra-mixed4", action="store_true",
-                   help="also time the 4-mode R=64 workload: BF16 gathers + FP32 refinement vs FP32")
+    p.add_argument("--no-mixed4", action="store_true",
+                   help="skip the 4-mode R=64 mixed-precision comparison (BF16 gathers + FP32 sweep vs FP32) "
+                        "and its scaled-down comparison with the FP64 oracle")
     p.add_argument("--batch-count", type=int, default=512)
-    p.add_argument("--sched-train", type=int, default=120)
     p.add_argument("--sched-heldout", type=int, default=40)
     p.add_argument("--variant", type=int, default=0, help="MTTKRP kernel variant for every mode (0 = default)")
     p.add_argument("--chunk", type=int, default=0, help="MTTKRP chunk size (0 = default)")
@@ -162,12 +162,14 @@ class Clocks:
 # ---------------------------------------------------------------------------
 # CPU baseline: the oracle as it stands, on a bounded sample
 # ---------------------------------------------------------------------------
-def cpu_oracle_rate(t_cpu_inds, t_cpu_vals, dims, R, seconds):
+def cpu_oracle_rate(t_cpu_inds, t_cpu_vals, dims, R, seconds, threads=1):
     """Times one oracle CP-ALS iteration on a prefix sample sized for about
-    `seconds` of CPU work. Returns (Gnnz*R/s, sample description)."""
+    `seconds` of CPU work, on `threads` host threads (the oracle's threaded
+    MTTKRP and row loops). Returns (Gnnz*R/s, seconds, sample size)."""
     import numpy as np
 
     import oracle
+    oracle.set_threads(threads)
     nnz = t_cpu_vals.shape[0]
 
     def run(s):
@@ -205,9 +207,11 @@ def reference_arm(args, rank, world):
     del t
     import oracle
     R = args.rank
+    cores, model = host_cpu()
+    threads = oracle.set_threads(cores)
     # one step = one oracle CP-ALS iteration on a bounded prefix sample
     budget = max(3.0, 150.0 / max(1, args.steps + args.warmup))
-    _, t1, s = cpu_oracle_rate(inds, vals, [480_000, 18_000, 2_000], R, min(budget, 15.0))
+    _, t1, s = cpu_oracle_rate(inds, vals, [480_000, 18_000, 2_000], R, min(budget, 15.0), threads)
     sub_i = [np.ascontiguousarray(x[:s]) for x in inds]
     sub_v = np.ascontiguousarray(vals[:s])
     dims = [480_000, 18_000, 2_000]
@@ -226,9 +230,10 @@ def reference_arm(args, rank, world):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "rank": R, "sample_nnz": s},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "host_cores": cores, "cpu_model": model,
                          "sample": "one CP-ALS iteration (3 MTTKRPs + solve + fit) of the FP64 C oracle "
-                                   "on the first %d non-zeros, single thread" % s},
+                                   "on the first %d non-zeros, %d threads" % (s, threads)},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -271,9 +276,46 @@ NCU_TRAFFIC = {"kernel": "mttkrp_flag_kernel<3, float, 2, 2, 32, 1, 1, 0>", "var
 # The same for the default BF16-gather kernel (variant 11).
 NCU_TRAFFIC_BF16 = {"kernel": "mttkrp_flag_kernel<3, __nv_bfloat16, 4, 2, 16, 1, 1, 1>", "variant": 11,
                     "nnz": 20_000_000, "bytes": [367.383296e6, 360.050944e6, 358.682368e6]}
-# FP32 FMA peak from the unit counts and the clock: 152 SMs x 128 FP32
-# lanes x 2 flops x 2.07 GHz.
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+def fp32_peak_tflops(dev, sm_mhz=None):
+    """FP32 FMA peak from the unit counts and the clock: the device's SM
+    count x 128 FP32 lanes x 2 flops x the maximum SM clock (from
+    MEASURED_PEAKS.json when present, else 2,070 MHz)."""
+    import torch
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    if sm_mhz is None:
+        sm_mhz = 2070.0
+        path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+        if os.path.exists(path):
+            with open(path) as f:
+                sm_mhz = float(json.load(f).get("sm_max_mhz", sm_mhz))
+    return sms * 128 * 2 * sm_mhz * 1e6 / 1e12, sms, sm_mhz
+
+
+def host_cpu():
+    """(logical cores, CPU model) of this host: lscpu's vendor and model name,
+    else /proc/cpuinfo's model name."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True).stdout
+        kv = {}
+        for line in out.splitlines():
+            if ":" in line:
+                k, v = line.split(":", 1)
+                kv.setdefault(k.strip().lower(), v.strip())
+        parts = [kv.get("vendor id"), kv.get("model name")]
+        model = " ".join(p for p in parts if p) or None
+    except Exception:
+        pass
+    if model is None:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.split(":")[0].strip().lower() == "model name":
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    return os.cpu_count() or 1, model or "unknown"
 
 
 def batched_extra(args, dev):
@@ -293,15 +335,33 @@ def batched_extra(args, dev):
         tensors.append((x.dims, x.inds, x.vals))
     gen_s = time.time() - t0
     work = sum(len(d) * int(v.numel()) * R for d, _, v in tensors) * iters
+    # byte model of one MTTKRP sweep over every tensor and mode (the batch's
+    # CSFs take the ascending level order): values and leaf indices, fids and
+    # fptr of the upper levels, each distinct factor row once, the output rows
+    sweep_bytes = 0
+    for d, inds, v in tensors:
+        n = len(d)
+        distinct = [int(torch.unique(x).numel()) for x in inds]
+        for root in range(n):
+            order = [root] + sorted((m for m in range(n) if m != root), key=lambda m: (d[m], m))
+            key = torch.zeros_like(inds[0], dtype=torch.int64)
+            fib = 0
+            for l in range(n - 1):
+                key = key * int(d[order[l]]) + inds[order[l]].long()
+                fib += int(torch.unique(key).numel())
+            sweep_bytes += int(v.numel()) * 8 + fib * 8 + sum(distinct[order[l]] for l in range(1, n)) * R * 4
+            sweep_bytes += int(d[root]) * R * 4
     side = torch.cuda.Stream()
     with torch.cuda.stream(side):
         t0 = time.time()
-        b = sptt.Batch(tensors, R, seed=1, use_graph=1)
+        b = sptt.Batch(tensors, R, seed=1, use_graph=1, plan=1)
         create_s = time.time() - t0
+        sched, tuned_ms, ncand = b.schedule()
         b.init()
         b.run(iters)  # direct launch
         b.run(iters)  # captured
         grid, chunks, tiles = b.info()
+        ph0 = sptt.sptt_batch_phase_ms(b.handle)
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         reps = 3
         ev0.record(side)
@@ -310,7 +370,11 @@ def batched_extra(args, dev):
         ev1.record(side)
         torch.cuda.synchronize()
         batched_s = ev0.elapsed_time(ev1) / 1e3 / reps
-        phase_ms = sptt.sptt_batch_phase_ms(b.handle)
+        ph1 = sptt.sptt_batch_phase_ms(b.handle)
+        phase_ms = {k: ph1[k] - ph0[k] for k in ph1}  # the timed runs only
+    peak, peak_kind = measured_peaks()
+    m_s = phase_ms["mttkrp"] / 1e3 / reps  # CTA 0's MTTKRP-phase wall time per run (closing barrier included)
+    achieved = sweep_bytes * iters / m_s / 1e9 if m_s > 0 else None
     # one tensor at a time through the single-tensor path (creation not timed)
     cpds = [sptt.Cpd(d, i, v, R, seed=1 + k).init() for k, (d, i, v) in enumerate(tensors)]
     for c in cpds:
@@ -327,15 +391,26 @@ def batched_extra(args, dev):
     return {"tensors": len(tensors), "total_nnz": int(sum(int(v.numel()) for _, _, v in tensors)),
             "rank": R, "iters": iters, "grid": grid, "chunks_per_mode": chunks[:4], "gen_s": round(gen_s, 1),
             "create_s": round(create_s, 1), "batched_s_per_run": batched_s,
-            "phase_ms_all_runs": phase_ms,
+            "plan": {"kind": "batched autotuner (plan 1)", "chosen": {"chunk": sched[0], "variant": sched[2]},
+                     "candidates_timed": ncand, "chosen_timed_run_ms": tuned_ms},
+            "mttkrp_roofline": {"bound": "hbm", "bytes_per_run": sweep_bytes * iters, "phase_s_per_run": m_s,
+                                "achieved": achieved, "peak": peak, "unit": "GB/s",
+                                "frac": None if achieved is None else achieved / peak, "peak_kind": peak_kind,
+                                "time_source": "CTA 0's MTTKRP-phase wall time (globaltimer), closing barrier "
+                                               "included"},
+            "phase_ms_timed_runs": phase_ms,
             "batched_GnnzR_per_s": work / batched_s / 1e9, "sequential_s": seq_s,
             "sequential_GnnzR_per_s": work / seq_s / 1e9, "speedup": seq_s / batched_s}
 
 
 def mixed4_extra(args, dev):
-    """The 4-mode mixed-precision workload: BF16 gathers for 25 iterations plus
-    one FP32 refinement sweep against 26 FP32 iterations from the same start,
-    R = 64: s/iter of each and the fit difference."""
+    """The 4-mode mixed-precision workload, 2e6 x 5e5 x 5e4 x 1e3, 1.5e8
+    non-zeros, R = 64, from the same initial factors:
+      fixed count: 25 BF16 iterations + one FP32 refinement sweep against 26
+        FP32 iterations (time of the whole run, the sweep included);
+      converged: both run until the fit gains less than 1e-5 per iteration
+        (Algorithm 1's stop rule), the mixed run then does its FP32 sweep.
+    Also the BF16 R = 64 MTTKRP's HBM fraction under the byte model."""
     import torch
 
     import paper_1812_05961_gb300 as sptt
@@ -348,14 +423,18 @@ def mixed4_extra(args, dev):
     torch.cuda.empty_cache()
     R = 64
     stream = torch.cuda.current_stream()
+    distinct = [int(torch.unique(x).numel()) for x in t.inds]
     out = {"workload": "power-law 4-mode %s, %d nnz, Zipf(1.2), values U(0,1), R=64" %
                        ("x".join(map(str, t.dims)), t.nnz), "gen_s": round(gen_s, 1)}
+
+    def ev():
+        return torch.cuda.Event(enable_timing=True)
+
     for name, prec in (("fp32", sptt.SPTT_F32), ("bf16", sptt.SPTT_BF16)):
-        t1 = time.time()
-        c = sptt.Cpd(t.dims, t.inds, t.vals, R, seed=3, precision=prec).init()
+        c = sptt.Cpd(t.dims, t.inds, t.vals, R, seed=3, precision=prec, profile=1).init()
         torch.cuda.synchronize()
-        create_s = time.time() - t1
-        a, b, e = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        c.timers()
+        a, b, e = ev(), ev(), ev()
         a.record(stream)
         c.iterate(25)
         b.record(stream)
@@ -365,17 +444,87 @@ def mixed4_extra(args, dev):
             c.iterate(1)
         e.record(stream)
         torch.cuda.synchronize()
-        s_iter = a.elapsed_time(b) / 25 / 1e3
-        out[name] = {"s_per_iter": s_iter, "last_sweep_s": b.elapsed_time(e) / 1e3,
-                     "total_s": a.elapsed_time(e) / 1e3, "fit": c.fit()[0], "create_s": round(create_s, 2),
-                     "GnnzR_per_s": 4 * t.nnz * R / s_iter / 1e9}
+        tm = c.timers()
+        fixed_fit = c.fit()[0]
+        # the same run continued to the stop rule, then (mixed) one FP32 sweep
+        c.init()
+        a2, b2 = ev(), ev()
+        a2.record(stream)
+        done = c.iterate(2000, 1e-5)
+        if prec == sptt.SPTT_BF16:
+            c.refine(1)
+        b2.record(stream)
+        torch.cuda.synchronize()
+        out[name] = {"s_per_iter": a.elapsed_time(b) / 25 / 1e3, "last_sweep_s": b.elapsed_time(e) / 1e3,
+                     "total_26_s": a.elapsed_time(e) / 1e3, "s_per_iter_incl_sweep": a.elapsed_time(e) / 26 / 1e3,
+                     "fit_26": fixed_fit,
+                     "converged": {"iters": done, "fit": c.fit()[0], "s": a2.elapsed_time(b2) / 1e3},
+                     "mttkrp_ms_per_launch": tm["mttkrp"][0] / max(tm["mttkrp"][1], 1),
+                     "GnnzR_per_s": 4 * t.nnz * R * 26 / (a.elapsed_time(e) / 1e3) / 1e9}
+        if prec == sptt.SPTT_BF16:
+            csfs = [sptt.Csf(t.dims, t.inds, t.vals, r) for r in range(4)]
+            bpl = sum(byte_model(cs, t.dims, R, distinct, 2) for cs in csfs) / 4
+            del csfs
+            peak, kind = measured_peaks()
+            ach = bpl / (out[name]["mttkrp_ms_per_launch"] * 1e-3) / 1e9
+            out[name]["roofline"] = {"bound": "hbm", "bytes_per_launch": int(bpl), "achieved": ach, "peak": peak,
+                                     "unit": "GB/s", "frac": ach / peak, "peak_kind": kind}
         del c
         torch.cuda.empty_cache()
-    out["delta_fit_bf16_vs_fp32"] = out["bf16"]["fit"] - out["fp32"]["fit"]
-    out["speedup_per_iter_bf16_vs_fp32"] = out["fp32"]["s_per_iter"] / out["bf16"]["s_per_iter"]
-    out["speedup_total_bf16_plus_refine_vs_fp32"] = out["fp32"]["total_s"] / out["bf16"]["total_s"]
+    out["delta_fit_26_bf16_vs_fp32"] = out["bf16"]["fit_26"] - out["fp32"]["fit_26"]
+    out["delta_fit_converged_bf16_vs_fp32"] = out["bf16"]["converged"]["fit"] - out["fp32"]["converged"]["fit"]
+    out["speedup_26_bf16_plus_sweep_vs_fp32"] = out["fp32"]["total_26_s"] / out["bf16"]["total_26_s"]
+    out["speedup_converged"] = out["fp32"]["converged"]["s"] / out["bf16"]["converged"]["s"]
     del t
     torch.cuda.empty_cache()
+    return out
+
+
+def mixed_vs_oracle_extra(dev):
+    """Mixed precision against the FP64 oracle on a scaled-down 4-mode
+    power-law tensor (8,000 x 2,000 x 500 x 100, 3e5 non-zeros, Zipf(1.2),
+    R = 64), from the same initial factors: after K = 26 and K = 100
+    iterations, the oracle, the FP32 path and the mixed path (K - 1 BF16
+    iterations + one FP32 sweep); signed fit differences against the oracle
+    and each factor's relative error."""
+    import numpy as np
+
+    import oracle
+    import paper_1812_05961_gb300 as sptt
+    import tensorgen
+    dims, nnz, R, seed = (8000, 2000, 500, 100), 300_000, 64, 3
+    counts = (26, 100)
+    t = tensorgen.sample_unique(dims, nnz, 31, "cpu", dist="zipf", s=1.2, values="uniform")
+    inds, vals = t.numpy()
+    cores, _ = host_cpu()
+    threads = oracle.set_threads(cores)
+    t0 = time.time()
+    ref = {k: oracle.cpd_als(inds, vals, dims, R, k, seed=seed) for k in counts}
+    oracle_s = time.time() - t0
+    out = {"workload": "power-law 4-mode 8000x2000x500x100, 3e5 nnz, Zipf(1.2), U(0,1), R=64",
+           "oracle": {"threads": threads, "s": round(oracle_s, 1),
+                      "fit": {str(k): float(ref[k]["fits"][-1]) for k in counts}}}
+    di = [x.to(dev) for x in t.inds]
+    dv = t.vals.to(dev)
+
+    def rel(a, b):
+        a = a.numpy().astype(np.float64)
+        return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+    for k in counts:
+        row = {}
+        for name, prec in (("fp32", sptt.SPTT_F32), ("mixed", sptt.SPTT_BF16)):
+            c = sptt.Cpd(dims, di, dv, R, seed=seed, precision=prec).init()
+            if prec == sptt.SPTT_BF16:
+                c.iterate(k - 1)
+                c.refine(1)
+            else:
+                c.iterate(k)
+            fit = c.fit()[0]
+            row[name] = {"fit": fit, "delta_fit_vs_oracle": fit - float(ref[k]["fits"][-1]),
+                         "factor_rel_err": [rel(c.factor(m), ref[k]["factors"][m]) for m in range(4)]}
+            del c
+        out["iters_%d" % k] = row
     return out
 
 
@@ -436,47 +585,33 @@ def one_csf_extra(args, t, R, dev):
 
 
 def sched_extra(args, dev):
-    """The learned scheduler: trained on autotuner sweeps of generated tensors,
-    evaluated on held-out ones and on a 5-mode probe tensor."""
-    import math as _m
-
-    import numpy as np
+    """The learned scheduler the package ships (trained on the GPU by the
+    library's MLP kernels on autotuner sweeps of generated tensors; see
+    paper_1812_05961_gb300/train_scheduler.py) against the library's fixed
+    default rule, on held-out generated tensors of the same distribution
+    (other seeds) and on a 5-mode probe tensor; regret = time of the chosen
+    schedule over the best one found by the exhaustive autotuner, minus 1."""
     import torch
 
-    import paper_1812_05961_gb300 as sptt
-    from paper_1812_05961_gb300 import schedtrain
+    from paper_1812_05961_gb300 import schedtrain, train_scheduler
     import tensorgen
 
-    def specs(n, seed):
-        g = np.random.default_rng(seed)
-        out = []
-        for i in range(n):
-            nm = int(g.integers(3, 6))
-            dims = [int(_m.exp(g.uniform(_m.log(100), _m.log(1e7)))) for _ in range(nm)]
-            space = float(np.prod(dims, dtype=np.float64))
-            nnz = int(min(_m.exp(g.uniform(_m.log(1e5), _m.log(2e7))), space / 4))
-            out.append((dims, max(nnz, 1000), float(g.uniform(0.8, 1.5)), int(g.choice([8, 16, 32, 64])),
-                        seed * 10000 + i))
-        return out
-
-    def dataset(sp):
-        ds = schedtrain.Dataset()
-        for dims, nnz, s_, R, sd in sp:
-            t = tensorgen.sample_unique(dims, nnz, sd, dev, "zipf", s=s_, values="uniform")
-            ds.samples += schedtrain.sweep_tensor(t.dims, t.inds, t.vals, R, reps=3)
-            del t
-            torch.cuda.empty_cache()
-        return ds
-
+    if not os.path.exists(train_scheduler.MODEL):
+        return {"unavailable": "no trained model at %s" % os.path.basename(train_scheduler.MODEL)}
+    with open(train_scheduler.MODEL) as f:
+        meta = json.load(f).get("meta", {})
+    model = train_scheduler.load()
     t0 = time.time()
-    train = dataset(specs(args.sched_train, 21))
-    held = dataset(specs(args.sched_heldout, 77))
-    probe = dataset([([1_000_000, 1_000_000, 100_000, 10_000, 500], 20_000_000, 1.1, 32, 5)])
-    sweep_s = time.time() - t0
-    model, hist = schedtrain.train(train, steps=3000, lr=3e-3)
-    res = {"train_samples": len(train.samples), "heldout_samples": len(held.samples), "sweep_s": round(sweep_s, 1),
-           "loss_first_last": [float(hist[0]), float(hist[-1])]}
-    for name, ds in (("heldout", held), ("probe_5mode_2e7", probe)):
+    held = train_scheduler.sweep(train_scheduler.tensor_specs(args.sched_heldout, seed=77), dev)
+    dims = [1_000_000, 1_000_000, 100_000, 10_000, 500]
+    t = tensorgen.sample_unique(dims, 200_000_000, 5, dev, "zipf", s=1.1, values="uniform")
+    probe = schedtrain.Dataset(schedtrain.sweep_tensor(t.dims, t.inds, t.vals, 32, reps=3, label="probe"))
+    del t
+    torch.cuda.empty_cache()
+    res = {"model": {k: meta.get(k) for k in ("tensors", "samples", "nnz_max", "steps", "loss_first_last")},
+           "heldout_tensors": args.sched_heldout, "heldout_samples": len(held.samples),
+           "sweep_s": round(time.time() - t0, 1)}
+    for name, ds in (("heldout", held), ("probe_5mode_2e8_r32", probe)):
         res[name] = {"learned": schedtrain.summarize(schedtrain.regret(ds, model)),
                      "default": schedtrain.summarize(schedtrain.regret(ds))}
     return res
@@ -504,9 +639,14 @@ def ours(args, rank, world, local):
     distinct = [int(torch.unique(x).numel()) for x in t.inds]
     torch.cuda.empty_cache()  # drop the generator's temporaries
 
-    # CSFs (one per root) are built inside the handle; build them here too for the byte model
-    csfs = [sptt.Csf(dims, t.inds, t.vals, r) for r in range(3)]
+    # CSFs (one per root) are built inside the handle; build the same ones
+    # here (the level order the handle takes by default) for the byte model
     bf16 = args.precision == "bf16"
+    gdt = sptt.SPTT_BF16 if bf16 else sptt.SPTT_F32
+    sched = None if (args.variant == 0 and args.chunk == 0) else (args.chunk, 256, args.variant, 0)
+    kinds = [sptt.sptt_sched_default(dims, r, R, gdt, nnz)[3] if sched is None else sched[3] for r in range(3)]
+    orders = [sptt.sptt_level_order(dims, r, kinds[r]) for r in range(3)]
+    csfs = [sptt.Csf(dims, t.inds, t.vals, r, level_order=orders[r]) for r in range(3)]
     s_f = 2 if bf16 else 4
     bytes_per = [byte_model(c, dims, R, distinct, s_f) for c in csfs]
     flops_per = [flop_model(c, R) for c in csfs]
@@ -515,7 +655,6 @@ def ours(args, rank, world, local):
     del csfs
 
     t_build = time.time()
-    sched = None if (args.variant == 0 and args.chunk == 0) else (args.chunk, 256, args.variant, 0)
     cpd = sptt.Cpd(dims, t.inds, t.vals, R, seed=1, profile=1, sched=sched,
                    precision=sptt.SPTT_BF16 if bf16 else sptt.SPTT_F32)
     t_build = time.time() - t_build
@@ -561,14 +700,16 @@ def ours(args, rank, world, local):
     if sched is None and R in (16,) and len(dims) == 3 and ncu is not None:
         traffic = sum(ncu["bytes"]) / 3 * nnz / ncu["nnz"]
     flops_s = sum(flops_per) * args.steps / (mttkrp_ms * 1e-3) / 1e12
+    fp32_peak, n_sms, peak_mhz = fp32_peak_tflops(dev)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "traffic_source": None if traffic is None else
                 "ncu dram__bytes_read.sum + dram__bytes_write.sum of %s at %d nnz, scaled by nnz (mean of the 3 roots)"
                 % (ncu["kernel"], ncu["nnz"]),
                 "every_gather_bytes_per_launch": [int(b) for b in gather_per],
-                "fp32_fma": {"achieved_tflops": flops_s, "peak_tflops": FP32_PEAK_TFLOPS,
-                             "frac": flops_s / FP32_PEAK_TFLOPS, "peak_kind": "derived from unit counts and clock"},
+                "fp32_fma": {"achieved_tflops": flops_s, "peak_tflops": fp32_peak,
+                             "frac": flops_s / fp32_peak,
+                             "peak_kind": "derived: %d SMs x 128 FP32 lanes x 2 x %.0f MHz" % (n_sms, peak_mhz)},
                 "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                 else "fallback 6.8 TB/s",
                 "bytes_per_launch": [int(b) for b in bytes_per],
@@ -604,23 +745,32 @@ def ours(args, rank, world, local):
 
     extras = {}
     if not args.no_extras:
-        # mixed precision vs FP32 at the same start, plus rank 32
+        # mixed precision vs FP32 at the same start, plus rank 32: 20
+        # iterations each; the mixed run's last iteration is its FP32
+        # refinement sweep, and its time is counted
         res = {}
         for name, prec, r in (("fp32_r16", sptt.SPTT_F32, R), ("bf16_r16", sptt.SPTT_BF16, R),
                               ("fp32_r32", sptt.SPTT_F32, 32), ("bf16_r32", sptt.SPTT_BF16, 32)):
             c = sptt.Cpd(dims, t.inds, t.vals, r, seed=1, precision=prec).init()
-            c.iterate(2)
+            c.iterate(1)  # warm-up: the first call of each precision captures its graph
+            if prec == sptt.SPTT_BF16:
+                c.refine(1)
+            c.init()
             torch.cuda.synchronize()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            c.iterate(18)
+            if prec == sptt.SPTT_BF16:
+                c.iterate(19)
+                c.refine(1)
+            else:
+                c.iterate(20)
             b.record(stream)
             torch.cuda.synchronize()
-            s_iter = a.elapsed_time(b) / 18 / 1e3
-            if prec == sptt.SPTT_BF16:
-                c.refine(1)
+            s_iter = a.elapsed_time(b) / 20 / 1e3
             res[name] = {"s_per_iter": s_iter, "fit_after_20": c.fit()[0],
-                         "GnnzR_per_s": 3 * nnz * r / s_iter / 1e9}
+                         "GnnzR_per_s": 3 * nnz * r / s_iter / 1e9,
+                         "note": "20 iterations timed from the initial factors" +
+                                 (", the last one the FP32 refinement sweep" if prec == sptt.SPTT_BF16 else "")}
             del c
         for r in (16, 32):
             f32, b16 = res["fp32_r%d" % r], res["bf16_r%d" % r]
@@ -628,28 +778,35 @@ def ours(args, rank, world, local):
             b16["speedup_vs_fp32"] = f32["s_per_iter"] / b16["s_per_iter"]
         extras["precision_and_rank"] = res
 
-    if args.extra_batched:
+    if not args.no_extras and not args.no_batched and rank == 0:
         del cpd
         torch.cuda.empty_cache()
         extras["batched"] = batched_extra(args, dev)
-    if args.extra_sched:
+    if not args.no_extras and not args.no_sched and rank == 0:
         torch.cuda.empty_cache()
         extras["scheduler"] = sched_extra(args, dev)
     if args.extra_one_csf:
         torch.cuda.empty_cache()
         extras["one_csf"] = one_csf_extra(args, t, R, dev)
-    if args.extra_mixed4:
+    if not args.no_extras and not args.no_mixed4 and rank == 0:
         torch.cuda.empty_cache()
         extras["mixed_precision_4mode"] = mixed4_extra(args, dev)
+    if not args.no_extras and not args.no_mixed4 and rank == 0 and world == 1:
+        torch.cuda.empty_cache()
+        extras["mixed_vs_oracle"] = mixed_vs_oracle_extra(dev)
 
     cpu_base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
         ci = [x.cpu().numpy() for x in t.inds]
         cv = t.vals.cpu().numpy()
-        rate, secs, s = cpu_oracle_rate(ci, cv, dims, R, args.cpu_seconds)
-        cpu_base = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+        cores, model = host_cpu()
+        threads = oracle.set_threads(cores)
+        rate, secs, s = cpu_oracle_rate(ci, cv, dims, R, args.cpu_seconds, threads)
+        cpu_base = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+                    "host_cores": cores, "cpu_model": model,
                     "sample": "one CP-ALS iteration (3 MTTKRPs + solve + fit) of the FP64 C oracle on "
-                              "the first %d of the %d non-zeros, single thread, %.1f s" % (s, nnz, secs)}
+                              "the first %d of the %d non-zeros, %d threads, %.1f s" % (s, nnz, threads, secs)}
 
     clocks = clk.summary()
     if rank == 0:
@@ -662,7 +819,8 @@ def ours(args, rank, world, local):
                        "mttkrp_sched": "default" if sched is None else list(sched),
                        "l2": "inputs larger than L2 (CSF about 0.8 GB per mode)",
                        "parallelism": "replicas" if world > 1 else "single",
-                       "nfibs_per_root": nfibs, "gen_s": round(t_gen, 1), "cpd_create_s": round(t_build, 2)},
+                       "nfibs_per_root": nfibs, "level_orders": orders,
+                       "gen_s": round(t_gen, 1), "cpd_create_s": round(t_build, 2)},
             "roofline": roofline, "cpu_baseline": cpu_base, "e2e": e2e, "gpu_launches": launches,
             "clocks": clocks, "routines_ms_per_iter": routines, "fit": fit, "extras": extras,
         }
