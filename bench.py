@@ -48,16 +48,13 @@ def parse():
     p.add_argument("--e2e-iters", type=int, default=20)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-extras", action="store_true")
+    p.add_argument("--extras", default="precision,mixed4,mixed_vs_oracle,batched,sched,tiling",
+                   help="comma list of the extra measurements to run (default: all): precision (FP32 vs BF16 "
+                        "at R = 16, 32), mixed4 (4-mode R = 64 mixed vs FP32), mixed_vs_oracle, batched (512 "
+                        "tensors, autotuned plan), sched (learned scheduler vs the default), tiling (R = 32)")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
-    p.add_argument("--no-batched", action="store_true",
-                   help="skip the 512-tensor batched workload (one persistent launch per run, autotuned plan)")
-    p.add_argument("--no-sched", action="store_true",
-                   help="skip the learned scheduler's held-out regret against the fixed default")
     p.add_argument("--extra-one-csf", action="store_true",
                    help="also time one CSF for all modes (non-root MTTKRPs with privatised hot rows)")
-    p.add_argument("--no-mixed4", action="store_true",
-                   help="skip the 4-mode R=64 mixed-precision comparison (BF16 gathers + FP32 sweep vs FP32) "
-                        "and its scaled-down comparison with the FP64 oracle")
     p.add_argument("--batch-count", type=int, default=512)
     p.add_argument("--sched-heldout", type=int, default=40)
     p.add_argument("--variant", type=int, default=0, help="MTTKRP kernel variant for every mode (0 = default)")
@@ -267,15 +264,20 @@ def every_gather_model(csf, R, s_f=4):
     return sum(csf.nfibs[1:]) * R * s_f
 
 
-# DRAM bytes (read + write) per launch of the default FP32 MTTKRP kernel,
-# from one ncu capture of the 2e7-non-zero case of this workload (roots
-# 0, 1, 2); the traffic is dominated by the leaf-record stream, so it is
-# scaled to other sizes by the number of non-zeros.
-NCU_TRAFFIC = {"kernel": "mttkrp_flag_kernel<3, float, 2, 2, 32, 1, 1, 0>", "variant": 7, "nnz": 20_000_000,
-               "bytes": [368.293888e6, 409.197568e6, 409.038336e6]}
-# The same for the default BF16-gather kernel (variant 11).
-NCU_TRAFFIC_BF16 = {"kernel": "mttkrp_flag_kernel<3, __nv_bfloat16, 4, 2, 16, 1, 1, 1>", "variant": 11,
-                    "nnz": 20_000_000, "bytes": [367.383296e6, 360.050944e6, 358.682368e6]}
+# DRAM bytes (read + write) per launch of the default MTTKRP kernels, from
+# one ncu capture at 3.4e7 non-zeros of this workload (roots 0, 1, 2; at this
+# size the default rule picks the kernels it picks at 1e8: the table kernel
+# for roots 0 and 1, the select walk for root 2); the traffic is dominated by
+# the leaf-record stream, so it is scaled to other sizes by the number of
+# non-zeros.
+NCU_TRAFFIC = {"kernel": "mttkrp_table_kernel<3, float, 2, 1024, 16> (roots 0, 1), "
+                         "mttkrp_select_kernel<3, float, 4, 2, 16> (root 2)",
+               "nnz": 34_000_000, "bytes": [685.780480e6, 801.106176e6, 685.219840e6]}
+# The same for the default BF16-gather kernel (variant 13 at every root).
+NCU_TRAFFIC_BF16 = {"kernel": "mttkrp_select_kernel<3, __nv_bfloat16, 4, 2, 16>", "nnz": 34_000_000,
+                    "bytes": [643.358976e6, 643.095296e6, 640.092160e6]}
+
+
 def fp32_peak_tflops(dev, sm_mhz=None):
     """FP32 FMA peak from the unit counts and the clock: the device's SM
     count x 128 FP32 lanes x 2 flops x the maximum SM clock (from
@@ -477,6 +479,46 @@ def mixed4_extra(args, dev):
     out["speedup_converged"] = out["fp32"]["converged"]["s"] / out["bf16"]["converged"]["s"]
     del t
     torch.cuda.empty_cache()
+    return out
+
+
+def tiling_extra(args, t, dev):
+    """Mode tiling at R = 32 with FP32 gathers on the bench tensor (the
+    2,000-row leaf factor is 256 KB, above the 160 KB shared-memory table):
+    tiles of as many rows as the table holds against the untiled default;
+    s/iter, MTTKRP ms per launch, the HBM fraction under the untiled CSFs'
+    byte model (the same MTTKRP work) and the fit after 10 iterations."""
+    import torch
+
+    import paper_1812_05961_gb300 as sptt
+    R, dims = 32, t.dims
+    distinct = [int(torch.unique(x).numel()) for x in t.inds]
+    stream = torch.cuda.current_stream()
+    orders = [sptt.sptt_level_order(dims, r, sptt.sptt_sched_default(dims, r, R, sptt.SPTT_F32, t.nnz)[3])
+              for r in range(3)]
+    csfs = [sptt.Csf(dims, t.inds, t.vals, r, level_order=orders[r]) for r in range(3)]
+    bpl = sum(byte_model(c, dims, R, distinct, 4) for c in csfs) / 3
+    del csfs
+    peak, kind = measured_peaks()
+    out = {"rank": R, "byte_model_per_launch_untiled": int(bpl)}
+    for name, kw in (("untiled", {}), ("tiled", {"leaf_tile_rows": -1})):
+        c = sptt.Cpd(dims, t.inds, t.vals, R, seed=1, profile=1, **kw).init()
+        c.iterate(2)
+        torch.cuda.synchronize()
+        c.timers()
+        base = c.timers()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        c.iterate(8)
+        b.record(stream)
+        torch.cuda.synchronize()
+        tm = c.timers()
+        ms = (tm["mttkrp"][0] - base["mttkrp"][0]) / max(tm["mttkrp"][1] - base["mttkrp"][1], 1)
+        out[name] = {"s_per_iter": a.elapsed_time(b) / 8 / 1e3, "mttkrp_ms_per_launch": ms,
+                     "frac_of_hbm_under_untiled_model": bpl / (ms * 1e-3) / 1e9 / peak, "fit_after_10": c.fit()[0]}
+        del c
+        torch.cuda.empty_cache()
+    out["peak_kind"] = kind
     return out
 
 
@@ -697,7 +739,8 @@ def ours(args, rank, world, local):
     # measured traffic applies while the timed kernel is the captured one
     traffic = None
     ncu = NCU_TRAFFIC_BF16 if bf16 else NCU_TRAFFIC
-    if sched is None and R in (16,) and len(dims) == 3 and ncu is not None:
+    # (the FP32 capture is of the kernels the default rule picks from 2^25 non-zeros on)
+    if sched is None and R in (16,) and len(dims) == 3 and ncu is not None and (bf16 or nnz >= 2 ** 25):
         traffic = sum(ncu["bytes"]) / 3 * nnz / ncu["nnz"]
     flops_s = sum(flops_per) * args.steps / (mttkrp_ms * 1e-3) / 1e12
     fp32_peak, n_sms, peak_mhz = fp32_peak_tflops(dev)
@@ -744,7 +787,8 @@ def ours(args, rank, world, local):
         del h_inds, h_vals
 
     extras = {}
-    if not args.no_extras:
+    want = set() if args.no_extras else set(x.strip() for x in args.extras.split(",") if x.strip())
+    if "precision" in want:
         # mixed precision vs FP32 at the same start, plus rank 32: 20
         # iterations each; the mixed run's last iteration is its FP32
         # refinement sweep, and its time is counted
@@ -778,20 +822,23 @@ def ours(args, rank, world, local):
             b16["speedup_vs_fp32"] = f32["s_per_iter"] / b16["s_per_iter"]
         extras["precision_and_rank"] = res
 
-    if not args.no_extras and not args.no_batched and rank == 0:
+    if "batched" in want and rank == 0:
         del cpd
         torch.cuda.empty_cache()
         extras["batched"] = batched_extra(args, dev)
-    if not args.no_extras and not args.no_sched and rank == 0:
+    if "sched" in want and rank == 0:
         torch.cuda.empty_cache()
         extras["scheduler"] = sched_extra(args, dev)
+    if "tiling" in want and rank == 0:
+        torch.cuda.empty_cache()
+        extras["tiling"] = tiling_extra(args, t, dev)
     if args.extra_one_csf:
         torch.cuda.empty_cache()
         extras["one_csf"] = one_csf_extra(args, t, R, dev)
-    if not args.no_extras and not args.no_mixed4 and rank == 0:
+    if "mixed4" in want and rank == 0:
         torch.cuda.empty_cache()
         extras["mixed_precision_4mode"] = mixed4_extra(args, dev)
-    if not args.no_extras and not args.no_mixed4 and rank == 0 and world == 1:
+    if "mixed_vs_oracle" in want and rank == 0 and world == 1:
         torch.cuda.empty_cache()
         extras["mixed_vs_oracle"] = mixed_vs_oracle_extra(dev)
 

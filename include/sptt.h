@@ -161,8 +161,8 @@ sptt_status sptt_csf_copy_level(const sptt_csf *csf, int32_t level, int32_t *fpt
  *               shared memory once per CTA, 16-byte segments, one CTA of
  *               1024 threads in batches of 2 / 512 threads in batches of 4,
  *               used when that copy is at most 160 KB (else run as 13).
- *               Default: 13; with F32 gathers on a tensor of at least 2^25
- *               non-zeros whose leaf factor fits, 14. Variants 7 and 9..15
+ *               Default: 13; with F32 gathers on a 3-mode tensor of at
+ *               least 2^25 non-zeros whose leaf factor fits, 14. Variants 7 and 9..15
  *               (and so the default) read packed
  *               16-byte leaf records that the first call builds (16 bytes
  *               per non-zero on the device, kept with the CSF)
@@ -175,7 +175,7 @@ typedef struct {
                        length, 1 = descending, 2 = the shortest mode at the leaves and
                        the others ascending above it; ignored by sptt_mttkrp. CP-ALS
                        without a schedule builds order 2 for FP32 gathers on a
-                       tensor of at least 2^25 non-zeros when the shortest mode's
+                       3-mode tensor of at least 2^25 non-zeros when the shortest mode's
                        factor fits the shared-memory table of the default kernel
                        (160 KB), else order 0 */
 } sptt_sched;
@@ -296,6 +296,16 @@ sptt_status sptt_gram_noalloc(const float *A, int64_t rows, int32_t rank, int32_
  *                 mode takes the output-conflict strategy (privatised hot
  *                 rows or global reductions) that ran faster in a timing
  *                 at create time (which therefore synchronises).
+ *   leaf_tile_rows  mode tiling (SPLATT's tiling option, which the paper's
+ *                 port omits, Section V): 0 = off; > 0: every mode whose CSF
+ *                 has a leaf mode longer than this splits its non-zeros into
+ *                 tiles of that many leaf indices, each its own CSF, and runs
+ *                 its MTTKRP tile by tile with that tile's leaf rows in shared
+ *                 memory (rows x round_up(rank, 8) x 4 bytes must be at most
+ *                 160 KB, else BAD_ARG), adding the tiles' results in tile
+ *                 order; -1: tiles as large as that table holds. Needs
+ *                 csf_mode 0 and plan 0; tensors of 3 or more modes; at most
+ *                 1024 tiles per mode (a mode with more stays untiled)
  */
 typedef struct sptt_mlp sptt_mlp;
 typedef struct {
@@ -309,6 +319,7 @@ typedef struct {
     int32_t plan;
     const sptt_mlp *mlp;
     int32_t csf_mode;
+    int32_t leaf_tile_rows;
 } sptt_opts;
 
 typedef struct sptt_cpd sptt_cpd;
@@ -441,7 +452,7 @@ int32_t sptt_sched_candidates(int64_t nnz, sptt_sched *out, int32_t cap);
 /* The schedule the library uses for the root-`root` MTTKRP of a tensor of
  * nnz non-zeros with these mode lengths (host array), rank and gather type
  * when none is given: the level order CP-ALS builds (2 with F32 gathers on a
- * tensor of at least 2^25 non-zeros when the shortest other mode's factor
+ * 3-mode tensor of at least 2^25 non-zeros when the shortest other mode's factor
  * fits the 160 KB shared-memory table, else 0), the default variant for that
  * order's leaf mode and size, and the default chunk.
  * This is the fixed rule the learned scheduler is measured against. */

@@ -59,7 +59,7 @@ class sptt_opts(ctypes.Structure):
                 ("refine_iters", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("profile", ctypes.c_int32), ("sched", ctypes.POINTER(sptt_sched)),
                 ("mode_sched", ctypes.POINTER(sptt_sched)), ("plan", ctypes.c_int32),
-                ("mlp", ctypes.c_void_p), ("csf_mode", ctypes.c_int32)]
+                ("mlp", ctypes.c_void_p), ("csf_mode", ctypes.c_int32), ("leaf_tile_rows", ctypes.c_int32)]
 
 
 _lib = None
@@ -197,9 +197,10 @@ def _sched(s):
 
 
 def _opts(seed=0, precision=SPTT_F32, refine_iters=0, use_graph=0, profile=0, sched=None,
-          mode_sched=None, plan=0, mlp=None, csf_mode=0):
+          mode_sched=None, plan=0, mlp=None, csf_mode=0, leaf_tile_rows=0):
     o = sptt_opts(seed, precision, refine_iters, use_graph, profile, None, None, plan,
-                  None if mlp is None else (mlp.handle if hasattr(mlp, "handle") else mlp), csf_mode)
+                  None if mlp is None else (mlp.handle if hasattr(mlp, "handle") else mlp), csf_mode,
+                  leaf_tile_rows)
     keep = []
     if sched is not None:
         one = _sched(sched)

@@ -43,6 +43,13 @@ struct sptt_cpd {
     cudaEvent_t ev_fork[SPTT_MAX_MODES] = {nullptr};
     cudaEvent_t ev_join[SPTT_MAX_MODES] = {nullptr};
     sptt_csf *csf[SPTT_MAX_MODES] = {nullptr};
+    // opts.leaf_tile_rows: the modes whose MTTKRP runs over leaf-index tiles
+    // (tiling.cu), each tile a CSF of its own; tbase = each tile's first leaf
+    // index; their MTTKRP result is full (Mfull, dims x ld)
+    std::vector<sptt_csf *> tcsf[SPTT_MAX_MODES];
+    std::vector<int64_t> tbase[SPTT_MAX_MODES];
+    int32_t tleaf[SPTT_MAX_MODES] = {0};  // the leaf mode of a tiled mode's CSFs
+    float *Mfull = nullptr;
     // csf_mode 1/2: one CSF for every mode; one_level[n] = the tree level of mode n
     sptt_csf *one = nullptr;
     int32_t one_level[SPTT_MAX_MODES] = {0};
@@ -145,10 +152,29 @@ sptt_status run_iteration(sptt_cpd *c, bool bf16) {
             }
             SPTT_CUDA(cudaEventRecord(c->ev_join[n], c->side));
         }
+        const bool tiled = !c->tcsf[n].empty();
         {
             Timed t(c, 0);
-            if (L == 0) SPTT_TRY(mttkrp_launch(cs, fac, dt, c->ld, c->M, c->Mh, sched, c->st));
-            else SPTT_TRY(mttkrp_mode_launch(cs, L, fac, dt, c->ld, c->M, &c->one_sched[n], c->st));
+            if (tiled) {
+                // the tiles' MTTKRPs, each added into the full result in tile order
+                SPTT_TRY(fill_zero_launch(c->Mfull, (size_t)c->dims[n] * c->ld * sizeof(float), c->st));
+                // the leaf rows of a tile fit the shared-memory table (the 512-thread form for BF16 rows)
+                sptt_sched ts = sched ? *sched : sptt_sched{};
+                if (!sched) ts.variant = bf16 ? 15 : 14;
+                const int esz = bf16 ? 2 : 4;
+                for (size_t k = 0; k < c->tcsf[n].size(); ++k) {
+                    const void *tf[SPTT_MAX_MODES];
+                    for (int m = 0; m < N; ++m) tf[m] = fac[m];
+                    const int lm = c->tleaf[n];
+                    tf[lm] = static_cast<const char *>(fac[lm]) + (size_t)c->tbase[n][k] * c->ld * esz;
+                    SPTT_TRY(mttkrp_launch(c->tcsf[n][k], tf, dt, c->ld, c->M, c->Mh, &ts, c->st));
+                    SPTT_TRY(tile_accumulate_launch(c->tcsf[n][k], c->M, c->Mh, c->ld, c->Mfull, c->st));
+                }
+            } else if (L == 0) {
+                SPTT_TRY(mttkrp_launch(cs, fac, dt, c->ld, c->M, c->Mh, sched, c->st));
+            } else {
+                SPTT_TRY(mttkrp_mode_launch(cs, L, fac, dt, c->ld, c->M, &c->one_sched[n], c->st));
+            }
         }
         if (fork) {
             SPTT_CUDA(cudaStreamWaitEvent(c->st, c->ev_join[n], 0));
@@ -157,9 +183,10 @@ sptt_status run_iteration(sptt_cpd *c, bool bf16) {
             SPTT_TRY(normal_prep_launch(c->G, N, n, c->rank, &c->w, c->st));
         }
         // the compact result of a root mode maps slice f to row fids[0][f];
-        // a non-root mode's result is full (row i is row i)
-        const int32_t *rowmap = L == 0 ? cs->fids[0] : nullptr;
-        const int64_t nrows = L == 0 ? cs->nfibs[0] : c->dims[n];
+        // a non-root mode's result and a tiled mode's are full (row i is row i)
+        const int32_t *rowmap = (L == 0 && !tiled) ? cs->fids[0] : nullptr;
+        const int64_t nrows = (L == 0 && !tiled) ? cs->nfibs[0] : c->dims[n];
+        const float *Mres = tiled ? c->Mfull : c->M;
         {
             Timed t(c, 2);
             // rows of mode n without a slice come out zero: clear A (and its
@@ -167,7 +194,8 @@ sptt_status run_iteration(sptt_cpd *c, bool bf16) {
             SPTT_TRY(fill_zero_launch(c->A[n], (size_t)c->dims[n] * c->ld * sizeof(float), c->st));
             if (c->Ab[n])
                 SPTT_TRY(fill_zero_launch(c->Ab[n], (size_t)c->dims[n] * c->ld * sizeof(__nv_bfloat16), c->st));
-            SPTT_TRY(postsolve_launch(c->M, L == 0 ? c->Mh : nullptr, L == 0 ? cs->hidx : nullptr, rowmap, c->A[n],
+            const bool compact = L == 0 && !tiled;
+            SPTT_TRY(postsolve_launch(Mres, compact ? c->Mh : nullptr, compact ? cs->hidx : nullptr, rowmap, c->A[n],
                                       nrows, &c->w, c->st));
         }
         {
@@ -195,8 +223,16 @@ sptt_status prepare_all(sptt_cpd *c) {
                 SPTT_TRY(mttkrp_mode_prepare(c->one, c->one_level[n], c->ld, &c->one_sched[n], c->st));
         return SPTT_OK;
     }
-    for (int n = 0; n < c->N; ++n)
-        SPTT_TRY(mttkrp_prepare(c->csf[n], c->has_msched[n] ? &c->msched[n] : nullptr, c->st));
+    for (int n = 0; n < c->N; ++n) {
+        const sptt_sched *s = c->has_msched[n] ? &c->msched[n] : nullptr;
+        if (c->tcsf[n].empty()) {
+            SPTT_TRY(mttkrp_prepare(c->csf[n], s, c->st));
+            continue;
+        }
+        sptt_sched ts = s ? *s : sptt_sched{};
+        if (!s) ts.variant = 14;
+        for (auto *t : c->tcsf[n]) SPTT_TRY(mttkrp_prepare(t, &ts, c->st));
+    }
     return SPTT_OK;
 }
 
@@ -280,8 +316,10 @@ sptt_status step(sptt_cpd *c, bool bf16) {
 sptt_status read_fit(sptt_cpd *c, int64_t it, double *out) {
     SPTT_CUDA(cudaMemcpyAsync(out, c->fits + (it % kFitHistory), sizeof(double), cudaMemcpyDeviceToHost, c->st));
     if (c->one) SPTT_TRY(sptt_csf_check(c->one, c->st));  // synchronises
-    for (int m = 0; m < c->N; ++m)
+    for (int m = 0; m < c->N; ++m) {
         if (c->csf[m]) SPTT_TRY(sptt_csf_check(c->csf[m], c->st));
+        for (auto *t : c->tcsf[m]) SPTT_TRY(sptt_csf_check(t, c->st));
+    }
     return SPTT_OK;
 }
 
@@ -291,11 +329,13 @@ void destroy(sptt_cpd *c) {
     if (c->one) csf_destroy(c->one);
     for (int m = 0; m < SPTT_MAX_MODES; ++m) {
         if (c->csf[m]) csf_destroy(c->csf[m]);
+        for (auto *t : c->tcsf[m]) csf_destroy(t);
         if (c->A[m]) dev_free(c->A[m], c->st);
         if (c->Ab[m]) dev_free(c->Ab[m], c->st);
         if (c->G[m]) dev_free(c->G[m], c->st);
     }
     if (c->M) dev_free(c->M, c->st);
+    if (c->Mfull) dev_free(c->Mfull, c->st);
     if (c->Mh) dev_free(c->Mh, c->st);
     if (c->normx2) dev_free(c->normx2, c->st);
     if (c->fits) dev_free(c->fits, c->st);
@@ -351,6 +391,11 @@ extern "C" sptt_status sptt_cpd_create(const sptt_coo *coo, int32_t rank, const 
     if (o.csf_mode != 0 && (o.plan != 0 || o.mode_sched))
         return set_error(SPTT_ERR_BAD_ARG, "one CSF for all modes takes one schedule (opts.sched) and plan 0");
     if (o.plan == 2 && !o.mlp) return set_error(SPTT_ERR_BAD_ARG, "opts.plan = 2 needs opts.mlp");
+    if (o.leaf_tile_rows < -1) return set_error(SPTT_ERR_BAD_ARG, "opts.leaf_tile_rows must be -1, 0 or > 0");
+    if (o.leaf_tile_rows != 0 && (o.csf_mode != 0 || o.plan != 0))
+        return set_error(SPTT_ERR_BAD_ARG, "leaf tiling takes one CSF per mode and plan 0");
+    if (o.leaf_tile_rows > 0 && !leaf_table_fits(o.leaf_tile_rows, (rank + 7) / 8 * 8, 4))
+        return set_error(SPTT_ERR_BAD_ARG, "opts.leaf_tile_rows rows of the factor must fit the 160 KB shared-memory table");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     sptt_cpd *c = new sptt_cpd();
     struct Guard {
@@ -410,9 +455,26 @@ extern "C" sptt_status sptt_cpd_create(const sptt_coo *coo, int32_t rank, const 
                 c->msched[m] = cands[best];
                 c->has_msched[m] = true;
             }
-            const int kind = c->has_msched[m] ? c->msched[m].order : default_order_kind(c, m, coo->nnz);
+            // with leaf tiling and no schedule, 3-mode tensors put the shortest other
+            // mode at the leaves (fewest tiles)
+            const int kind = c->has_msched[m] ? c->msched[m].order
+                             : (o.leaf_tile_rows != 0 && c->N == 3) ? 2
+                                                                     : default_order_kind(c, m, coo->nnz);
             int32_t order[SPTT_MAX_MODES];
             level_order(c->dims, c->N, m, kind, order);
+            if (o.leaf_tile_rows != 0) {
+                // leaf tiling: tiles of leaf_tile_rows rows (-1: as many as the table holds)
+                // wherever the leaf factor is larger than one tile and the tiles are few enough
+                const int32_t rows = o.leaf_tile_rows > 0 ? o.leaf_tile_rows
+                                                          : (int32_t)(kTableMaxBytes / ((size_t)c->ld * 4));
+                const int64_t dl = c->dims[order[c->N - 1]];
+                const int64_t nt = (dl + rows - 1) / rows;
+                if (c->N >= 3 && nt > 1 && nt <= kMaxTiles) {
+                    c->tleaf[m] = order[c->N - 1];
+                    SPTT_TRY(tiles_build(&dc.coo, m, order, rows, st, &c->tcsf[m], &c->tbase[m]));
+                    continue;
+                }
+            }
             SPTT_TRY(csf_build_device(&dc.coo, m, order, st, &c->csf[m]));
             if (o.plan == 2) {  // learned scheduler on the default CSF's statistics
                 float feat[16];
@@ -434,14 +496,24 @@ extern "C" sptt_status sptt_cpd_create(const sptt_coo *coo, int32_t rank, const 
     }
     int64_t max_rows = 0, max_slices = 0, max_heavy = 0;
     SPTT_TRY(prepare_all(c));
+    int64_t max_full = 0;  // rows of the full result of the tiled modes
     for (int m = 0; m < c->N; ++m) {
         const int64_t rows = c->dims[m];
         if (rows > max_rows) max_rows = rows;
-        // rows of the MTTKRP result of mode m: compact for a root mode, full otherwise
-        const sptt_csf *cs = c->one ? c->one : c->csf[m];
-        const int64_t mrows = (c->one && c->one_level[m] > 0) ? rows : cs->nfibs[0];
-        if (mrows > max_slices) max_slices = mrows;
-        if (cs->nheavy > max_heavy) max_heavy = cs->nheavy;
+        if (!c->tcsf[m].empty()) {
+            // a tile's compact result goes through M and Mh, the sum of the tiles through Mfull
+            if (rows > max_full) max_full = rows;
+            for (auto *t : c->tcsf[m]) {
+                if (t->nfibs[0] > max_slices) max_slices = t->nfibs[0];
+                if (t->nheavy > max_heavy) max_heavy = t->nheavy;
+            }
+        } else {
+            // rows of the MTTKRP result of mode m: compact for a root mode, full otherwise
+            const sptt_csf *cs = c->one ? c->one : c->csf[m];
+            const int64_t mrows = (c->one && c->one_level[m] > 0) ? rows : cs->nfibs[0];
+            if (mrows > max_slices) max_slices = mrows;
+            if (cs->nheavy > max_heavy) max_heavy = cs->nheavy;
+        }
         SPTT_TRY(dev_alloc_n(&c->A[m], (size_t)rows * c->ld, st));
         SPTT_TRY(fill_zero_launch(c->A[m], (size_t)rows * c->ld * sizeof(float), st));
         if (o.precision == SPTT_BF16) {
@@ -451,6 +523,7 @@ extern "C" sptt_status sptt_cpd_create(const sptt_coo *coo, int32_t rank, const 
         SPTT_TRY(dev_alloc_n(&c->G[m], (size_t)rank * rank, st));
     }
     SPTT_TRY(dev_alloc_n(&c->M, (size_t)max_slices * c->ld, st));
+    if (max_full > 0) SPTT_TRY(dev_alloc_n(&c->Mfull, (size_t)max_full * c->ld, st));
     SPTT_TRY(dev_alloc_n(&c->Mh, (size_t)max_heavy * c->ld, st));
     SPTT_TRY(dev_alloc_n(&c->normx2, 1, st));
     SPTT_TRY(dev_alloc_n(&c->fits, kFitHistory, st));
@@ -458,8 +531,24 @@ extern "C" sptt_status sptt_cpd_create(const sptt_coo *coo, int32_t rank, const 
     SPTT_TRY(dev_alloc_n(&c->iter_dev, 1, st));
     SPTT_TRY(fill_zero_launch(c->iter_dev, sizeof(int64_t), st));
     SPTT_TRY(dense_work_alloc(&c->w, rank, c->ld, max_rows, st));
-    const sptt_csf *c0 = c->one ? c->one : c->csf[0];
-    SPTT_TRY(sumsq_launch(c0->vals, c0->nfibs[c0->nmodes - 1], c->normx2, st));
+    // |X|^2 over the coalesced non-zeros: any untiled CSF holds all of them, a
+    // tiled mode's tiles together do
+    const sptt_csf *c0 = c->one;
+    for (int m = 0; m < c->N && !c0; ++m) c0 = c->csf[m];
+    if (c0) {
+        SPTT_TRY(sumsq_launch(c0->vals, c0->nfibs[c0->nmodes - 1], c->normx2, st));
+    } else {
+        double total = 0.0;
+        for (auto *t : c->tcsf[0]) {
+            double part = 0.0;
+            SPTT_TRY(sumsq_launch(t->vals, t->nfibs[t->nmodes - 1], c->normx2, st));
+            SPTT_CUDA(cudaMemcpyAsync(&part, c->normx2, sizeof(double), cudaMemcpyDeviceToHost, st));
+            SPTT_CUDA(cudaStreamSynchronize(st));
+            total += part;
+        }
+        SPTT_CUDA(cudaMemcpyAsync(c->normx2, &total, sizeof(double), cudaMemcpyHostToDevice, st));
+        SPTT_CUDA(cudaStreamSynchronize(st));
+    }
     if (c->one && !(c->has_msched[0] && c->msched[0].variant != 0)) {
         for (int m = 0; m < c->N; ++m)
             SPTT_TRY(init_factor_launch(c->opts.seed, m, c->dims[m], c->rank, c->ld, c->A[m], st));

@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/sptt.h"
 
@@ -193,14 +194,16 @@ int32_t default_chunk(int64_t nnz);
 constexpr size_t kTableMaxBytes = 160 * 1024;
 // Whether a leaf factor of leaf_rows rows of ld elements of esz bytes fits.
 bool leaf_table_fits(int64_t leaf_rows, int32_t ld, int esz);
-// Smallest tensor for which the defaults take the table kernel (below it the
-// shortest mode at the leaves multiplies the leaf-parent fibers more than the
-// shared-memory table saves).
+// Smallest tensor for which the defaults take the table kernel: on smaller
+// tensors, and on any tensor of 4 or more modes (whose leaf-parent fibers are
+// tuples of 3 or more indices, nearly one per leaf), putting the shortest mode
+// at the leaves multiplies the fibers more than the shared-memory table saves.
 constexpr int64_t kTableMinNnz = int64_t(1) << 25;
-// The default MTTKRP variant for a gather type, row width, leaf-mode length and size.
-int default_variant(int32_t dtype, int32_t ld, int64_t leaf_rows, int64_t nnz);
+// The default MTTKRP variant for a gather type, row width, leaf-mode length,
+// size and mode count.
+int default_variant(int32_t dtype, int32_t ld, int64_t leaf_rows, int64_t nnz, int nmodes);
 // The default CSF level-order kind of the CSF rooted at `root` (see
-// level_order): with FP32 gathers, N >= 3 and at least kTableMinNnz
+// level_order): with FP32 gathers on a 3-mode tensor of at least kTableMinNnz
 // non-zeros, 2 when the shortest other mode's factor fits the shared-memory
 // table, else 0.
 int default_order_kind(const int64_t *dims, int nmodes, int root, int32_t ld, int32_t dtype, int64_t nnz);
@@ -212,6 +215,20 @@ sptt_status mttkrp_mode_prepare(sptt_csf *csf, int32_t L, int32_t ld, const sptt
 sptt_status mttkrp_mode_launch(sptt_csf *csf, int32_t L, const void *const *factors, int32_t dtype, int32_t ld,
                                float *out, const sptt_sched *sched, cudaStream_t st);
 int csf_level_of(const sptt_csf *csf, int32_t mode);
+
+// ---------------------------------------------------------------------------
+// Mode tiling (tiling.cu)
+// ---------------------------------------------------------------------------
+constexpr int kMaxTiles = 1024;
+// The CSFs (rooted at `root`, level order `order`) of the tiles of a device
+// COO whose leaf-mode index lies in [t * rows, (t + 1) * rows), leaf index
+// rebased; base[i] = the first leaf index of csfs[i]'s tile (empty tiles are
+// skipped). BAD_ARG for an index out of range. Synchronises.
+sptt_status tiles_build(const sptt_coo *coo_dev, int32_t root, const int32_t *order, int32_t rows,
+                        cudaStream_t st, std::vector<sptt_csf *> *csfs, std::vector<int64_t> *base);
+// out[fids0[f]] += row f of the tile's compact MTTKRP (FP64 rows where it has them).
+sptt_status tile_accumulate_launch(const sptt_csf *tile, const float *compact, const double *heavy, int32_t ld,
+                                   float *out, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // Dense kernels (dense.cu)

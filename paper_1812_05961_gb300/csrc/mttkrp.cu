@@ -353,13 +353,13 @@ int32_t default_chunk(int64_t nnz) {
 static bool staged_variant(int v) { return v == 6 || v == 8; }
 
 // The default variant: the select walk with 16-byte segments in batches of 4
-// (within 4-15 % of the best candidate on average for every rank 8-64 and
-// both gather types over generated tensors of 1e5-2e7 non-zeros), and for
-// large tensors with FP32 gathers whose leaf factor fits in shared memory
-// the table kernel (on the 1e8-non-zero 3-mode power-law tensor 12 % faster
-// than the best global-memory walk).
-int default_variant(int32_t dtype, int32_t ld, int64_t leaf_rows, int64_t nnz) {
-    if (dtype == SPTT_F32 && nnz >= kTableMinNnz && leaf_table_fits(leaf_rows, ld, 4)) return 14;
+// (the best single candidate over generated tensors of 1e5-2e7 non-zeros,
+// 3-5 modes, ranks 8-64, both gather types: 11 % above the best per tensor on
+// average), and for large 3-mode tensors with FP32 gathers whose leaf factor
+// fits in shared memory the table kernel (on the 1e8-non-zero 3-mode
+// power-law tensor 12 % faster than the best global-memory walk).
+int default_variant(int32_t dtype, int32_t ld, int64_t leaf_rows, int64_t nnz, int nmodes) {
+    if (dtype == SPTT_F32 && nmodes == 3 && nnz >= kTableMinNnz && leaf_table_fits(leaf_rows, ld, 4)) return 14;
     return 13;
 }
 
@@ -368,7 +368,7 @@ bool leaf_table_fits(int64_t leaf_rows, int32_t ld, int esz) {
 }
 
 int default_order_kind(const int64_t *dims, int nmodes, int root, int32_t ld, int32_t dtype, int64_t nnz) {
-    if (dtype != SPTT_F32 || nmodes < 3 || nnz < kTableMinNnz) return 0;
+    if (dtype != SPTT_F32 || nmodes != 3 || nnz < kTableMinNnz) return 0;
     int64_t shortest = -1;
     for (int k = 0; k < nmodes; ++k)
         if (k != root && (shortest < 0 || dims[k] < shortest)) shortest = dims[k];
@@ -394,7 +394,7 @@ sptt_status mttkrp_launch(sptt_csf *csf, const void *const *factors, int32_t dty
     const int64_t nnz = csf->nfibs[N - 1];
     if (nnz == 0) return SPTT_OK;
     int variant = sched ? sched->variant : 0;
-    if (variant == 0) variant = default_variant(dtype, ld, csf->dims[csf->order[N - 1]], nnz);
+    if (variant == 0) variant = default_variant(dtype, ld, csf->dims[csf->order[N - 1]], nnz, N);
     // the table kernels need the whole leaf factor in shared memory
     if (table_variant(variant) && !leaf_table_fits(csf->dims[csf->order[N - 1]], ld, dtype == SPTT_BF16 ? 2 : 4))
         variant = 13;

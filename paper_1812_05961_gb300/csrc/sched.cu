@@ -360,7 +360,7 @@ extern "C" sptt_status sptt_sched_default(const int64_t *dims, int32_t nmodes, i
     s.order = default_order_kind(dims, nmodes, root, ld, factor_dtype, nnz);
     int32_t order[kMaxModes];
     level_order(dims, nmodes, root, s.order, order);
-    s.variant = default_variant(factor_dtype, ld, dims[order[nmodes - 1]], nnz);
+    s.variant = default_variant(factor_dtype, ld, dims[order[nmodes - 1]], nnz, nmodes);
     s.chunk = default_chunk(nnz);
     s.block = 256;
     *out = s;
