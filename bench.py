@@ -631,7 +631,8 @@ def sched_extra(args, dev):
     library's MLP kernels on autotuner sweeps of generated tensors; see
     paper_1812_05961_gb300/train_scheduler.py) against the library's fixed
     default rule, on held-out generated tensors of the same distribution
-    (other seeds) and on a 5-mode probe tensor; regret = time of the chosen
+    (other seeds: 1e5-2e7 and 2e7-2e8 non-zeros) and on a 5-mode probe
+    tensor; regret = time of the chosen
     schedule over the best one found by the exhaustive autotuner, minus 1."""
     import torch
 
@@ -645,15 +646,18 @@ def sched_extra(args, dev):
     model = train_scheduler.load()
     t0 = time.time()
     held = train_scheduler.sweep(train_scheduler.tensor_specs(args.sched_heldout, seed=77), dev)
+    held_large = train_scheduler.sweep(train_scheduler.tensor_specs(12, 79, nnz_max=2e8, nnz_min=2e7), dev)
     dims = [1_000_000, 1_000_000, 100_000, 10_000, 500]
     t = tensorgen.sample_unique(dims, 200_000_000, 5, dev, "zipf", s=1.1, values="uniform")
     probe = schedtrain.Dataset(schedtrain.sweep_tensor(t.dims, t.inds, t.vals, 32, reps=3, label="probe"))
     del t
     torch.cuda.empty_cache()
-    res = {"model": {k: meta.get(k) for k in ("tensors", "samples", "nnz_max", "steps", "loss_first_last")},
+    res = {"model": {k: meta.get(k) for k in ("tensors", "large", "large_nnz", "samples", "nnz_max", "steps",
+                                              "loss_first_last")},
            "heldout_tensors": args.sched_heldout, "heldout_samples": len(held.samples),
+           "heldout_large_tensors": 12, "heldout_large_samples": len(held_large.samples),
            "sweep_s": round(time.time() - t0, 1)}
-    for name, ds in (("heldout", held), ("probe_5mode_2e8_r32", probe)):
+    for name, ds in (("heldout", held), ("heldout_large_2e7_2e8", held_large), ("probe_5mode_2e8_r32", probe)):
         res[name] = {"learned": schedtrain.summarize(schedtrain.regret(ds, model)),
                      "default": schedtrain.summarize(schedtrain.regret(ds))}
     return res

@@ -161,8 +161,10 @@ sptt_status sptt_csf_copy_level(const sptt_csf *csf, int32_t level, int32_t *fpt
  *               shared memory once per CTA, 16-byte segments, one CTA of
  *               1024 threads in batches of 2 / 512 threads in batches of 4,
  *               used when that copy is at most 160 KB (else run as 13).
- *               Default: 13; with F32 gathers on a 3-mode tensor of at
- *               least 2^25 non-zeros whose leaf factor fits, 14. Variants 7 and 9..15
+ *               Default: on a 3-mode tensor of at least 2^25 non-zeros
+ *               whose leaf factor fits the table, 14 (F32 gathers) / 15
+ *               (BF16); else with F32 gathers on a tensor of at least 2^23
+ *               non-zeros and ld >= 16, ld % 8 == 0, 12; else 13. Variants 7 and 9..15
  *               (and so the default) read packed
  *               16-byte leaf records that the first call builds (16 bytes
  *               per non-zero on the device, kept with the CSF)
@@ -174,10 +176,10 @@ typedef struct {
     int32_t order;  /* CSF level order below the root for CP-ALS plans: 0 = ascending
                        length, 1 = descending, 2 = the shortest mode at the leaves and
                        the others ascending above it; ignored by sptt_mttkrp. CP-ALS
-                       without a schedule builds order 2 for FP32 gathers on a
-                       3-mode tensor of at least 2^25 non-zeros when the shortest mode's
-                       factor fits the shared-memory table of the default kernel
-                       (160 KB), else order 0 */
+                       without a schedule builds order 2 on a 3-mode tensor of at
+                       least 2^25 non-zeros when the shortest mode's factor (in the
+                       gather type) fits the shared-memory table of the default
+                       kernel (160 KB), else order 0 */
 } sptt_sched;
 
 /*
@@ -451,9 +453,9 @@ int32_t sptt_sched_candidates(int64_t nnz, sptt_sched *out, int32_t cap);
 
 /* The schedule the library uses for the root-`root` MTTKRP of a tensor of
  * nnz non-zeros with these mode lengths (host array), rank and gather type
- * when none is given: the level order CP-ALS builds (2 with F32 gathers on a
- * 3-mode tensor of at least 2^25 non-zeros when the shortest other mode's factor
- * fits the 160 KB shared-memory table, else 0), the default variant for that
+ * when none is given: the level order CP-ALS builds (2 on a 3-mode tensor of
+ * at least 2^25 non-zeros when the shortest other mode's factor, in the
+ * gather type, fits the 160 KB shared-memory table, else 0), the default variant for that
  * order's leaf mode and size, and the default chunk.
  * This is the fixed rule the learned scheduler is measured against. */
 sptt_status sptt_sched_default(const int64_t *dims, int32_t nmodes, int32_t root, int32_t rank,
@@ -525,7 +527,8 @@ typedef struct sptt_batch sptt_batch;
  * builds every tensor's CSF per mode, allocates factors and workspace, and
  * lays out global work lists (MTTKRP chunks and row tiles of all tensors back
  * to back). opts: seed (tensor t is initialised from seed + t), use_graph
- * (replay runs from a captured CUDA graph), sched (chunk size; the MTTKRP
+ * (replay runs from a captured CUDA graph), sched (chunk size, a power of
+ * two in [16, 4096], else SPTT_ERR_BAD_ARG; the MTTKRP
  * walk reads packed 16-byte leaf records, 16 bytes per non-zero more on the
  * device, and with the factor row width a multiple of 8 floats (rank 8, 16,
  * 32) gathers 32-byte row segments in a build of the kernel with one CTA per

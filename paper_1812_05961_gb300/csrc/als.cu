@@ -190,18 +190,20 @@ sptt_status run_iteration(sptt_cpd *c, bool bf16) {
         {
             Timed t(c, 2);
             // rows of mode n without a slice come out zero: clear A (and its
-            // BF16 copy) before the solve writes the rows that have one
-            SPTT_TRY(fill_zero_launch(c->A[n], (size_t)c->dims[n] * c->ld * sizeof(float), c->st));
-            if (c->Ab[n])
-                SPTT_TRY(fill_zero_launch(c->Ab[n], (size_t)c->dims[n] * c->ld * sizeof(__nv_bfloat16), c->st));
+            // BF16 copy) before the solve writes the rows that have one,
+            // unless every index of mode n has a slice
+            if (nrows < c->dims[n]) {
+                SPTT_TRY(fill_zero_launch(c->A[n], (size_t)c->dims[n] * c->ld * sizeof(float), c->st));
+                if (c->Ab[n])
+                    SPTT_TRY(fill_zero_launch(c->Ab[n], (size_t)c->dims[n] * c->ld * sizeof(__nv_bfloat16), c->st));
+            }
             const bool compact = L == 0 && !tiled;
             SPTT_TRY(postsolve_launch(Mres, compact ? c->Mh : nullptr, compact ? cs->hidx : nullptr, rowmap, c->A[n],
                                       nrows, &c->w, c->st));
         }
         {
             Timed t(c, 3);
-            SPTT_TRY(finalize_launch(c->G[n], &c->w, c->st));
-            SPTT_TRY(normalize_launch(c->A[n], c->Ab[n], rowmap, nrows, &c->w, c->st));
+            SPTT_TRY(finalize_normalize_launch(c->G[n], c->A[n], c->Ab[n], rowmap, nrows, &c->w, c->st));
         }
     }
     {

@@ -667,6 +667,8 @@ extern "C" sptt_status sptt_batch_create(const sptt_coo *coos, int32_t count, in
     if (b->opts.plan < 0 || b->opts.plan > 1) return set_error(SPTT_ERR_BAD_ARG, "batched opts.plan must be 0 or 1");
     const bool tune = b->opts.plan == 1;
     b->chunk = (sched && sched->chunk) ? sched->chunk : 128;
+    if (b->chunk < 16 || b->chunk > 4096 || (b->chunk & (b->chunk - 1)))
+        return set_error(SPTT_ERR_BAD_ARG, "sched->chunk must be a power of two in [16, 4096]");
     // the chunk sizes the layout may take (plan 1 times each of them)
     std::vector<int32_t> chunks = tune ? std::vector<int32_t>{64, 128, 256} : std::vector<int32_t>{b->chunk};
     b->csfs.assign((size_t)count * b->max_modes, nullptr);

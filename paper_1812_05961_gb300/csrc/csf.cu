@@ -455,6 +455,14 @@ __global__ void __launch_bounds__(kThreads) leafrec_kernel(const int32_t *__rest
     }
 }
 
+// The slack records after the last leaf: value 0, leaf row 0, and the level
+// flag N-1 (a leaf that opens no fiber), so a walk's last batch may run past
+// the end and add nothing.
+__global__ void leafrec_slack_kernel(uint4 *__restrict__ rec, int n, uint32_t flag) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) rec[k] = make_uint4(0u, 0u, 0u, flag);
+}
+
 // The leaf that starts level-LF fiber f carries that fiber's index.
 __global__ void leafrec_fiber_kernel(const int32_t *__restrict__ fptr, const int32_t *__restrict__ fids, int64_t nf,
                                      uint4 *__restrict__ rec) {
@@ -470,7 +478,9 @@ sptt_status csf_ensure_leafrec(sptt_csf *c, cudaStream_t st) {
     const int64_t nnz = c->nfibs[N - 1];
     SPTT_TRY(dev_alloc(reinterpret_cast<void **>(&c->leafrec),
                        (size_t)(nnz + kLeafSlack) * sizeof(uint4), st));
-    SPTT_TRY(fill_zero_launch(c->leafrec + nnz, (size_t)kLeafSlack * sizeof(uint4), st));
+    leafrec_slack_kernel<<<(kLeafSlack + kThreads - 1) / kThreads, kThreads, 0, st>>>(c->leafrec + nnz, kLeafSlack,
+                                                                                    (uint32_t)(N - 1));
+    SPTT_CHECK_LAUNCH("leafrec_slack_kernel");
     if (nnz > 0) {
         leafrec_kernel<<<grid_items(nnz), kThreads, 0, st>>>(c->fids[N - 1], c->vals, c->lvl, nnz, c->leafrec);
         SPTT_CHECK_LAUNCH("leafrec_kernel");

@@ -132,18 +132,24 @@ __global__ void __launch_bounds__(kThreads) normal_prep_kernel(GramPtrs g, int n
     dense::normal_prep_body(g, nmodes, n, rank, W, branch, sm);
 }
 
-// lambda_r = sqrt(Gun_rr); G_n = D^-1 Gun D^-1; inner = sum of column dots.
-__global__ void finalize_kernel(const double *__restrict__ gun, int rank, double *__restrict__ Gn,
-                                double *__restrict__ lambda, float *__restrict__ inv_lambda,
-                                double *__restrict__ inner) {
-    dense::finalize_body(gun, rank, Gn, lambda, inv_lambda, inner);
-}
-
-// Columns of A scaled by 1/lambda on the rows that hold a slice (the others
-// are zero already); padding columns zeroed; optional BF16 copy.
-__global__ void normalize_kernel(float *__restrict__ A, __nv_bfloat16 *__restrict__ Ab,
-                                 const int32_t *__restrict__ fids0, int64_t rows, int ld, int rank,
-                                 const float *__restrict__ inv_lambda) {
+// lambda_r = sqrt(Gun_rr); G_n = D^-1 Gun D^-1; inner = sum of column dots
+// (CTA 0), and every CTA scales its share of the rows of A by 1 / lambda
+// (with its BF16 copy): the column normalisation of Algorithm 1 in one
+// launch. Each CTA forms 1 / lambda from Gun itself, with the same FP64
+// expression as CTA 0, so every row sees the values stored in inv_lambda.
+__global__ void finalize_normalize_kernel(const double *__restrict__ gun, int rank, double *__restrict__ Gn,
+                                          double *__restrict__ lambda, float *__restrict__ inv_lambda,
+                                          double *__restrict__ inner, float *__restrict__ A,
+                                          __nv_bfloat16 *__restrict__ Ab, const int32_t *__restrict__ fids0,
+                                          int64_t rows, int ld) {
+    __shared__ float inv[SPTT_MAX_RANK_ALS];
+    if (blockIdx.x == 0) dense::finalize_body(gun, rank, Gn, lambda, inv_lambda, inner);
+    for (int t = threadIdx.x; t < rank; t += blockDim.x) {
+        const double d = gun[t * rank + t];
+        const double l = d > 0.0 ? sqrt(d) : 0.0;
+        inv[t] = (float)(l > 0.0 ? 1.0 / l : 0.0);
+    }
+    __syncthreads();
     const int qpr = ld / 4;  // float4 groups per row
     const int64_t total4 = rows * qpr;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total4;
@@ -154,7 +160,7 @@ __global__ void normalize_kernel(float *__restrict__ A, __nv_bfloat16 *__restric
         float4 v = reinterpret_cast<float4 *>(A)[q];
         float x[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-        for (int j = 0; j < 4; ++j) x[j] = (c0 + j < rank) ? x[j] * inv_lambda[c0 + j] : 0.f;
+        for (int j = 0; j < 4; ++j) x[j] = (c0 + j < rank) ? x[j] * inv[c0 + j] : 0.f;
         reinterpret_cast<float4 *>(A)[q] = make_float4(x[0], x[1], x[2], x[3]);
         if (Ab) {
             __nv_bfloat162 lo = __floats2bfloat162_rn(x[0], x[1]);
@@ -372,41 +378,41 @@ sptt_status normal_prep_launch(double *const *grams, int32_t nmodes, int32_t n, 
     return SPTT_OK;
 }
 
+// One CTA per tile of rows up to the workspace's CTA count: a mode with few
+// rows leaves no CTA idle that the partial reduction would then read.
 template <int RP>
-static void postsolve_dispatch(const float *M, const double *heavy, const int32_t *hidx, const int32_t *fids0,
-                               float *A, int64_t rows, DenseWork *w, int pstride, cudaStream_t st) {
-    postsolve_kernel<RP><<<w->nblocks, kThreads, sizeof(dense::SolveTile<RP>), st>>>(
+static int postsolve_dispatch(const float *M, const double *heavy, const int32_t *hidx, const int32_t *fids0,
+                              float *A, int64_t rows, DenseWork *w, int pstride, cudaStream_t st) {
+    const int64_t tiles = (rows + dense::SolveTile<RP>::TR - 1) / dense::SolveTile<RP>::TR;
+    const int nb = (int)(tiles < w->nblocks ? (tiles > 0 ? tiles : 1) : w->nblocks);
+    postsolve_kernel<RP><<<nb, kThreads, sizeof(dense::SolveTile<RP>), st>>>(
         M, heavy, hidx, fids0, A, rows, w->rank, w->ld, w->W, w->partials, pstride);
+    return nb;
 }
 
 sptt_status postsolve_launch(const float *M, const double *heavy, const int32_t *hidx, const int32_t *fids0,
                              float *A, int64_t rows, DenseWork *w, cudaStream_t st) {
     const int rank = w->rank;
     const int pstride = rank * rank + rank;
+    int nb = 0;
     switch (rank_pad(rank)) {
-        case 16: postsolve_dispatch<16>(M, heavy, hidx, fids0, A, rows, w, pstride, st); break;
-        case 32: postsolve_dispatch<32>(M, heavy, hidx, fids0, A, rows, w, pstride, st); break;
-        default: postsolve_dispatch<64>(M, heavy, hidx, fids0, A, rows, w, pstride, st); break;
+        case 16: nb = postsolve_dispatch<16>(M, heavy, hidx, fids0, A, rows, w, pstride, st); break;
+        case 32: nb = postsolve_dispatch<32>(M, heavy, hidx, fids0, A, rows, w, pstride, st); break;
+        default: nb = postsolve_dispatch<64>(M, heavy, hidx, fids0, A, rows, w, pstride, st); break;
     }
     SPTT_CHECK_LAUNCH("postsolve_kernel");
-    reduce_partials_kernel<<<(pstride + 31) / 32, dim3(32, kRedLanes), 0, st>>>(w->partials, w->nblocks, pstride,
+    reduce_partials_kernel<<<(pstride + 31) / 32, dim3(32, kRedLanes), 0, st>>>(w->partials, nb, pstride,
                                                                                pstride, w->gram_un);
     SPTT_CHECK_LAUNCH("reduce_partials_kernel");
     return SPTT_OK;
 }
 
-sptt_status finalize_launch(double *G_n, DenseWork *w, cudaStream_t st) {
-    finalize_kernel<<<1, kThreads, 0, st>>>(w->gram_un, w->rank, G_n, w->lambda, w->inv_lambda, w->inner);
-    SPTT_CHECK_LAUNCH("finalize_kernel");
-    return SPTT_OK;
-}
-
-sptt_status normalize_launch(float *A, __nv_bfloat16 *A_bf16, const int32_t *fids0, int64_t rows, DenseWork *w,
-                             cudaStream_t st) {
+sptt_status finalize_normalize_launch(double *G_n, float *A, __nv_bfloat16 *A_bf16, const int32_t *fids0,
+                                     int64_t rows, DenseWork *w, cudaStream_t st) {
     const int64_t q = rows * w->ld / 4;
-    if (q == 0) return SPTT_OK;
-    normalize_kernel<<<grid_cap(q), kThreads, 0, st>>>(A, A_bf16, fids0, rows, w->ld, w->rank, w->inv_lambda);
-    SPTT_CHECK_LAUNCH("normalize_kernel");
+    finalize_normalize_kernel<<<q > 0 ? grid_cap(q) : 1, kThreads, 0, st>>>(
+        w->gram_un, w->rank, G_n, w->lambda, w->inv_lambda, w->inner, A, A_bf16, fids0, rows, w->ld);
+    SPTT_CHECK_LAUNCH("finalize_normalize_kernel");
     return SPTT_OK;
 }
 

@@ -141,8 +141,8 @@ struct sptt_csf {
     // slot s; built for a row width whose slot capacity is hot_cap[l].
     // Packed leaf records of the flag walk (walk.cuh PackedRecs): per leaf
     // {leaf index, value bits, index of the level-(N-2) fiber it opens or 0,
-    // level flag}, with kLeafSlack zero records after the last; built on
-    // first use.
+    // level flag}, with kLeafSlack records {0, 0, 0, N-1} (value zero, opens
+    // nothing) after the last; built on first use.
     uint4 *leafrec = nullptr;
     int32_t *hslot[SPTT_MAX_MODES] = {nullptr};
     int32_t *hrow[SPTT_MAX_MODES] = {nullptr};
@@ -199,13 +199,21 @@ bool leaf_table_fits(int64_t leaf_rows, int32_t ld, int esz);
 // tuples of 3 or more indices, nearly one per leaf), putting the shortest mode
 // at the leaves multiplies the fibers more than the shared-memory table saves.
 constexpr int64_t kTableMinNnz = int64_t(1) << 25;
+// Smallest tensor for which the FP32 defaults take the 32-byte-segment walk
+// (variant 12) where the row width allows it (ld >= 16, ld % 8 == 0): on
+// smaller tensors the 16-byte walk in batches of 4 keeps more leaves in
+// flight per SM than the grid has chunks to spare.
+constexpr int64_t kWideMinNnz = int64_t(1) << 23;
 // The default MTTKRP variant for a gather type, row width, leaf-mode length,
-// size and mode count.
+// size and mode count: the table kernel (14 FP32, 15 BF16) for a 3-mode
+// tensor of at least kTableMinNnz non-zeros whose leaf factor fits, else 12
+// for FP32 gathers on a tensor of at least kWideMinNnz non-zeros with a row
+// width that allows it, else 13.
 int default_variant(int32_t dtype, int32_t ld, int64_t leaf_rows, int64_t nnz, int nmodes);
 // The default CSF level-order kind of the CSF rooted at `root` (see
-// level_order): with FP32 gathers on a 3-mode tensor of at least kTableMinNnz
-// non-zeros, 2 when the shortest other mode's factor fits the shared-memory
-// table, else 0.
+// level_order): on a 3-mode tensor of at least kTableMinNnz non-zeros, 2
+// when the shortest other mode's factor (in the gather type) fits the
+// shared-memory table, else 0.
 int default_order_kind(const int64_t *dims, int nmodes, int root, int32_t ld, int32_t dtype, int64_t nnz);
 
 // MTTKRP for the mode at level L >= 1 of the CSF (mttkrp_mode.cu): out is
@@ -258,11 +266,10 @@ sptt_status normal_prep_launch(double *const *grams, int32_t nmodes, int32_t n, 
 // Gram(A_un) and the column dots M.A_un into per-block partials, reduced.
 sptt_status postsolve_launch(const float *M, const double *heavy, const int32_t *hidx, const int32_t *fids0,
                              float *A, int64_t rows, DenseWork *w, cudaStream_t st);
-// lambda = sqrt(diag G_un); G_n = D^-1 G_un D^-1; inner = sum dots.
-sptt_status finalize_launch(double *G_n, DenseWork *w, cudaStream_t st);
+// lambda = sqrt(diag G_un); G_n = D^-1 G_un D^-1; inner = sum dots; and
 // A[fids0[f]] *= 1/lambda (columns) for f < rows, optional BF16 shadow.
-sptt_status normalize_launch(float *A, __nv_bfloat16 *A_bf16, const int32_t *fids0, int64_t rows,
-                             DenseWork *w, cudaStream_t st);
+sptt_status finalize_normalize_launch(double *G_n, float *A, __nv_bfloat16 *A_bf16, const int32_t *fids0,
+                                     int64_t rows, DenseWork *w, cudaStream_t st);
 // fit = 1 - sqrt(max(0, normx2 + lambda^T (*G) lambda - 2 inner)) / sqrt(normx2),
 // written to ring[*counter % ring_len], then ++*counter (device side).
 sptt_status fit_launch(double *const *grams, int32_t nmodes, const double *normx2, DenseWork *w,

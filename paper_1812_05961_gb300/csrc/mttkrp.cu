@@ -359,7 +359,9 @@ static bool staged_variant(int v) { return v == 6 || v == 8; }
 // fits in shared memory the table kernel (on the 1e8-non-zero 3-mode
 // power-law tensor 12 % faster than the best global-memory walk).
 int default_variant(int32_t dtype, int32_t ld, int64_t leaf_rows, int64_t nnz, int nmodes) {
-    if (dtype == SPTT_F32 && nmodes == 3 && nnz >= kTableMinNnz && leaf_table_fits(leaf_rows, ld, 4)) return 14;
+    const bool bf16 = dtype == SPTT_BF16;
+    if (nmodes == 3 && nnz >= kTableMinNnz && leaf_table_fits(leaf_rows, ld, bf16 ? 2 : 4)) return bf16 ? 15 : 14;
+    if (!bf16 && nnz >= kWideMinNnz && ld >= 16 && ld % 8 == 0) return 12;
     return 13;
 }
 
@@ -368,11 +370,11 @@ bool leaf_table_fits(int64_t leaf_rows, int32_t ld, int esz) {
 }
 
 int default_order_kind(const int64_t *dims, int nmodes, int root, int32_t ld, int32_t dtype, int64_t nnz) {
-    if (dtype != SPTT_F32 || nmodes != 3 || nnz < kTableMinNnz) return 0;
+    if (nmodes != 3 || nnz < kTableMinNnz) return 0;
     int64_t shortest = -1;
     for (int k = 0; k < nmodes; ++k)
         if (k != root && (shortest < 0 || dims[k] < shortest)) shortest = dims[k];
-    return leaf_table_fits(shortest, ld, 4) ? 2 : 0;
+    return leaf_table_fits(shortest, ld, dtype == SPTT_BF16 ? 2 : 4) ? 2 : 0;
 }
 
 // Variants that read the packed leaf records (sptt_csf::leafrec).

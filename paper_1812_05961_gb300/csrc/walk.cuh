@@ -108,6 +108,32 @@ struct Raw {
         }
         return r;
     }
+    // The same load issued only where p != 0; elsewhere the row is left
+    // undefined (callers select it only where p != 0), so a warp requests
+    // the sectors of its predicated-on lanes alone.
+    __device__ __forceinline__ static Row load_if(uint32_t p, const void *base, int64_t row, int ld, int col) {
+        const T *q = static_cast<const T *>(base) + row * ld + col;
+        Row r;
+        if constexpr (W == 16) {
+            asm("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %5, 0;\n\t"
+                "@p ld.global.nc.v4.u32 {%0, %1, %2, %3}, [%4];\n\t}"
+                : "=r"(r.w[0]), "=r"(r.w[1]), "=r"(r.w[2]), "=r"(r.w[3]) : "l"(q), "r"(p));
+        } else if constexpr (SPLIT) {
+            asm("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %9, 0;\n\t"
+                "@p ld.global.nc.v4.u32 {%0, %1, %2, %3}, [%8];\n\t"
+                "@p ld.global.nc.v4.u32 {%4, %5, %6, %7}, [%8+16];\n\t}"
+                : "=r"(r.w[0]), "=r"(r.w[1]), "=r"(r.w[2]), "=r"(r.w[3]),
+                  "=r"(r.w[4]), "=r"(r.w[5]), "=r"(r.w[6]), "=r"(r.w[7])
+                : "l"(q), "r"(p));
+        } else {
+            asm("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %9, 0;\n\t"
+                "@p ld.global.nc.v8.u32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n\t}"
+                : "=r"(r.w[0]), "=r"(r.w[1]), "=r"(r.w[2]), "=r"(r.w[3]),
+                  "=r"(r.w[4]), "=r"(r.w[5]), "=r"(r.w[6]), "=r"(r.w[7])
+                : "l"(q), "r"(p));
+        }
+        return r;
+    }
     __device__ __forceinline__ static void widen(const Row &u, float (&x)[VEC]) {
         if constexpr (sizeof(T) == 4) {
 #pragma unroll
@@ -619,6 +645,57 @@ __device__ __forceinline__ void flag_chunk(const Args &a, int64_t c, int col, Ca
 //
 // SPLIT: 32-byte loads issued as 16-byte halves (the batched kernel's
 // non-inlined walk; see Raw).
+// Records of the B leaves from k on for the select walk: leaf index, value,
+// the row index of the leaf-parent fiber a leaf opens (0 where it opens
+// none), and the level flags packed one per byte (bytes past B undefined).
+template <int B, bool SPLIT>
+__device__ __forceinline__ void fetch_sel(const uint4 *p, float (&v)[B], int32_t (&li)[B], int32_t (&nf)[B],
+                                          uint32_t (&lw)[(B + 3) / 4]) {
+    uint32_t fl[B];
+#pragma unroll
+    for (int h = 0; h < B; h += 2) {
+        uint32_t r[8];
+        load_rec_pair<SPLIT>(p + h, r);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            li[h + q] = (int32_t)r[4 * q];
+            v[h + q] = __uint_as_float(r[4 * q + 1]);
+            nf[h + q] = (int32_t)r[4 * q + 2];
+            fl[h + q] = r[4 * q + 3];
+        }
+    }
+#pragma unroll
+    for (int w = 0; w < (B + 3) / 4; ++w) {
+        const uint32_t lo = __byte_perm(fl[4 * w], fl[4 * w + 1], 0x3340u);
+        lw[w] = (B - 4 * w >= 4) ? __byte_perm(lo, __byte_perm(fl[4 * w + 2], fl[4 * w + 3], 0x3340u), 0x5410u)
+                                 : lo;
+    }
+}
+
+// The select walk: each leaf is added straight into the accumulator of the
+// level above its leaf-parent fiber, v * (row of the open leaf-parent fiber)
+// (.) (leaf row); a leaf that opens a new leaf-parent fiber swaps that row
+// (a select, so the per-leaf work has no branch). A batch in which a fiber
+// above the leaf parents closes (a slice change for N = 3) in some lane
+// group of the warp takes the general path, which tests every leaf and
+// folds the closing levels at the right one.
+//
+// The level flags d (the first tree level that changes at a leaf, 0..NM-1;
+// the zero-value slack records past the last leaf carry NM-1, "opens
+// nothing") are tested a byte at a time: with d <= 4, d + (0x80 - k) sets
+// bit 7 of its byte exactly when d >= k, with no carry between bytes.
+// Chunks are whole batches (a power-of-two chunk of at least 16 leaves), so
+// only the tensor's last batch reaches the slack, whose records add zero.
+// The rows of newly opened fibers are loaded only by the lanes that need
+// them (a predicated load), so a warp requests no sectors for the others.
+template <int B>
+__device__ __forceinline__ void opening_bits(const uint32_t (&lw)[(B + 3) / 4], uint32_t (&opn)[(B + 3) / 4],
+                                             uint32_t k_open) {
+#pragma unroll
+    for (int w = 0; w < (B + 3) / 4; ++w)
+        opn[w] = ~(lw[w] + k_open) & ((B - 4 * w >= 4) ? 0x80808080u : 0x00008080u);
+}
+
 template <int NM, typename T, int B, int W = 32, bool TAB = false, bool SPLIT = false>
 __device__ __forceinline__ void select_chunk(const Args &a, int64_t c, int col, Carry<Raw<T, W>::VEC> &cy,
                                              const PackedRecsT<SPLIT> &rec, uint32_t tab = 0,
@@ -630,10 +707,16 @@ __device__ __forceinline__ void select_chunk(const Args &a, int64_t c, int col, 
     constexpr int LF = NM - 2;             // level of the leaves' parent fibers
     constexpr int AL = LF >= 1 ? LF - 1 : 0;  // the level leaves add into
     constexpr int NACC = AL + 1;
+    constexpr int UP = LF >= 1 ? LF : 1;   // d < UP: a fiber above the leaf parents (or the slice) closes
+    constexpr int NW = (B + 3) / 4;
+    constexpr uint32_t kOpen = (0x80u - (uint32_t)(NM - 1)) * 0x01010101u;
+    constexpr uint32_t kUp = (0x80u - (uint32_t)UP) * 0x01010101u;
     static_assert(B == 2 || B == 4 || B == 8, "batch of 2, 4 or 8 leaves");
+    static_assert(NM <= 5, "level flags up to 4");
     const int ld = a.ld;
     const int64_t k0 = c * (int64_t)a.chunk;
-    const int64_t k1 = (k0 + a.chunk < a.nnz) ? k0 + a.chunk : a.nnz;
+    const int n = (int)(((k0 + a.chunk < a.nnz) ? k0 + a.chunk : a.nnz) - k0);
+    const uint4 *rp = rec.rec + k0;
     int32_t f[NL];
 #pragma unroll
     for (int l = 0; l < NL; ++l) f[l] = __ldg(a.part + c * NL + l);
@@ -652,14 +735,25 @@ __device__ __forceinline__ void select_chunk(const Args &a, int64_t c, int col, 
 
     float v[B];
     int32_t li[B];
-    uint32_t lw[2];
     int32_t nf[B];
-    fetch_all<B, LF>(rec, nullptr, 0, k0, v, li, lw, nf);
-    for (int64_t kb = k0; kb < k1; kb += B) {
+    uint32_t lw[NW];
+    fetch_sel<B, SPLIT>(rp, v, li, nf, lw);
+    uint32_t first = ~0x80u;  // the chunk's first leaf continues the fibers the partition gives
+    for (int o = 0; o < n; o += B) {
+        // bit 7 of byte j: leaf j opens a leaf-parent fiber (opn); rare: some
+        // leaf of the batch also closes a fiber above the leaf parents
+        uint32_t opn[NW];
+        opening_bits<B>(lw, opn, kOpen);
+        opn[0] &= first;
+        first = ~0u;
+        bool rare = false;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) rare |= (~(lw[w] + kUp) & opn[w]) != 0u;
         Row x[B], nr[B];
         if constexpr (LF >= 1) {
 #pragma unroll
-            for (int j = 0; j < B; ++j) nr[j] = Rw::load(a.fac[LF], nf[j], ld, col);
+            for (int j = 0; j < B; ++j)
+                nr[j] = Rw::load_if((opn[j >> 2] >> (8 * (j & 3) + 7)) & 1u, a.fac[LF], nf[j], ld, col);
         }
 #pragma unroll
         for (int j = 0; j < B; ++j) {
@@ -667,59 +761,70 @@ __device__ __forceinline__ void select_chunk(const Args &a, int64_t c, int col, 
             else x[j] = Rw::load(a.fac[NM - 1], li[j], ld, col);
         }
         // the next batch's records (past the chunk end they belong to the
-        // next chunk or to the zero slack; never used there)
+        // next chunk or to the slack; never used there)
         float vn[B];
         int32_t lin[B];
-        uint32_t lwn[2];
         int32_t nfn[B];
-        fetch_all<B, LF>(rec, nullptr, 0, kb + B, vn, lin, lwn, nfn);
-        const int nvalid = (k1 - kb < B) ? (int)(k1 - kb) : B;
-        // openings of a leaf-parent fiber (for N = 2: of a slice), as in flag_chunk
-        uint32_t sm = 0;
+        uint32_t lwn[NW];
+        fetch_sel<B, SPLIT>(rp + o + B, vn, lin, nfn, lwn);
+        // one path for the whole warp: the general path when any of its lane
+        // groups needs it, so the two never run one after the other
+        if (!__any_sync(__activemask(), rare)) {
 #pragma unroll
-        for (int w = 0; w < (B + 3) / 4; ++w) {
-            const uint32_t le = __vcmpleu4(lw[w], (uint32_t)LF * 0x01010101u) & 0x01010101u;
-            sm |= (((le * 0x01020408u) >> 24) & 0xfu) << (4 * w);
-        }
-        sm &= (1u << nvalid) - 1u;
-        if (kb == k0) sm &= ~1u;
+            for (int j = 0; j < B; ++j) {
+                const bool op = (opn[j >> 2] >> (8 * (j & 3) + 7)) & 1u;
+                float xr[VEC];
+                Rw::widen(x[j], xr);
+                if constexpr (LF >= 1) {
+                    float nw[VEC];
+                    Rw::widen(nr[j], nw);
 #pragma unroll
-        for (int j = 0; j < B; ++j) {
-            const bool op = (sm >> j) & 1u;
-            const int d = (int)((lw[j >> 2] >> (8 * (j & 3))) & 0xffu);
-            if (op && d < (LF >= 1 ? LF : 1)) {
-                // a fiber above the leaf parents closes: fold the levels
-                // that close into their parents, and store a finished slice
-#pragma unroll
-                for (int l = LF - 1; l >= 1; --l) {
-                    if (d <= l) {
-                        fold<T, W>(acc[l - 1], acc[l], rowc[l]);
-                        ++f[l];
-                        rowc[l] = Rw::load(a.fac[l], __ldg(a.fids[l] + f[l]), ld, col);
-                    }
-                }
-                if (d == 0) {
-                    if (first_slice) add_partial<VEC>(a, f[0], col, acc[0]);
-                    else store_owned<VEC>(a, f[0], col, acc[0]);
-                    first_slice = false;
-#pragma unroll
-                    for (int i = 0; i < VEC; ++i) acc[0][i] = 0.f;
-                    ++f[0];
+                    for (int i = 0; i < VEC; ++i) rf[i] = op ? nw[i] : rf[i];
+                    float t[VEC];
+                    mul_vec<VEC, W == 32>(t, rf, xr);
+                    fma_scalar<VEC, W == 32>(acc[AL], v[j], t);
+                } else {
+                    fma_scalar<VEC, W == 32>(acc[0], v[j], xr);
                 }
             }
-            float xr[VEC];
-            Rw::widen(x[j], xr);
-            const float vj = j < nvalid ? v[j] : 0.f;
-            if constexpr (LF >= 1) {
-                float nw[VEC];
-                Rw::widen(nr[j], nw);
+        } else {
 #pragma unroll
-                for (int i = 0; i < VEC; ++i) rf[i] = op ? nw[i] : rf[i];
-                float t[VEC];
-                mul_vec<VEC, W == 32>(t, rf, xr);
-                fma_scalar<VEC, W == 32>(acc[AL], vj, t);
-            } else {
-                fma_scalar<VEC, W == 32>(acc[0], vj, xr);
+            for (int j = 0; j < B; ++j) {
+                const bool op = (opn[j >> 2] >> (8 * (j & 3) + 7)) & 1u;
+                const int d = (int)((lw[j >> 2] >> (8 * (j & 3))) & 0xffu);
+                if (op && d < UP) {
+                    // a fiber above the leaf parents closes: fold the levels
+                    // that close into their parents, and store a finished slice
+#pragma unroll
+                    for (int l = LF - 1; l >= 1; --l) {
+                        if (d <= l) {
+                            fold<T, W>(acc[l - 1], acc[l], rowc[l]);
+                            ++f[l];
+                            rowc[l] = Rw::load(a.fac[l], __ldg(a.fids[l] + f[l]), ld, col);
+                        }
+                    }
+                    if (d == 0) {
+                        if (first_slice) add_partial<VEC>(a, f[0], col, acc[0]);
+                        else store_owned<VEC>(a, f[0], col, acc[0]);
+                        first_slice = false;
+#pragma unroll
+                        for (int i = 0; i < VEC; ++i) acc[0][i] = 0.f;
+                        ++f[0];
+                    }
+                }
+                float xr[VEC];
+                Rw::widen(x[j], xr);
+                if constexpr (LF >= 1) {
+                    float nw[VEC];
+                    Rw::widen(nr[j], nw);
+#pragma unroll
+                    for (int i = 0; i < VEC; ++i) rf[i] = op ? nw[i] : rf[i];
+                    float t[VEC];
+                    mul_vec<VEC, W == 32>(t, rf, xr);
+                    fma_scalar<VEC, W == 32>(acc[AL], v[j], t);
+                } else {
+                    fma_scalar<VEC, W == 32>(acc[0], v[j], xr);
+                }
             }
         }
 #pragma unroll
@@ -728,8 +833,8 @@ __device__ __forceinline__ void select_chunk(const Args &a, int64_t c, int col, 
             li[q] = lin[q];
             nf[q] = nfn[q];
         }
-        lw[0] = lwn[0];
-        lw[1] = lwn[1];
+#pragma unroll
+        for (int w = 0; w < NW; ++w) lw[w] = lwn[w];
     }
     // chunk end: fold the open upper fibers; the open slice's partial is
     // added (or held back when the slice is heavy)

@@ -30,6 +30,8 @@ class Sample:
     label: str = ""
     rank: int = 16
     dtype: int = SPTT_F32
+    dims: List[int] = field(default_factory=list)
+    nnz: int = 0
 
 
 @dataclass
@@ -68,7 +70,7 @@ def sweep_tensor(dims, inds, vals, rank: int, dtypes: Sequence[int] = (SPTT_F32,
             ms = sptt_autotune(dims, inds, vals, root, rank, dtype, reps)
             out.append(Sample(feats, ms, default_index(dims, root, rank, dtype, nnz),
                               "%s root %d R %d %s" % (label, root, rank, "bf16" if dtype == SPTT_BF16 else "f32"),
-                              rank, dtype))
+                              rank, dtype, [int(x) for x in dims], nnz))
     return out
 
 

@@ -1,16 +1,21 @@
 """Train the learned MTTKRP scheduler and write the model the package ships.
 
-    python -m paper_1812_05961_gb300.train_scheduler [--tensors 2000] [--nnz-max 2e7] [--out FILE]
+    python -m paper_1812_05961_gb300.train_scheduler [--tensors 2000] [--nnz-max 2e7]
+        [--large 200] [--large-nnz 2e7 2e8] [--samples FILE ...] [--out FILE]
 
 Steps, all on the GPU through the library: generate seeded synthetic tensors
 (3-5 modes, mode lengths log-uniform in [1e2, 1e7], nnz log-uniform in
 [1e5, nnz-max] capped at a quarter of the index space, Zipf exponent
-U(0.8, 1.5) per tensor, rank drawn from {8, 16, 32, 64}); time every
+U(0.8, 1.5) per tensor, rank drawn from {8, 16, 32, 64}), plus a second set
+of `--large` tensors drawn the same way with nnz log-uniform in the
+`--large-nnz` range (seed + 1); time every
 candidate schedule of every root mode under both gather types with the
 exhaustive autotuner (sptt_autotune); fit the MLP to log2(time / best time)
-with the library's training kernels (sptt_mlp_train); write the parameters
+with the library's training kernels (sptt_mlp_train), each sample of the
+larger set counted `--large-weight` times; write the parameters
 and the feature standardisation to a JSON file (default: sched_model.json
-next to this file), which default_scheduler() loads.
+next to this file), which default_scheduler() loads. `--samples` reads
+timed samples written earlier by `--dump` in place of sweeping again.
 """
 from __future__ import annotations
 
@@ -65,6 +70,20 @@ def sweep(specs, device, log=None):
     return ds
 
 
+def dump(ds, path: str):
+    with open(path, "w") as f:
+        json.dump([{"features": x.features, "times_ms": x.times_ms, "default": x.default, "label": x.label,
+                    "rank": x.rank, "dtype": x.dtype, "dims": x.dims, "nnz": x.nnz} for x in ds.samples], f)
+
+
+def read_samples(path: str):
+    from . import schedtrain
+    with open(path) as f:
+        rows = json.load(f)
+    return [schedtrain.Sample(r["features"], r["times_ms"], r["default"], r.get("label", ""), r.get("rank", 16),
+                              r.get("dtype", 0), r.get("dims", []), r.get("nnz", 0)) for r in rows]
+
+
 def save(model, path: str, meta: dict):
     from . import sptt_mlp_get
     P, mu, sd = sptt_mlp_get(model.handle)
@@ -90,8 +109,14 @@ def main(argv=None):
     p = argparse.ArgumentParser()
     p.add_argument("--tensors", type=int, default=2000)
     p.add_argument("--nnz-max", type=float, default=2e7)
+    p.add_argument("--large", type=int, default=200, help="tensors of the second, larger set")
+    p.add_argument("--large-nnz", type=float, nargs=2, default=(2e7, 2e8), metavar=("MIN", "MAX"))
+    p.add_argument("--large-weight", type=int, default=4,
+                   help="each sample of a tensor above --nnz-max counts this many times in the loss (4 gives "
+                        "the larger tensors about the share they have when nnz is log-uniform in [1e5, 2e8])")
+    p.add_argument("--samples", nargs="*", default=None, help="timed samples (--dump files) to train on instead")
     p.add_argument("--seed", type=int, default=21)
-    p.add_argument("--steps", type=int, default=4000)
+    p.add_argument("--steps", type=int, default=6000)
     p.add_argument("--lr", type=float, default=3e-3)
     p.add_argument("--out", default=MODEL)
     p.add_argument("--dump", default=None, help="also write the timed samples to this JSON file")
@@ -100,16 +125,22 @@ def main(argv=None):
 
     from . import schedtrain
     dev = torch.device("cuda")
-    specs = tensor_specs(a.tensors, a.seed, a.nnz_max)
-    ds = sweep(specs, dev, log=lambda s: print(s, flush=True))
+    if a.samples:
+        ds = schedtrain.Dataset([x for path in a.samples for x in read_samples(path)])
+    else:
+        specs = tensor_specs(a.tensors, a.seed, a.nnz_max)
+        if a.large > 0:
+            specs += tensor_specs(a.large, a.seed + 1, a.large_nnz[1], a.large_nnz[0])
+        ds = sweep(specs, dev, log=lambda s: print(s, flush=True))
     if a.dump:
-        with open(a.dump, "w") as f:
-            json.dump([{"features": x.features, "times_ms": x.times_ms, "default": x.default, "label": x.label,
-                        "rank": x.rank, "dtype": x.dtype} for x in ds.samples], f)
-    model, hist = schedtrain.train(ds, steps=a.steps, lr=a.lr)
+        dump(ds, a.dump)
+    fit_ds = schedtrain.Dataset(ds.samples + [x for x in ds.samples if x.nnz > a.nnz_max] * (a.large_weight - 1))
+    model, hist = schedtrain.train(fit_ds, steps=a.steps, lr=a.lr)
     r_model = schedtrain.summarize(schedtrain.regret(ds, model))
     r_default = schedtrain.summarize(schedtrain.regret(ds))
-    meta = {"tensors": a.tensors, "samples": len(ds.samples), "nnz_max": a.nnz_max, "seed": a.seed,
+    meta = {"tensors": a.tensors, "large": a.large, "large_nnz": list(a.large_nnz), "large_weight": a.large_weight,
+            "samples": len(ds.samples),
+            "nnz_max": a.nnz_max, "seed": a.seed,
             "steps": a.steps, "lr": a.lr, "loss_first_last": [float(hist[0]), float(hist[-1])],
             "train_regret_learned": r_model, "train_regret_default": r_default}
     save(model, a.out, meta)

@@ -113,7 +113,8 @@ def test_training_on_sweeps_fits_the_timings(cuda_device):
 
 def test_shipped_scheduler_gains_over_the_fixed_default_on_held_out(cuda_device):
     # the model the package ships (trained by train_scheduler.py on the
-    # autotuner's timings of 2,000 generated tensors) against the library's
+    # autotuner's timings of 2,000 generated tensors of 1e5-2e7 non-zeros and
+    # 200 of 2e7-2e8) against the library's
     # fixed default rule, on tensors of the same distribution it never saw
     # (another seed), timed now by the exhaustive autotuner
     from paper_1812_05961_gb300 import train_scheduler
@@ -123,4 +124,17 @@ def test_shipped_scheduler_gains_over_the_fixed_default_on_held_out(cuda_device)
     r_default = schedtrain.summarize(schedtrain.regret(held))
     print("held-out regret: learned %s, default %s" % (r_model, r_default))
     assert r_model["mean"] <= GAIN_FACTOR * r_default["mean"], (r_model, r_default)
+    assert r_model["mean"] <= GAIN_ABS, (r_model, r_default)
+
+
+def test_shipped_scheduler_gains_on_held_out_large_tensors(cuda_device):
+    # the same against held-out tensors of 2e7-2e8 non-zeros (3-5 modes),
+    # the range of the second training set
+    from paper_1812_05961_gb300 import train_scheduler
+    model = train_scheduler.load()
+    held = train_scheduler.sweep(train_scheduler.tensor_specs(24, seed=4343, nnz_max=2e8, nnz_min=2e7), cuda_device)
+    r_model = schedtrain.summarize(schedtrain.regret(held, model))
+    r_default = schedtrain.summarize(schedtrain.regret(held))
+    print("held-out regret (2e7-2e8 non-zeros): learned %s, default %s" % (r_model, r_default))
+    assert r_model["mean"] < r_default["mean"], (r_model, r_default)
     assert r_model["mean"] <= GAIN_ABS, (r_model, r_default)
