@@ -271,11 +271,13 @@ def every_gather_model(csf, R, s_f=4):
 # the leaf-record stream, so it is scaled to other sizes by the number of
 # non-zeros.
 NCU_TRAFFIC = {"kernel": "mttkrp_table_kernel<3, float, 2, 1024, 16> (roots 0, 1), "
-                         "mttkrp_select_kernel<3, float, 4, 2, 16> (root 2)",
-               "nnz": 34_000_000, "bytes": [685.780480e6, 801.106176e6, 685.219840e6]}
-# The same for the default BF16-gather kernel (variant 13 at every root).
-NCU_TRAFFIC_BF16 = {"kernel": "mttkrp_select_kernel<3, __nv_bfloat16, 4, 2, 16>", "nnz": 34_000_000,
-                    "bytes": [643.358976e6, 643.095296e6, 640.092160e6]}
+                         "mttkrp_select_kernel<3, float, 2, 2, 32> (root 2)",
+               "nnz": 34_000_000, "bytes": [656.884224e6, 763.970816e6, 741.069568e6]}
+# The same for the default BF16-gather kernels (the same rule: the BF16 table
+# kernel at roots 0 and 1, variant 13 at root 2).
+NCU_TRAFFIC_BF16 = {"kernel": "mttkrp_table_kernel<3, __nv_bfloat16, 4, 512, 16> (roots 0, 1), "
+                              "mttkrp_select_kernel<3, __nv_bfloat16, 4, 2, 16> (root 2)",
+                    "nnz": 34_000_000, "bytes": [648.861952e6, 663.849728e6, 639.768832e6]}
 
 
 def fp32_peak_tflops(dev, sm_mhz=None):
@@ -743,8 +745,8 @@ def ours(args, rank, world, local):
     # measured traffic applies while the timed kernel is the captured one
     traffic = None
     ncu = NCU_TRAFFIC_BF16 if bf16 else NCU_TRAFFIC
-    # (the FP32 capture is of the kernels the default rule picks from 2^25 non-zeros on)
-    if sched is None and R in (16,) and len(dims) == 3 and ncu is not None and (bf16 or nnz >= 2 ** 25):
+    # (the captures are of the kernels the default rule picks from 2^25 non-zeros on)
+    if sched is None and R in (16,) and len(dims) == 3 and ncu is not None and nnz >= 2 ** 25:
         traffic = sum(ncu["bytes"]) / 3 * nnz / ncu["nnz"]
     flops_s = sum(flops_per) * args.steps / (mttkrp_ms * 1e-3) / 1e12
     fp32_peak, n_sms, peak_mhz = fp32_peak_tflops(dev)
