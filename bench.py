@@ -272,12 +272,12 @@ def every_gather_model(csf, R, s_f=4):
 # non-zeros.
 NCU_TRAFFIC = {"kernel": "mttkrp_table_kernel<3, float, 2, 1024, 16> (roots 0, 1), "
                          "mttkrp_select_kernel<3, float, 2, 2, 32> (root 2)",
-               "nnz": 34_000_000, "bytes": [656.884224e6, 763.970816e6, 741.069568e6]}
+               "nnz": 34_000_000, "bytes": [657.552896e6, 764.358144e6, 740.582912e6]}
 # The same for the default BF16-gather kernels (the same rule: the BF16 table
 # kernel at roots 0 and 1, variant 13 at root 2).
 NCU_TRAFFIC_BF16 = {"kernel": "mttkrp_table_kernel<3, __nv_bfloat16, 4, 512, 16> (roots 0, 1), "
                               "mttkrp_select_kernel<3, __nv_bfloat16, 4, 2, 16> (root 2)",
-                    "nnz": 34_000_000, "bytes": [648.861952e6, 663.849728e6, 639.768832e6]}
+                    "nnz": 34_000_000, "bytes": [648.869632e6, 664.093696e6, 639.894784e6]}
 
 
 def fp32_peak_tflops(dev, sm_mhz=None):
