@@ -20,9 +20,10 @@ constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kSortItems = 16;
 constexpr int kSortTile = kSortThreads * kSortItems;  // 4096
 constexpr int kWarpSpan = 32 * kSortItems;            // 512 keys per warp
-constexpr int kRadixBits = 8;
-constexpr int kRadix = 1 << kRadixBits;
-static_assert(kRadix == kSortThreads, "one thread per digit in the scatter kernel");
+// Digits of 8 or 9 bits (RB): a key of nbits bits takes ceil(nbits / RB)
+// passes, and 9-bit digits save a pass where that count drops (45-bit keys:
+// 5 passes instead of 6). Each thread owns RB - 7 digits of a tile's table.
+constexpr int kMaxRadix = 1 << 9;
 
 __device__ __forceinline__ int pad_idx(int i) { return i + (i >> 5); }
 
@@ -154,12 +155,14 @@ __global__ void __launch_bounds__(kScanThreads) scan_down_kernel(const In in,  /
 // ---------------------------------------------------------------------------
 // Radix sort
 // ---------------------------------------------------------------------------
+template <int RB>
 __global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(const uint64_t *__restrict__ keys,
                                                                   int64_t n, int shift, int64_t ntiles,
                                                                   int32_t *__restrict__ counts) {
-    __shared__ int hist[kSortWarps][kRadix];
+    constexpr int R = 1 << RB;
+    __shared__ int hist[kSortWarps][R];
     const int warp = threadIdx.x >> 5;
-    for (int i = threadIdx.x; i < kSortWarps * kRadix; i += kSortThreads) (&hist[0][0])[i] = 0;
+    for (int i = threadIdx.x; i < kSortWarps * R; i += kSortThreads) (&hist[0][0])[i] = 0;
     __syncthreads();
     const int64_t base = (int64_t)blockIdx.x * kSortTile;
     // all of the thread's keys are requested before the first is counted
@@ -172,32 +175,38 @@ __global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(const uint64_t
 #pragma unroll
     for (int j = 0; j < kSortItems; ++j) {
         const int64_t i = base + j * kSortThreads + threadIdx.x;
-        if (i < n) atomicAdd(&hist[warp][(int)((k[j] >> shift) & (kRadix - 1))], 1);
+        if (i < n) atomicAdd(&hist[warp][(int)((k[j] >> shift) & (R - 1))], 1);
     }
     __syncthreads();
-    int d = threadIdx.x;
-    int s = 0;
+    for (int d = threadIdx.x; d < R; d += kSortThreads) {
+        int s = 0;
 #pragma unroll
-    for (int w = 0; w < kSortWarps; ++w) s += hist[w][d];
-    counts[(int64_t)d * ntiles + blockIdx.x] = s;
+        for (int w = 0; w < kSortWarps; ++w) s += hist[w][d];
+        counts[(int64_t)d * ntiles + blockIdx.x] = s;
+    }
 }
 
+template <int RB>
 struct ScatterSmem {
-    int whist[kSortWarps][kRadix];
-    int tile_start[kRadix];
+    int whist[kSortWarps][1 << RB];
+    int tile_start[1 << RB];
     uint64_t keys[kSortTile];
     uint32_t vals[kSortTile];
 };
 
+template <int RB>
 __global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(
     const uint64_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
     uint64_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out, int64_t n, int shift,
     int64_t ntiles, const int32_t *__restrict__ offsets) {
+    constexpr int R = 1 << RB;
+    constexpr int DPT = R / kSortThreads;  // digits per thread in the tile's offset scan
+    static_assert(DPT * kSortThreads == R, "whole digits per thread");
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    ScatterSmem &sm = *reinterpret_cast<ScatterSmem *>(smem_raw);
+    ScatterSmem<RB> &sm = *reinterpret_cast<ScatterSmem<RB> *>(smem_raw);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned lt_mask = (1u << lane) - 1u;
-    for (int i = threadIdx.x; i < kSortWarps * kRadix; i += kSortThreads) (&sm.whist[0][0])[i] = 0;
+    for (int i = threadIdx.x; i < kSortWarps * R; i += kSortThreads) (&sm.whist[0][0])[i] = 0;
     __syncthreads();
 
     const int64_t base = (int64_t)blockIdx.x * kSortTile;
@@ -214,7 +223,7 @@ __global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(
         const bool valid = li < tile_n;
         k[j] = valid ? keys_in[base + li] : 0ull;
         v[j] = valid ? vals_in[base + li] : 0u;
-        dg[j] = (int)((k[j] >> shift) & (kRadix - 1));
+        dg[j] = (int)((k[j] >> shift) & (R - 1));
     }
     // Stable rank of every key within its warp's span, in (j, lane) order.
 #pragma unroll
@@ -235,18 +244,31 @@ __global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(
         loc[j] = old + r;
     }
     __syncthreads();
-    // Per digit: exclusive offsets of the warps, then of the digits in the tile.
+    // Per digit: exclusive offsets of the warps, then of the digits in the
+    // tile (thread t owns digits t * DPT .. t * DPT + DPT - 1).
     {
-        const int d = threadIdx.x;
-        int run = 0;
+        int run[DPT];
+        int sum = 0;
 #pragma unroll
-        for (int w = 0; w < kSortWarps; ++w) {
-            int c = sm.whist[w][d];
-            sm.whist[w][d] = run;
-            run += c;
+        for (int q = 0; q < DPT; ++q) {
+            const int d = threadIdx.x * DPT + q;
+            int r = 0;
+#pragma unroll
+            for (int w = 0; w < kSortWarps; ++w) {
+                const int c = sm.whist[w][d];
+                sm.whist[w][d] = r;
+                r += c;
+            }
+            run[q] = r;
+            sum += r;
         }
         int tot;
-        sm.tile_start[d] = block_exclusive_scan<kSortThreads>(run, tot);
+        int start = block_exclusive_scan<kSortThreads>(sum, tot);
+#pragma unroll
+        for (int q = 0; q < DPT; ++q) {
+            sm.tile_start[threadIdx.x * DPT + q] = start;
+            start += run[q];
+        }
     }
     __syncthreads();
 #pragma unroll
@@ -261,7 +283,7 @@ __global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(
     __syncthreads();
     for (int p = threadIdx.x; p < tile_n; p += kSortThreads) {
         const uint64_t key = sm.keys[p];
-        const int d = (int)((key >> shift) & (kRadix - 1));
+        const int d = (int)((key >> shift) & (R - 1));
         const int64_t g = (int64_t)offsets[(int64_t)d * ntiles + blockIdx.x] + (p - sm.tile_start[d]);
         keys_out[g] = key;
         vals_out[g] = sm.vals[p];
@@ -298,22 +320,19 @@ sptt_status scan_exclusive_level(const uint8_t *d, int level, int32_t *out, int6
     return scan_exclusive(InLevelLE{d, level}, out, n, with_total, st);
 }
 
-sptt_status radix_sort_pairs(uint64_t *&keys, uint32_t *&vals, uint64_t *&keys_alt,
-                             uint32_t *&vals_alt, int64_t n, int nbits, cudaStream_t st) {
-    if (n <= 1 || nbits <= 0) return SPTT_OK;
-    const int64_t ntiles = (n + kSortTile - 1) / kSortTile;
-    DevBuf counts;
-    SPTT_TRY(counts.alloc<int32_t>((size_t)kRadix * ntiles + 1, st));
-    SPTT_CUDA(cudaFuncSetAttribute(radix_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)sizeof(ScatterSmem)));
-    for (int shift = 0; shift < nbits; shift += kRadixBits) {
-        radix_hist_kernel<<<(unsigned)ntiles, kSortThreads, 0, st>>>(keys, n, shift, ntiles,
-                                                                      counts.as<int32_t>());
+namespace {
+
+template <int RB>
+sptt_status radix_sort_passes(uint64_t *&keys, uint32_t *&vals, uint64_t *&keys_alt, uint32_t *&vals_alt,
+                              int64_t n, int nbits, int64_t ntiles, int32_t *counts, cudaStream_t st) {
+    SPTT_CUDA(cudaFuncSetAttribute(radix_scatter_kernel<RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)sizeof(ScatterSmem<RB>)));
+    for (int shift = 0; shift < nbits; shift += RB) {
+        radix_hist_kernel<RB><<<(unsigned)ntiles, kSortThreads, 0, st>>>(keys, n, shift, ntiles, counts);
         SPTT_CHECK_LAUNCH("radix_hist_kernel");
-        SPTT_TRY(scan_exclusive_i32(counts.as<int32_t>(), counts.as<int32_t>(), (int64_t)kRadix * ntiles,
-                                    false, st));
-        radix_scatter_kernel<<<(unsigned)ntiles, kSortThreads, sizeof(ScatterSmem), st>>>(
-            keys, vals, keys_alt, vals_alt, n, shift, ntiles, counts.as<int32_t>());
+        SPTT_TRY(scan_exclusive_i32(counts, counts, (int64_t)(1 << RB) * ntiles, false, st));
+        radix_scatter_kernel<RB><<<(unsigned)ntiles, kSortThreads, sizeof(ScatterSmem<RB>), st>>>(
+            keys, vals, keys_alt, vals_alt, n, shift, ntiles, counts);
         SPTT_CHECK_LAUNCH("radix_scatter_kernel");
         uint64_t *tk = keys;
         keys = keys_alt;
@@ -323,6 +342,20 @@ sptt_status radix_sort_pairs(uint64_t *&keys, uint32_t *&vals, uint64_t *&keys_a
         vals_alt = tv;
     }
     return SPTT_OK;
+}
+
+}  // namespace
+
+sptt_status radix_sort_pairs(uint64_t *&keys, uint32_t *&vals, uint64_t *&keys_alt,
+                             uint32_t *&vals_alt, int64_t n, int nbits, cudaStream_t st) {
+    if (n <= 1 || nbits <= 0) return SPTT_OK;
+    const int64_t ntiles = (n + kSortTile - 1) / kSortTile;
+    DevBuf counts;
+    SPTT_TRY(counts.alloc<int32_t>((size_t)kMaxRadix * ntiles + 1, st));
+    // 9-bit digits where they need fewer passes than 8-bit ones
+    if ((nbits + 8) / 9 < (nbits + 7) / 8)
+        return radix_sort_passes<9>(keys, vals, keys_alt, vals_alt, n, nbits, ntiles, counts.as<int32_t>(), st);
+    return radix_sort_passes<8>(keys, vals, keys_alt, vals_alt, n, nbits, ntiles, counts.as<int32_t>(), st);
 }
 
 }  // namespace sptt

@@ -162,3 +162,12 @@ def test_batched_rejects_unsupported(cuda_device):
     with pytest.raises(sptt.SpttError) as e:
         sptt.Batch([(x.dims, [i.cuda() for i in x.inds], x.vals.cuda())], 8)
     assert e.value.status == sptt.SPTT_ERR_UNSUPPORTED
+
+
+def test_batched_rejects_a_chunk_that_is_not_a_power_of_two(cuda_device):
+    # the walk's batches tile a chunk exactly: power-of-two chunks of at least 16 leaves
+    items = _batch(2, seed=3)
+    for chunk in (100, 8, 8192):
+        with pytest.raises(sptt.SpttError) as e:
+            sptt.Batch([(d, i, v) for d, i, v, _ in items], 8, sched=(chunk, 256, 4, 0))
+        assert e.value.status == sptt.SPTT_ERR_BAD_ARG, chunk
