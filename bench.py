@@ -654,7 +654,7 @@ def sched_extra(args, dev):
     probe = schedtrain.Dataset(schedtrain.sweep_tensor(t.dims, t.inds, t.vals, 32, reps=3, label="probe"))
     del t
     torch.cuda.empty_cache()
-    res = {"model": {k: meta.get(k) for k in ("tensors", "large", "large_nnz", "samples", "nnz_max", "steps",
+    res = {"model": {k: meta.get(k) for k in ("tensors", "strata", "nnz_range", "split", "samples", "steps",
                                               "loss_first_last")},
            "heldout_tensors": args.sched_heldout, "heldout_samples": len(held.samples),
            "heldout_large_tensors": 12, "heldout_large_samples": len(held_large.samples),

@@ -1,21 +1,24 @@
 """Train the learned MTTKRP scheduler and write the model the package ships.
 
-    python -m paper_1812_05961_gb300.train_scheduler [--tensors 2000] [--nnz-max 2e7]
-        [--large 200] [--large-nnz 2e7 2e8] [--samples FILE ...] [--out FILE]
+    python -m paper_1812_05961_gb300.train_scheduler [--tensors 2000] [--nnz-range 1e5 2e8]
+        [--split 2e7] [--samples FILE ...] [--out FILE]
 
 Steps, all on the GPU through the library: generate seeded synthetic tensors
-(3-5 modes, mode lengths log-uniform in [1e2, 1e7], nnz log-uniform in
-[1e5, nnz-max] capped at a quarter of the index space, Zipf exponent
-U(0.8, 1.5) per tensor, rank drawn from {8, 16, 32, 64}), plus a second set
-of `--large` tensors drawn the same way with nnz log-uniform in the
-`--large-nnz` range (seed + 1); time every
+(3-5 modes, mode lengths log-uniform in [1e2, 1e7], nnz log-uniform in the
+`--nnz-range` capped at a quarter of the index space, Zipf exponent
+U(0.8, 1.5) per tensor, rank drawn from {8, 16, 32, 64}); time every
 candidate schedule of every root mode under both gather types with the
 exhaustive autotuner (sptt_autotune); fit the MLP to log2(time / best time)
-with the library's training kernels (sptt_mlp_train), each sample of the
-larger set counted `--large-weight` times; write the parameters
+with the library's training kernels (sptt_mlp_train); write the parameters
 and the feature standardisation to a JSON file (default: sched_model.json
 next to this file), which default_scheduler() loads. `--samples` reads
 timed samples written earlier by `--dump` in place of sweeping again.
+
+The tensors are drawn in two strata of the log-uniform law, below and above
+`--split` (seeds `--seed` and `--seed` + 1), in the proportion the law gives
+them (for [1e5, 2e8] split at 2e7: 1,394 and 606 of 2,000), so that a set can
+be extended on either side without redrawing the other. tensor_specs(n, seed,
+...) draws tensor k identically whatever n is.
 """
 from __future__ import annotations
 
@@ -44,6 +47,18 @@ def tensor_specs(n: int, seed: int, nnz_max: float = 2e7, nnz_min: float = 1e5):
         R = int(g.choice([8, 16, 32, 64]))
         out.append((dims, max(nnz, 1000), s, R, seed * 100000 + i))
     return out
+
+
+def strata(n: int, lo: float, hi: float, split: float):
+    """Tensors below and above split of n drawn log-uniform in [lo, hi]."""
+    below = int(round(n * math.log(split / lo) / math.log(hi / lo))) if lo < split < hi else (n if split >= hi else 0)
+    return below, n - below
+
+
+def specs_for(n: int, seed: int, lo: float = 1e5, hi: float = 2e8, split: float = 2e7):
+    """The stratified draw of n tensors: specs below split (seed), then above (seed + 1)."""
+    below, above = strata(n, lo, hi, split)
+    return tensor_specs(below, seed, min(split, hi), lo) + tensor_specs(above, seed + 1, hi, max(split, lo))
 
 
 def sweep(specs, device, log=None):
@@ -108,12 +123,8 @@ def load(path: str = MODEL):
 def main(argv=None):
     p = argparse.ArgumentParser()
     p.add_argument("--tensors", type=int, default=2000)
-    p.add_argument("--nnz-max", type=float, default=2e7)
-    p.add_argument("--large", type=int, default=200, help="tensors of the second, larger set")
-    p.add_argument("--large-nnz", type=float, nargs=2, default=(2e7, 2e8), metavar=("MIN", "MAX"))
-    p.add_argument("--large-weight", type=int, default=4,
-                   help="each sample of a tensor above --nnz-max counts this many times in the loss (4 gives "
-                        "the larger tensors about the share they have when nnz is log-uniform in [1e5, 2e8])")
+    p.add_argument("--nnz-range", type=float, nargs=2, default=(1e5, 2e8), metavar=("MIN", "MAX"))
+    p.add_argument("--split", type=float, default=2e7, help="stratum boundary of the nnz draw")
     p.add_argument("--samples", nargs="*", default=None, help="timed samples (--dump files) to train on instead")
     p.add_argument("--seed", type=int, default=21)
     p.add_argument("--steps", type=int, default=6000)
@@ -125,23 +136,19 @@ def main(argv=None):
 
     from . import schedtrain
     dev = torch.device("cuda")
+    lo, hi = a.nnz_range
     if a.samples:
         ds = schedtrain.Dataset([x for path in a.samples for x in read_samples(path)])
     else:
-        specs = tensor_specs(a.tensors, a.seed, a.nnz_max)
-        if a.large > 0:
-            specs += tensor_specs(a.large, a.seed + 1, a.large_nnz[1], a.large_nnz[0])
-        ds = sweep(specs, dev, log=lambda s: print(s, flush=True))
+        ds = sweep(specs_for(a.tensors, a.seed, lo, hi, a.split), dev, log=lambda s: print(s, flush=True))
     if a.dump:
         dump(ds, a.dump)
-    fit_ds = schedtrain.Dataset(ds.samples + [x for x in ds.samples if x.nnz > a.nnz_max] * (a.large_weight - 1))
-    model, hist = schedtrain.train(fit_ds, steps=a.steps, lr=a.lr)
+    model, hist = schedtrain.train(ds, steps=a.steps, lr=a.lr)
     r_model = schedtrain.summarize(schedtrain.regret(ds, model))
     r_default = schedtrain.summarize(schedtrain.regret(ds))
-    meta = {"tensors": a.tensors, "large": a.large, "large_nnz": list(a.large_nnz), "large_weight": a.large_weight,
-            "samples": len(ds.samples),
-            "nnz_max": a.nnz_max, "seed": a.seed,
-            "steps": a.steps, "lr": a.lr, "loss_first_last": [float(hist[0]), float(hist[-1])],
+    meta = {"tensors": a.tensors, "strata": list(strata(a.tensors, lo, hi, a.split)), "nnz_range": [lo, hi],
+            "split": a.split, "samples": len(ds.samples), "seed": a.seed, "steps": a.steps, "lr": a.lr,
+            "loss_first_last": [float(hist[0]), float(hist[-1])],
             "train_regret_learned": r_model, "train_regret_default": r_default}
     save(model, a.out, meta)
     print(json.dumps(meta), flush=True)

@@ -113,8 +113,8 @@ def test_training_on_sweeps_fits_the_timings(cuda_device):
 
 def test_shipped_scheduler_gains_over_the_fixed_default_on_held_out(cuda_device):
     # the model the package ships (trained by train_scheduler.py on the
-    # autotuner's timings of 2,000 generated tensors of 1e5-2e7 non-zeros and
-    # 200 of 2e7-2e8) against the library's
+    # autotuner's timings of 2,000 generated tensors, nnz log-uniform in
+    # [1e5, 2e8]) against the library's
     # fixed default rule, on tensors of the same distribution it never saw
     # (another seed), timed now by the exhaustive autotuner
     from paper_1812_05961_gb300 import train_scheduler
