@@ -280,6 +280,19 @@ NCU_TRAFFIC_BF16 = {"kernel": "mttkrp_table_kernel<3, __nv_bfloat16, 4, 512, 16>
                     "nnz": 34_000_000, "bytes": [648.869632e6, 664.093696e6, 639.894784e6]}
 
 
+def input_checksum(t):
+    """An order-independent integer fingerprint of a COO tensor (the same
+    tensor gives the same value on any machine): per mode the sum of
+    (index + 1) times a mode constant, plus the sum of the values' bit
+    patterns, wrapped to 64 bits."""
+    import torch
+    h = 0
+    for m, x in enumerate(t.inds):
+        h += int(((x.long() + 1) * (2654435761 * (m + 1) + 1)).sum().item())
+    h += int(t.vals.contiguous().view(torch.int32).long().sum().item())
+    return "%016x" % (h % (1 << 64))
+
+
 def fp32_peak_tflops(dev, sm_mhz=None):
     """FP32 FMA peak from the unit counts and the clock: the device's SM
     count x 128 FP32 lanes x 2 flops x the maximum SM clock (from
@@ -873,7 +886,8 @@ def ours(args, rank, world, local):
                        "l2": "inputs larger than L2 (CSF about 0.8 GB per mode)",
                        "parallelism": "replicas" if world > 1 else "single",
                        "nfibs_per_root": nfibs, "level_orders": orders,
-                       "gen_s": round(t_gen, 1), "cpd_create_s": round(t_build, 2)},
+                       "gen_s": round(t_gen, 1), "cpd_create_s": round(t_build, 2),
+                       "input_checksum": input_checksum(t)},
             "roofline": roofline, "cpu_baseline": cpu_base, "e2e": e2e, "gpu_launches": launches,
             "clocks": clocks, "routines_ms_per_iter": routines, "fit": fit, "extras": extras,
         }

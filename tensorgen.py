@@ -90,10 +90,13 @@ def _unique_coords(coords: torch.Tensor, dims) -> torch.Tensor:
 
 
 def _zipf_table(n: int, s: float, device) -> torch.Tensor:
-    k = torch.arange(1, n + 1, dtype=torch.float64, device=device)
+    # built on the CPU, whose cumulative sum adds in a fixed order (a GPU
+    # scan's float64 rounding varied from run to run, and with it a few
+    # drawn coordinates), then moved to the device
+    k = torch.arange(1, n + 1, dtype=torch.float64)
     w = k.pow(-float(s))
     cdf = torch.cumsum(w, 0)
-    return cdf / cdf[-1]
+    return (cdf / cdf[-1]).to(device)
 
 
 def _draw_mode(n_samples, I, dist, s, perm, table, g, device):
