@@ -426,7 +426,9 @@ def mixed4_extra(args, dev):
       fixed count: 25 BF16 iterations + one FP32 refinement sweep against 26
         FP32 iterations (time of the whole run, the sweep included);
       converged: both run until the fit gains less than 1e-5 per iteration
-        (Algorithm 1's stop rule), the mixed run then does its FP32 sweep.
+        (Algorithm 1's stop rule), the mixed run then does its FP32 sweep;
+      and 26 FP32 iterations from the same start rounded to BF16 (the fit's
+        sensitivity to a BF16-sized change of the start alone).
     Also the BF16 R = 64 MTTKRP's HBM fraction under the byte model."""
     import torch
 
@@ -488,6 +490,17 @@ def mixed4_extra(args, dev):
                                      "unit": "GB/s", "frac": ach / peak, "peak_kind": kind}
         del c
         torch.cuda.empty_cache()
+    # plain FP32 from the same start rounded to BF16: how far the 26-iteration
+    # fit moves under a BF16-sized change of the start alone
+    c = sptt.Cpd(t.dims, t.inds, t.vals, R, seed=3).init()
+    start = [c.factor(m).to(torch.bfloat16).float() for m in range(len(t.dims))]
+    c.init(start)
+    c.iterate(26)
+    out["fp32_from_bf16_start_fit_26"] = c.fit()[0]
+    del c, start
+    torch.cuda.empty_cache()
+    out["delta_fit_26_fp32_from_bf16_start_vs_fp32"] = out["fp32_from_bf16_start_fit_26"] - out["fp32"]["fit_26"]
+    out["delta_fit_26_bf16_vs_fp32_from_bf16_start"] = out["bf16"]["fit_26"] - out["fp32_from_bf16_start_fit_26"]
     out["delta_fit_26_bf16_vs_fp32"] = out["bf16"]["fit_26"] - out["fp32"]["fit_26"]
     out["delta_fit_converged_bf16_vs_fp32"] = out["bf16"]["converged"]["fit"] - out["fp32"]["converged"]["fit"]
     out["speedup_26_bf16_plus_sweep_vs_fp32"] = out["fp32"]["total_26_s"] / out["bf16"]["total_26_s"]
