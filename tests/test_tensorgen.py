@@ -55,3 +55,32 @@ def test_batch_specs():
         assert 1 <= nnz <= 2_000_000
     t = tensorgen.batch_member(specs[0][0], min(specs[0][1], 3000), seed=9)
     assert len(set(_keys(t))) == t.nnz
+
+
+def test_scheduler_specs_follow_the_log_uniform_law_in_two_strata():
+    # the training draw: tensor k of a stratum is the same whatever the count,
+    # the strata split n in the law's proportion, every nnz is inside its
+    # stratum's range (or capped at a quarter of the index space)
+    from paper_1812_05961_gb300 import train_scheduler as ts
+    lo, hi, split = 1e5, 2e8, 2e7
+    below, above = ts.strata(2000, lo, hi, split)
+    assert (below, above) == (1394, 606)
+    assert ts.strata(10, lo, hi, 1e9) == (10, 0) and ts.strata(10, lo, hi, 1.0) == (0, 10)
+    a = ts.tensor_specs(50, 21, split, lo)
+    assert ts.tensor_specs(20, 21, split, lo) == a[:20]
+    specs = ts.specs_for(200, 77, lo, hi, split)
+    assert len(specs) == 200
+    for k, (dims, nnz, s, R, seed) in enumerate(specs):
+        space = 1.0
+        for d in dims:
+            space *= d
+        top = split if k < 139 else hi
+        bot = lo if k < 139 else split
+        assert 3 <= len(dims) <= 5 and R in (8, 16, 32, 64) and 0.8 <= s <= 1.5
+        assert nnz <= top and (nnz >= bot or nnz >= min(space / 4, bot) - 1 or nnz == 1000)
+
+
+def test_zipf_table_is_built_on_the_host():
+    # the same table whatever the device it is asked for (a fixed-order sum)
+    t = tensorgen._zipf_table(1000, 1.1, "cpu")
+    assert t.dtype == torch.float64 and t[-1] == 1.0 and bool((t[1:] >= t[:-1]).all())
