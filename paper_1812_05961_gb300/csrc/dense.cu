@@ -338,6 +338,22 @@ sptt_status dense_work_alloc(DenseWork *w, int32_t rank, int32_t ld, int64_t /*m
                                    (int)sizeof(dense::SolveTile<32>)));
     SPTT_CUDA(cudaFuncSetAttribute(postsolve_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)sizeof(dense::SolveTile<64>)));
+    int per_sm = 0;
+    switch (rank_pad(rank)) {
+        case 16:
+            SPTT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, postsolve_kernel<16>, kThreads,
+                                                                    sizeof(dense::SolveTile<16>)));
+            break;
+        case 32:
+            SPTT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, postsolve_kernel<32>, kThreads,
+                                                                    sizeof(dense::SolveTile<32>)));
+            break;
+        default:
+            SPTT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, postsolve_kernel<64>, kThreads,
+                                                                    sizeof(dense::SolveTile<64>)));
+            break;
+    }
+    w->solve_resident = device_sm_count() * (per_sm > 0 ? per_sm : 1);
     return SPTT_OK;
 }
 
@@ -378,13 +394,15 @@ sptt_status normal_prep_launch(double *const *grams, int32_t nmodes, int32_t n, 
     return SPTT_OK;
 }
 
-// One CTA per tile of rows up to the workspace's CTA count: a mode with few
-// rows leaves no CTA idle that the partial reduction would then read.
+// One CTA per tile of rows up to the CTAs the GPU holds at once: a mode with
+// few rows leaves no CTA idle that the partial reduction would then read, and
+// a large one runs in one wave, each CTA looping over its tiles.
 template <int RP>
 static int postsolve_dispatch(const float *M, const double *heavy, const int32_t *hidx, const int32_t *fids0,
                               float *A, int64_t rows, DenseWork *w, int pstride, cudaStream_t st) {
     const int64_t tiles = (rows + dense::SolveTile<RP>::TR - 1) / dense::SolveTile<RP>::TR;
-    const int nb = (int)(tiles < w->nblocks ? (tiles > 0 ? tiles : 1) : w->nblocks);
+    const int cap = w->solve_resident > 0 && w->solve_resident < w->nblocks ? w->solve_resident : w->nblocks;
+    const int nb = (int)(tiles < cap ? (tiles > 0 ? tiles : 1) : cap);
     postsolve_kernel<RP><<<nb, kThreads, sizeof(dense::SolveTile<RP>), st>>>(
         M, heavy, hidx, fids0, A, rows, w->rank, w->ld, w->W, w->partials, pstride);
     return nb;

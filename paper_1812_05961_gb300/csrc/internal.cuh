@@ -244,6 +244,7 @@ sptt_status tile_accumulate_launch(const sptt_csf *tile, const float *compact, c
 struct DenseWork {
     int32_t rank = 0, ld = 0;
     int32_t nblocks = 0;          // blocks of the row kernels (partials per block)
+    int32_t solve_resident = 0;   // row-solve CTAs resident on the GPU at once (its rank's tile)
     double *partials = nullptr;   // [nblocks][rank*rank + rank]
     double *gram_un = nullptr;    // rank*rank (+ rank dots)
     float *W = nullptr;           // rank*rank (FP32 copy of V^dagger)
